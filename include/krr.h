@@ -1,0 +1,190 @@
+/*
+ * krr.h -- C ABI of the GB300 kernel ridge regression library.
+ *
+ * The library solves the kernel ridge regression system (K + lambda I) c = y
+ * (Eq. (1) of Avron, Clarkson, Woodruff, "Faster Kernel Ridge Regression Using
+ * Sketching and Preconditioning") for the Gaussian kernel
+ * k(x, z) = exp(-||x - z||^2 / (2 sigma^2)) (Section 5) by preconditioned
+ * conjugate gradients with the random-Fourier-feature preconditioner
+ * Z Z^T + lambda_p I applied through the Woodbury identity (Algorithm 1,
+ * Section 3.1).  K is never stored: every product with it is recomputed.
+ *
+ * Conventions (every entry point):
+ *  - Every function returns a krr_status; KRR_OK is 0.  On any other status
+ *    krr_last_error(h) returns a message describing the failure.
+ *  - Matrices are row-major with an explicit leading dimension (elements).
+ *  - Pointers are plain device pointers unless the function says "host or
+ *    device": those accept either and stage host buffers through the
+ *    library's workspace.  The caller owns every input and output buffer.
+ *  - The handle owns its workspace and the preconditioner factors; it
+ *    allocates device memory lazily and frees it in krr_destroy.
+ *  - All work is enqueued on the handle's stream.  Entry points that return
+ *    device results return without synchronising except where a status
+ *    depends on device data (the solves, precond setup), which read a few
+ *    bytes back at the end.
+ *  - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef KRR_H_
+#define KRR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int krr_status;
+enum {
+  KRR_OK = 0,
+  KRR_EINVAL = 1,       /* bad argument (size, pointer, leading dimension)  */
+  KRR_ENOMEM = 2,       /* device allocation failed                         */
+  KRR_ECUDA = 3,        /* a CUDA runtime call failed                       */
+  KRR_ECHOL = 4,        /* Z^T Z + lambda_p I not positive definite         */
+  KRR_ENOTCONV = 5,     /* max_iter reached; outputs hold the last iterate  */
+  KRR_EBREAKDOWN = 6,   /* p.q <= 0 or r.z <= 0 (indefinite operator)       */
+  KRR_ENAN = 7,         /* NaN or Inf met in the iteration                  */
+  KRR_ETIMEOUT = 8,     /* a device loop hit its iteration cap              */
+  KRR_EUNSUPPORTED = 9  /* valid request this build does not implement      */
+};
+
+/* Arithmetic of a kernel-matrix product (the n^2 part of each iteration). */
+typedef enum {
+  KRR_FP64 = 0,        /* FP64 SIMT: distances from coordinate differences  */
+  KRR_FP32 = 1,        /* FP32 SIMT: the plain single-precision path        */
+  KRR_BF16 = 2,        /* tcgen05 BF16 tensor cores, FP32 accumulation      */
+  KRR_HP = 3,          /* extended precision for refinement residuals       */
+  KRR_MIXED = 4        /* solver only: BF16 inner PCG + HP refinement       */
+} krr_precision;
+
+/* How the preconditioner is applied (Section 3.1). */
+typedef enum {
+  KRR_APPLY_ZL = 0,    /* z = (r - Z L^-T L^-1 Z^T r) / lambda_p            */
+  KRR_APPLY_U = 1      /* z = (r - U^T U r) / lambda_p, U = L^-1 Z^T        */
+} krr_apply_form;
+
+#define KRR_MAX_RHS 16
+
+typedef struct {
+  double tol;          /* relative residual target tau (default 1e-6)        */
+  int max_iter;        /* PCG iteration cap (default 1000, Section 5)        */
+  double lambda_p;     /* preconditioner ridge; 0 means lambda (Table 2)     */
+  int precond;         /* 1: RFF Woodbury preconditioner, 0: plain CG        */
+  int precision;       /* krr_precision; KRR_MIXED adds refinement           */
+  int apply_form;      /* krr_apply_form                                     */
+  int use_graph;       /* 1: PCG loop as a CUDA-graph while node             */
+  double inner_tol;    /* KRR_MIXED: inner PCG relative tolerance            */
+  int max_outer;       /* KRR_MIXED: refinement step cap                     */
+  int z_bf16;          /* store Z in BF16 (-1 auto: BF16 for BF16/MIXED)     */
+  int warm_start;      /* 1: C holds x0 on entry                             */
+} krr_opts;
+
+typedef struct {
+  int status;                       /* same value the call returned          */
+  int k;                            /* number of right-hand sides            */
+  int iters[KRR_MAX_RHS];           /* PCG iterations per column (all steps) */
+  double rel_res[KRR_MAX_RHS];      /* final relative residual per column,   */
+                                    /* computed on device in the solve's     */
+                                    /* residual arithmetic                   */
+  int outer_steps;                  /* refinement steps (KRR_MIXED)          */
+  int matvecs;                      /* kernel-matrix products launched       */
+  double ms_setup;                  /* features + Gram + Cholesky + factors  */
+  double ms_solve;                  /* PCG (and refinement)                  */
+  double ms_total;
+} krr_report;
+
+typedef struct krr_handle krr_handle;
+
+/* Fill *o with the defaults listed above. */
+void krr_default_opts(krr_opts* o);
+
+/* Create a handle bound to `stream` (a cudaStream_t; NULL = legacy default
+ * stream) on the current device. */
+krr_status krr_create(krr_handle** h, void* stream);
+krr_status krr_destroy(krr_handle* h);
+krr_status krr_set_stream(krr_handle* h, void* stream);
+const char* krr_last_error(const krr_handle* h);
+const char* krr_status_string(krr_status s);
+
+/*
+ * Random Fourier features, Section 2.2:
+ *   Z[i, j] = sqrt(2/s) * cos(sum_t X[i, t] W[t, j] + b[j]).
+ * X: n x d (ldx), W: d x s (lds = s), b: s, Z: n x s output (ldz), all FP32.
+ * W has N(0, sigma^-2) entries and b is U[0, 2 pi) for the Gaussian kernel;
+ * they are inputs so that callers can reproduce a draw.
+ */
+krr_status krr_rff_features(krr_handle* h, const float* X, int n, int d, int ldx,
+                            const float* W, const float* b, int s,
+                            float* Z, int ldz);
+
+/*
+ * Kernel-matrix product, the per-iteration cost the paper names dominant
+ * (Section 3.1, "multiplying the kernel matrix by a vector"):
+ *   Q[i, :] = sum_j k(xr_i, xc_j) V[j, :] + shift * V[i, :]
+ * Xr: nr x d (ldxr), Xc: nc x d (ldxc), FP32.  V: nc x k (ldv), Q: nr x k
+ * (ldq).  V and Q are double for KRR_FP64 and KRR_HP and float for KRR_FP32
+ * and KRR_BF16.  `shift` (lambda of Eq. (1)) needs nr == nc and is added
+ * only when it is nonzero; pass Xr == Xc for the training system.
+ * 1 <= k <= KRR_MAX_RHS.
+ */
+krr_status krr_kernel_matvec(krr_handle* h, const float* Xr, int nr, int ldxr,
+                             const float* Xc, int nc, int ldxc, int d,
+                             double sigma, double shift,
+                             const void* V, int k, int ldv, void* Q, int ldq,
+                             int precision);
+
+/*
+ * Preconditioner set-up, Algorithm 1 lines 6-7 and Section 3.1:
+ *   G = Z^T Z + lambda_p I_s (FP64 accumulation), L L^T = G (FP64
+ *   Cholesky, lower L), then either U = L^-1 Z^T (KRR_APPLY_U, stored FP32
+ *   s x n) or L^-1 kept for triangular solves (KRR_APPLY_ZL).
+ * Z: n x s (ldz) FP32; the handle keeps its own copy (BF16 when z_bf16 is
+ * 1, in which case G is formed from the rounded values so that the stored
+ * factors describe exactly the operator applied).  s <= n.
+ * Returns KRR_ECHOL when a pivot of the Cholesky factorisation is <= 0.
+ */
+krr_status krr_precond_setup(krr_handle* h, const float* Z, int n, int s, int ldz,
+                             double lambda_p, int apply_form, int z_bf16);
+
+/*
+ * Apply the preconditioner inverse of the last krr_precond_setup
+ * (Algorithm 1 line 9):  Zout = (Z Z^T + lambda_p I)^-1 R.
+ * R, Zout: n x k double (ldr, ldo).  1 <= k <= KRR_MAX_RHS.
+ */
+krr_status krr_precond_apply(krr_handle* h, const double* R, int k, int ldr,
+                             double* Zout, int ldo);
+
+/*
+ * Algorithm 1 end to end: RFF features from (W, b), preconditioner set-up,
+ * PCG from x0 = 0 (or C when opts->warm_start) on (K + lambda I) C = Y,
+ * stopping when ||y - (K + lambda I) c|| <= tol ||y|| for every column
+ * (Section 5).  X: n x d (ldx) FP32; W: d x s FP32; b: s FP32;
+ * Y, C: n x k double (ldy, ldc).  X, W, b, Y and C may be host or device
+ * pointers.  With opts->precision == KRR_MIXED the inner PCG runs the BF16
+ * tensor-core product and an outer refinement loop recomputes the residual
+ * in KRR_HP arithmetic and FP64 vectors.  `rep` (may be NULL) receives the
+ * per-column report.  Returns KRR_ENOTCONV if max_iter is reached (C holds
+ * the last iterate), KRR_EBREAKDOWN / KRR_ENAN on breakdown.
+ */
+krr_status krr_pcg_solve(krr_handle* h, const float* X, int n, int d, int ldx,
+                         double sigma, double lambda,
+                         const float* W, const float* b, int s,
+                         const double* Y, int k, int ldy, double* C, int ldc,
+                         const krr_opts* opts, krr_report* rep);
+
+/*
+ * Predictor f(x) = sum_i c_i k(x_i, x) (Section 1) at m held-out points:
+ *   F = K(Xte, Xtr) C.  Xtr: n x d (ldxtr), Xte: m x d (ldxte) FP32,
+ * C: n x k double (ldc), F: m x k double (ldf); device pointers.
+ * precision: KRR_FP64, KRR_HP or KRR_FP32 (FP32 then widened).
+ */
+krr_status krr_predict(krr_handle* h, const float* Xtr, int n, int ldxtr,
+                       const float* Xte, int m, int ldxte, int d, double sigma,
+                       const double* C, int k, int ldc, double* F, int ldf,
+                       int precision);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KRR_H_ */

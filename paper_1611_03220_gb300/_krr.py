@@ -1,0 +1,222 @@
+"""ctypes binding of ``include/krr.h``: argument marshalling only.
+
+Every function here takes tensors (device) or numpy arrays (host), passes
+their pointers and sizes to the C ABI of the same name and raises
+``KrrError`` on a non-zero status.  No arithmetic of the method happens in
+Python.  The library must have been built (``paper_1611_03220_gb300.build()``);
+a missing library raises ``ImportError`` at import time, there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkrr_gb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: run paper_1611_03220_gb300.build() first")
+_lib = C.CDLL(LIB_PATH)
+
+KRR_MAX_RHS = 16
+STATUS = {0: "KRR_OK", 1: "KRR_EINVAL", 2: "KRR_ENOMEM", 3: "KRR_ECUDA", 4: "KRR_ECHOL",
+          5: "KRR_ENOTCONV", 6: "KRR_EBREAKDOWN", 7: "KRR_ENAN", 8: "KRR_ETIMEOUT",
+          9: "KRR_EUNSUPPORTED"}
+KRR_OK, KRR_EINVAL, KRR_ENOMEM, KRR_ECUDA, KRR_ECHOL = 0, 1, 2, 3, 4
+KRR_ENOTCONV, KRR_EBREAKDOWN, KRR_ENAN, KRR_ETIMEOUT, KRR_EUNSUPPORTED = 5, 6, 7, 8, 9
+PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2, "hp": 3, "mixed": 4}
+APPLY_FORM = {"zl": 0, "u": 1}
+
+
+class krr_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("lambda_p", C.c_double),
+                ("precond", C.c_int), ("precision", C.c_int), ("apply_form", C.c_int),
+                ("use_graph", C.c_int), ("inner_tol", C.c_double), ("max_outer", C.c_int),
+                ("z_bf16", C.c_int), ("warm_start", C.c_int)]
+
+
+class krr_report(C.Structure):
+    _fields_ = [("status", C.c_int), ("k", C.c_int), ("iters", C.c_int * KRR_MAX_RHS),
+                ("rel_res", C.c_double * KRR_MAX_RHS), ("outer_steps", C.c_int),
+                ("matvecs", C.c_int), ("ms_setup", C.c_double), ("ms_solve", C.c_double),
+                ("ms_total", C.c_double)]
+
+    def as_dict(self) -> dict:
+        k = self.k
+        return {"status": STATUS.get(self.status, self.status), "k": k,
+                "iters": list(self.iters[:k]), "rel_res": list(self.rel_res[:k]),
+                "outer_steps": self.outer_steps, "matvecs": self.matvecs,
+                "ms_setup": self.ms_setup, "ms_solve": self.ms_solve, "ms_total": self.ms_total}
+
+
+_vp, _i, _d = C.c_void_p, C.c_int, C.c_double
+_SIGS = {
+    "krr_default_opts": (None, [C.POINTER(krr_opts)]),
+    "krr_create": (_i, [C.POINTER(_vp), _vp]),
+    "krr_destroy": (_i, [_vp]),
+    "krr_set_stream": (_i, [_vp, _vp]),
+    "krr_last_error": (C.c_char_p, [_vp]),
+    "krr_status_string": (C.c_char_p, [_i]),
+    "krr_rff_features": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _i, _vp, _i]),
+    "krr_kernel_matvec": (_i, [_vp, _vp, _i, _i, _vp, _i, _i, _i, _d, _d, _vp, _i, _i, _vp, _i, _i]),
+    "krr_precond_setup": (_i, [_vp, _vp, _i, _i, _i, _d, _i, _i]),
+    "krr_precond_apply": (_i, [_vp, _vp, _i, _i, _vp, _i]),
+    "krr_pcg_solve": (_i, [_vp, _vp, _i, _i, _i, _d, _d, _vp, _vp, _i, _vp, _i, _i, _vp, _i,
+                           C.POINTER(krr_opts), C.POINTER(krr_report)]),
+    "krr_predict": (_i, [_vp, _vp, _i, _i, _vp, _i, _i, _i, _d, _vp, _i, _i, _vp, _i, _i]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+class KrrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(a) -> int:
+    """Data pointer of a torch tensor or a numpy array (no copy)."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _ld(a) -> int:
+    """Leading dimension (elements) of a row-major 2-D array."""
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"] or a.strides[1] == a.itemsize, "inner stride must be 1"
+        return a.strides[0] // a.itemsize
+    assert a.stride(1) == 1, "inner stride must be 1"
+    return a.stride(0)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Handle:
+    """Owns a ``krr_handle`` bound to a CUDA stream (torch's current one by default)."""
+
+    def __init__(self, stream=None):
+        self._h = _vp()
+        st = _lib.krr_create(C.byref(self._h), _stream_ptr(stream))
+        if st != KRR_OK:
+            raise KrrError(st, "krr_create failed")
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def set_stream(self, stream=None):
+        self._check(_lib.krr_set_stream(self._h, _stream_ptr(stream)))
+
+    def _check(self, st: int):
+        if st != KRR_OK:
+            raise KrrError(st, _lib.krr_last_error(self._h).decode())
+
+    def close(self):
+        if self._h:
+            _lib.krr_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def default_opts(**kw) -> krr_opts:
+    o = krr_opts()
+    _lib.krr_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISION[v]
+        if k == "apply_form" and isinstance(v, str):
+            v = APPLY_FORM[v]
+        setattr(o, k, v)
+    return o
+
+
+def krr_rff_features(h: Handle, X, W, b, Z):
+    """Z = sqrt(2/s) cos(X W + b) into the caller's Z (n x s float32, device)."""
+    n, d = X.shape
+    s = W.shape[1]
+    h._check(_lib.krr_rff_features(h.ptr, _ptr(X), n, d, _ld(X), _ptr(W), _ptr(b), s,
+                                   _ptr(Z), _ld(Z)))
+    return Z
+
+
+def krr_kernel_matvec(h: Handle, Xr, Xc, sigma: float, shift: float, V, Q, precision="fp64"):
+    """Q = K(Xr, Xc) V + shift V into the caller's Q (device tensors)."""
+    nr, d = Xr.shape
+    nc = Xc.shape[0]
+    k = V.shape[1]
+    prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    h._check(_lib.krr_kernel_matvec(h.ptr, _ptr(Xr), nr, _ld(Xr), _ptr(Xc), nc, _ld(Xc), d,
+                                    float(sigma), float(shift), _ptr(V), k, _ld(V), _ptr(Q),
+                                    _ld(Q), prec))
+    return Q
+
+
+def krr_precond_setup(h: Handle, Z, lambda_p: float, apply_form="zl", z_bf16: bool = False):
+    n, s = Z.shape
+    form = APPLY_FORM[apply_form] if isinstance(apply_form, str) else int(apply_form)
+    h._check(_lib.krr_precond_setup(h.ptr, _ptr(Z), n, s, _ld(Z), float(lambda_p), form,
+                                    1 if z_bf16 else 0))
+
+
+def krr_precond_apply(h: Handle, R, Zout):
+    k = R.shape[1]
+    h._check(_lib.krr_precond_apply(h.ptr, _ptr(R), k, _ld(R), _ptr(Zout), _ld(Zout)))
+    return Zout
+
+
+def krr_pcg_solve(h: Handle, X, sigma: float, lam: float, W, b, Y, C_out, opts: krr_opts | None = None,
+                  check: bool = True) -> dict:
+    """Algorithm 1 end to end into C_out; host (numpy) or device (torch) buffers.
+
+    Returns the report as a dict.  With ``check`` a non-OK status raises
+    (KRR_ENOTCONV included); otherwise the status is only reported.
+    """
+    n, d = X.shape
+    k = Y.shape[1]
+    s = W.shape[1] if W is not None else 0
+    rep = krr_report()
+    o = opts if opts is not None else default_opts()
+    st = _lib.krr_pcg_solve(h.ptr, _ptr(X), n, d, _ld(X), float(sigma), float(lam),
+                            _ptr(W) if W is not None else None,
+                            _ptr(b) if b is not None else None, s,
+                            _ptr(Y), k, _ld(Y), _ptr(C_out), _ld(C_out), C.byref(o), C.byref(rep))
+    if check:
+        h._check(st)
+    out = rep.as_dict()
+    out["status_code"] = st
+    return out
+
+
+def krr_predict(h: Handle, Xtr, Xte, sigma: float, Cc, F, precision="fp64"):
+    n, d = Xtr.shape
+    m = Xte.shape[0]
+    k = Cc.shape[1]
+    prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    h._check(_lib.krr_predict(h.ptr, _ptr(Xtr), n, _ld(Xtr), _ptr(Xte), m, _ld(Xte), d,
+                              float(sigma), _ptr(Cc), k, _ld(Cc), _ptr(F), _ld(F), prec))
+    return F

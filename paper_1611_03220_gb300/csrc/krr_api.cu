@@ -1,0 +1,850 @@
+// C ABI entry points, handle and the PCG driver.
+//
+// Algorithm 1 of the paper, end to end on one GPU:
+//   features Z (Section 2.2) -> G = Z^T Z + lambda_p I -> L L^T = G ->
+//   factors for the Woodbury apply (Section 3.1) -> PCG on (K + lambda I) c = y
+//   with K applied on the fly (Algorithm 1 line 9), stopping on the relative
+//   residual of every column (Section 5).
+// The PCG iteration is captured once per solve into a CUDA graph whose body
+// sits under a conditional WHILE node; the loop's last kernel decides on the
+// device whether to run again, so an entire solve is one graph launch.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <mutex>
+
+#include "krr_internal.cuh"
+#include "krr_tc.cuh"
+
+using namespace krr;
+
+struct krr_handle {
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;  // private stream for graph capture
+  int device = 0;
+  std::string err;
+  std::map<std::string, DevBuf> bufs;
+  Precond pc;
+  CgScalars* sc = nullptr;      // device
+  CgScalars* sc_host = nullptr; // pinned mirror
+  double* hostd = nullptr;      // pinned scratch (KRR_MAX_RHS * 4 doubles)
+  int* info = nullptr;          // device int
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  TcState tc;
+};
+
+namespace krr {
+
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!cached[dev]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+      v = 148;
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
+}  // namespace krr
+
+namespace {
+
+bool trace_on() {
+  static int on = -1;
+  if (on < 0) on = getenv("KRR_TRACE") ? 1 : 0;
+  return on == 1;
+}
+#define KRR_TRACE(...)                   \
+  do {                                   \
+    if (trace_on()) {                    \
+      fprintf(stderr, "[krr] " __VA_ARGS__); \
+      fprintf(stderr, "\n");             \
+      fflush(stderr);                    \
+    }                                    \
+  } while (0)
+
+void* ws(krr_handle* h, const std::string& name, size_t bytes) {
+  DevBuf& b = h->bufs[name];
+  if (bytes == 0) bytes = 16;
+  if (b.bytes < bytes) {
+    if (b.p) {
+      KRR_CUDA(cudaStreamSynchronize(h->stream));
+      KRR_CUDA(cudaFree(b.p));
+      b.p = nullptr;
+      b.bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw Error{KRR_ENOMEM, "cudaMalloc(" + std::to_string(bytes) + ") for " + name + ": " +
+                                  cudaGetErrorString(e)};
+    }
+    b.bytes = bytes;
+  }
+  return b.p;
+}
+
+template <typename T>
+T* wsT(krr_handle* h, const std::string& name, size_t elems) {
+  return reinterpret_cast<T*>(ws(h, name, elems * sizeof(T)));
+}
+
+void ensure_buf(DevBuf& b, size_t bytes) {
+  if (b.bytes >= bytes) return;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error{KRR_ENOMEM, std::string("preconditioner allocation: ") + cudaGetErrorString(e)};
+  }
+  b.bytes = bytes;
+}
+
+void free_buf(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+bool on_device(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Returns a device copy of a host-or-device buffer of `bytes`.
+const void* stage_in(krr_handle* h, const void* p, size_t bytes, const char* name) {
+  if (on_device(p)) return p;
+  void* d = ws(h, std::string("stage_") + name, bytes);
+  KRR_CUDA(cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, h->stream));
+  return d;
+}
+
+template <typename F>
+krr_status guard(krr_handle* h, F&& f) {
+  if (!h) return KRR_EINVAL;
+  try {
+    h->err.clear();
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != h->device) KRR_CUDA(cudaSetDevice(h->device));
+    krr_status st = f();
+    if (cur != h->device) cudaSetDevice(cur);
+    return st;
+  } catch (const Error& e) {
+    h->err = e.msg;
+    return e.st;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    return KRR_ECUDA;
+  }
+}
+
+double ms_between(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+    cudaGetLastError();
+    return 0.0;
+  }
+  return (double)ms;
+}
+
+// --------------------------------------------------------- kernel product --
+// Q = K(Xr, Xc) V + shift V in the requested arithmetic; V/Q double for
+// FP64/HP, float for FP32/BF16.
+void matvec_dispatch(krr_handle* h, cudaStream_t st, const float* Xr, int nr, int ldxr,
+                     const float* Xc, int nc, int ldxc, int d, double sigma, double shift,
+                     const void* V, int k, int ldv, void* Q, int ldq, int prec) {
+  switch (prec) {
+    case KRR_FP64:
+    case KRR_HP: {
+      double* part = wsT<double>(h, "mv_part64", mv_fp64_part_elems(nr, nc, k));
+      launch_mv_fp64(st, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, shift, (const double*)V, k, ldv,
+                     (double*)Q, ldq, part);
+      return;
+    }
+    case KRR_FP32: {
+      float* part = wsT<float>(h, "mv_part32", mv_fp32_part_elems(nr, nc, k));
+      float* nr_ = wsT<float>(h, "mv_nrm_r", (size_t)nr);
+      float* nc_ = wsT<float>(h, "mv_nrm_c", (size_t)nc);
+      launch_mv_fp32(st, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, shift, (const float*)V, k, ldv,
+                     (float*)Q, ldq, nr_, nc_, part);
+      return;
+    }
+    case KRR_BF16: {
+      tc_matvec(h->tc, st, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, shift, (const float*)V, k, ldv,
+                (float*)Q, ldq);
+      return;
+    }
+    default:
+      throw Error{KRR_EINVAL, "unknown precision " + std::to_string(prec)};
+  }
+}
+
+// Allocate the product's workspace ahead of a graph capture (no allocation
+// may happen while the loop body is being captured).
+void matvec_reserve(krr_handle* h, int n, int k, int prec) {
+  switch (prec) {
+    case KRR_FP64:
+    case KRR_HP:
+      wsT<double>(h, "mv_part64", mv_fp64_part_elems(n, n, k));
+      return;
+    case KRR_FP32:
+      wsT<float>(h, "mv_part32", mv_fp32_part_elems(n, n, k));
+      wsT<float>(h, "mv_nrm_r", (size_t)n);
+      wsT<float>(h, "mv_nrm_c", (size_t)n);
+      return;
+    case KRR_BF16:
+      tc_reserve(h->tc, h->stream, k);
+      return;
+    default:
+      return;
+  }
+}
+
+// ------------------------------------------------------------------- PCG --
+struct LoopOut {
+  int iters[KRR_MAX_RHS];
+  double rr[KRR_MAX_RHS];
+  double yy[KRR_MAX_RHS];
+  int flags;
+  int iter;
+};
+
+template <typename T>
+void pcg_loop(krr_handle* h, int n, int k, const double* Ytol, int ldy, T* x, T* r, T* p, T* z,
+              T* q, double tol, int max_iter, bool use_graph,
+              const std::function<void(cudaStream_t, const T*, T*)>& matvec,
+              const std::function<void(cudaStream_t, const T*, T*)>& apply, LoopOut* out,
+              int* matvecs, int prec) {
+  cudaStream_t st = h->stream;
+  double* part = wsT<double>(h, "cg_part", cg_part_elems(n, k));
+  matvec_reserve(h, n, k, prec);
+  launch_cg_init<T>(st, h->sc, Ytol, ldy, r, n, k, tol, max_iter, part);
+  if (apply)
+    apply(st, r, z);
+  else
+    KRR_CUDA(cudaMemcpyAsync(z, r, (size_t)n * k * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  launch_cg_rz_first<T>(st, h->sc, r, z, p, n, k, part);
+
+  auto body = [&](cudaStream_t s2, unsigned long long cond) {
+    matvec(s2, p, q);
+    launch_cg_alpha<T>(s2, h->sc, p, q, n, k, part);
+    launch_cg_update_xr<T>(s2, h->sc, x, r, p, q, n, k, part);
+    if (apply)
+      apply(s2, r, z);
+    else
+      KRR_CUDA(cudaMemcpyAsync(z, r, (size_t)n * k * sizeof(T), cudaMemcpyDeviceToDevice, s2));
+    launch_cg_rz<T>(s2, h->sc, r, z, n, k, part);
+    launch_cg_update_p<T>(s2, h->sc, p, z, n, k);
+    launch_cg_tail(s2, h->sc, cond);
+  };
+
+  int launched = 0;
+  if (max_iter > 0) {
+    if (use_graph) {
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      KRR_TRACE("pcg_loop: graph create n=%d k=%d max_iter=%d", n, k, max_iter);
+      KRR_CUDA(cudaGraphCreate(&graph, 0));
+      try {
+        cudaGraphConditionalHandle cond;
+        KRR_CUDA(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams params = {cudaGraphNodeTypeConditional};
+        params.conditional.handle = cond;
+        params.conditional.type = cudaGraphCondTypeWhile;
+        params.conditional.size = 1;
+        cudaGraphNode_t node;
+        KRR_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &params));
+        KRR_TRACE("pcg_loop: conditional node added, out=%p", (void*)params.conditional.phGraph_out);
+        cudaGraph_t bodyg = params.conditional.phGraph_out[0];
+        KRR_CUDA(cudaStreamBeginCaptureToGraph(h->cap, bodyg, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeRelaxed));
+        try {
+          body(h->cap, (unsigned long long)cond);
+        } catch (...) {
+          cudaGraph_t tmp;
+          cudaStreamEndCapture(h->cap, &tmp);
+          cudaGetLastError();
+          throw;
+        }
+        cudaGraph_t captured = nullptr;
+        KRR_TRACE("pcg_loop: body captured");
+        KRR_CUDA(cudaStreamEndCapture(h->cap, &captured));
+        KRR_TRACE("pcg_loop: capture ended");
+        KRR_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+        KRR_TRACE("pcg_loop: instantiated");
+        KRR_CUDA(cudaGraphLaunch(exec, st));
+        KRR_TRACE("pcg_loop: launched");
+      } catch (...) {
+        if (exec) cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        throw;
+      }
+      KRR_CUDA(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+      KRR_CUDA(cudaStreamSynchronize(st));
+      cudaGraphExecDestroy(exec);
+      cudaGraphDestroy(graph);
+      launched = h->sc_host->iter;
+    } else {
+      // host-driven loop: checks the device scalars every `chk` iterations
+      const int chk = 8;
+      for (int it = 0; it < max_iter; ++it) {
+        body(st, 0ull);
+        ++launched;
+        if ((it + 1) % chk == 0 || it + 1 == max_iter) {
+          KRR_CUDA(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+          KRR_CUDA(cudaStreamSynchronize(st));
+          int any = 0;
+          for (int c = 0; c < k; ++c) any |= h->sc_host->active[c];
+          if (!any || (h->sc_host->flags & (FLAG_BREAKDOWN | FLAG_NAN)) ||
+              h->sc_host->iter >= max_iter)
+            break;
+        }
+      }
+    }
+  }
+  KRR_CUDA(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+  KRR_CUDA(cudaStreamSynchronize(st));
+  for (int c = 0; c < k; ++c) {
+    out->iters[c] = h->sc_host->iters[c];
+    out->rr[c] = h->sc_host->rr[c];
+    out->yy[c] = h->sc_host->yy[c];
+  }
+  out->flags = h->sc_host->flags;
+  out->iter = h->sc_host->iter;
+  if (matvecs) *matvecs += launched;
+}
+
+// Per-column ||a_c||^2 read back to the host.
+template <typename T>
+void host_colnorm2(krr_handle* h, const T* a, int n, int k, int lda, double* out) {
+  double* part = wsT<double>(h, "cg_part", cg_part_elems(n, k));
+  double* dout = wsT<double>(h, "colnorm_out", KRR_MAX_RHS);
+  unsigned int* ctr = wsT<unsigned int>(h, "colnorm_ctr", 4);
+  KRR_CUDA(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned int), h->stream));
+  launch_colnorm2<T>(h->stream, a, n, k, lda, dout, part, ctr);
+  KRR_CUDA(cudaMemcpyAsync(h->hostd, dout, k * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  KRR_CUDA(cudaStreamSynchronize(h->stream));
+  for (int c = 0; c < k; ++c) out[c] = h->hostd[c];
+}
+
+void precond_setup_impl(krr_handle* h, const float* Z, int n, int s, int ldz, double lambda_p,
+                        int form, int z_bf16) {
+  KRR_REQUIRE(Z && n > 0 && s > 0 && ldz >= s, "precond_setup: bad Z / sizes");
+  KRR_REQUIRE(s <= n, "precond_setup: need s <= n");
+  KRR_REQUIRE(lambda_p > 0.0 && std::isfinite(lambda_p), "precond_setup: lambda_p must be > 0");
+  KRR_REQUIRE(form == KRR_APPLY_ZL || form == KRR_APPLY_U, "precond_setup: bad apply form");
+  cudaStream_t st = h->stream;
+  Precond& pc = h->pc;
+  pc.ready = false;
+  const size_t esz = z_bf16 ? 2 : 4;
+  ensure_buf(pc.Z, (size_t)n * s * esz);
+  launch_copy_z(st, Z, n, s, ldz, pc.Z.p, z_bf16);
+  ensure_buf(pc.L, (size_t)s * s * sizeof(double));
+  const int nch = gram_chunks(n, s);
+  double* part = wsT<double>(h, "gram_part", (size_t)nch * s * s);
+  launch_gram(st, pc.Z.p, z_bf16, n, s, lambda_p, (double*)pc.L.p, part, nch);
+  launch_cholesky(st, (double*)pc.L.p, s, h->info);
+  int info = 0;
+  KRR_CUDA(cudaMemcpyAsync(&h->hostd[0], h->info, sizeof(int), cudaMemcpyDeviceToHost, st));
+  KRR_CUDA(cudaStreamSynchronize(st));
+  memcpy(&info, &h->hostd[0], sizeof(int));
+  if (info != 0)
+    throw Error{KRR_ECHOL, "Z^T Z + lambda_p I is not positive definite (pivot " +
+                               std::to_string(info - 1) + ")"};
+  ensure_buf(pc.Linv, (size_t)s * s * sizeof(double));
+  launch_tri_inverse(st, (const double*)pc.L.p, s, (double*)pc.Linv.p);
+  if (form == KRR_APPLY_ZL) {
+    ensure_buf(pc.LinvT, (size_t)s * s * sizeof(double));
+    launch_transpose_d(st, (const double*)pc.Linv.p, s, (double*)pc.LinvT.p);
+    free_buf(pc.U);
+  } else {
+    ensure_buf(pc.U, (size_t)s * n * sizeof(float));
+    launch_form_u(st, (const double*)pc.Linv.p, pc.Z.p, z_bf16, n, s, (float*)pc.U.p);
+  }
+  pc.n = n;
+  pc.s = s;
+  pc.form = form;
+  pc.z_bf16 = z_bf16;
+  pc.lam_p = lambda_p;
+  pc.ready = true;
+}
+
+template <typename T>
+void apply_precond(krr_handle* h, cudaStream_t st, const T* R, int k, int ldr, T* Zo, int ldo) {
+  const Precond& pc = h->pc;
+  double* t1 = wsT<double>(h, "ap_t1", (size_t)pc.s * k);
+  double* t2 = wsT<double>(h, "ap_t2", (size_t)pc.s * k);
+  double* part = wsT<double>(h, "ap_part", apply_part_elems(pc.n, pc.s, k));
+  launch_apply<T>(st, pc, R, k, ldr, Zo, ldo, t1, t2, part);
+}
+
+struct SolveArgs {
+  const float* X;
+  int n, d, ldx;
+  double sigma, lambda;
+  const double* Y;
+  int k, ldy;
+  double* C;
+  int ldc;
+  krr_opts o;
+};
+
+// Plain PCG in element type T with product precision `prec`; FP64 true
+// residual restarts when the recursive residual passes but the true one
+// does not (up to three times).
+template <typename T>
+krr_status solve_plain(krr_handle* h, const SolveArgs& a, int prec, krr_report* rep,
+                       int* matvecs) {
+  cudaStream_t st = h->stream;
+  const int n = a.n, k = a.k;
+  const size_t nk = (size_t)n * k;
+  T* x = wsT<T>(h, "v_x", nk);
+  T* r = wsT<T>(h, "v_r", nk);
+  T* p = wsT<T>(h, "v_p", nk);
+  T* z = wsT<T>(h, "v_z", nk);
+  T* q = wsT<T>(h, "v_q", nk);
+  double* Yc = wsT<double>(h, "v_y", nk);     // Y packed with ld = k
+  double* Rd = wsT<double>(h, "v_rd", nk);    // FP64 true residual
+  double* AX = wsT<double>(h, "v_ax", nk);
+  ColScale one;
+  for (int c = 0; c < KRR_MAX_RHS; ++c) one.v[c] = 1.0;
+  launch_convert<double, double>(st, a.Y, n, k, a.ldy, Yc, k, one);
+  // initial x and r
+  if (a.o.warm_start) {
+    double* C0 = wsT<double>(h, "v_c0", nk);
+    launch_convert<double, double>(st, a.C, n, k, a.ldc, C0, k, one);
+    matvec_dispatch(h, st, a.X, n, a.ldx, a.X, n, a.ldx, a.d, a.sigma, a.lambda, C0, k, k, AX, k,
+                    KRR_FP64);
+    ++*matvecs;
+    launch_sub_d(st, Yc, k, AX, k, n, k, Rd, k);
+    launch_convert<double, T>(st, C0, n, k, k, x, k, one);
+    launch_convert<double, T>(st, Rd, n, k, k, r, k, one);
+  } else {
+    KRR_CUDA(cudaMemsetAsync(x, 0, nk * sizeof(T), st));
+    launch_convert<double, T>(st, Yc, n, k, k, r, k, one);
+  }
+  auto mv = [&](cudaStream_t s2, const T* V, T* Q) {
+    matvec_dispatch(h, s2, a.X, n, a.ldx, a.X, n, a.ldx, a.d, a.sigma, a.lambda, V, k, k, Q, k,
+                    prec);
+  };
+  std::function<void(cudaStream_t, const T*, T*)> ap;
+  if (a.o.precond)
+    ap = [&](cudaStream_t s2, const T* R, T* Zo) { apply_precond<T>(h, s2, R, k, k, Zo, k); };
+  int restarts = 0;
+  int total_iters[KRR_MAX_RHS] = {0};
+  krr_status status = KRR_OK;
+  LoopOut lo;
+  int remaining = a.o.max_iter;
+  for (;;) {
+    pcg_loop<T>(h, n, k, Yc, k, x, r, p, z, q, a.o.tol, remaining, a.o.use_graph != 0, mv, ap,
+                &lo, matvecs, prec);
+    for (int c = 0; c < k; ++c) total_iters[c] += lo.iters[c];
+    remaining -= lo.iter;
+    if (lo.flags & FLAG_NAN) {
+      status = KRR_ENAN;
+      break;
+    }
+    if (lo.flags & FLAG_BREAKDOWN) {
+      status = KRR_EBREAKDOWN;
+      break;
+    }
+    // true residual in FP64
+    ColScale one2 = one;
+    double* xd = wsT<double>(h, "v_xd", nk);
+    launch_convert<T, double>(st, x, n, k, k, xd, k, one2);
+    matvec_dispatch(h, st, a.X, n, a.ldx, a.X, n, a.ldx, a.d, a.sigma, a.lambda, xd, k, k, AX, k,
+                    prec == KRR_FP64 ? KRR_FP64 : (prec == KRR_FP32 ? KRR_FP64 : KRR_HP));
+    ++*matvecs;
+    launch_sub_d(st, Yc, k, AX, k, n, k, Rd, k);
+    double rr[KRR_MAX_RHS];
+    host_colnorm2<double>(h, Rd, n, k, k, rr);
+    bool ok = true;
+    for (int c = 0; c < k; ++c) {
+      double rel = lo.yy[c] > 0 ? std::sqrt(rr[c] / lo.yy[c]) : 0.0;
+      if (rep) rep->rel_res[c] = rel;
+      if (rel > a.o.tol) ok = false;
+    }
+    if (ok) break;
+    if (lo.flags & FLAG_CAP || remaining <= 0) {
+      status = KRR_ENOTCONV;
+      break;
+    }
+    if (prec != KRR_FP64 || restarts >= 3) {
+      // single precision reached its floor: report, do not loop forever
+      status = KRR_ENOTCONV;
+      break;
+    }
+    ++restarts;
+    launch_convert<double, T>(st, Rd, n, k, k, r, k, one);
+  }
+  launch_convert<T, double>(st, x, n, k, k, a.C, a.ldc, one);
+  if (rep) {
+    for (int c = 0; c < k; ++c) rep->iters[c] = total_iters[c];
+    rep->outer_steps = restarts;
+  }
+  return status;
+}
+
+// Mixed precision: BF16 tensor-core inner PCG with FP32 vectors; outer
+// iterative refinement with the residual in HP arithmetic and FP64 vectors.
+krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* matvecs) {
+  cudaStream_t st = h->stream;
+  const int n = a.n, k = a.k;
+  const size_t nk = (size_t)n * k;
+  double* Yc = wsT<double>(h, "v_y", nk);
+  double* Cd = wsT<double>(h, "v_cd", nk);
+  double* Rd = wsT<double>(h, "v_rd", nk);
+  double* AX = wsT<double>(h, "v_ax", nk);
+  double* Rs = wsT<double>(h, "v_rs", nk);  // scaled residual (inner tolerance reference)
+  float* x = wsT<float>(h, "v_xf", nk);
+  float* r = wsT<float>(h, "v_rf", nk);
+  float* p = wsT<float>(h, "v_pf", nk);
+  float* z = wsT<float>(h, "v_zf", nk);
+  float* q = wsT<float>(h, "v_qf", nk);
+  ColScale one;
+  for (int c = 0; c < KRR_MAX_RHS; ++c) one.v[c] = 1.0;
+  launch_convert<double, double>(st, a.Y, n, k, a.ldy, Yc, k, one);
+  if (a.o.warm_start) {
+    launch_convert<double, double>(st, a.C, n, k, a.ldc, Cd, k, one);
+    matvec_dispatch(h, st, a.X, n, a.ldx, a.X, n, a.ldx, a.d, a.sigma, a.lambda, Cd, k, k, AX, k,
+                    KRR_HP);
+    ++*matvecs;
+    launch_sub_d(st, Yc, k, AX, k, n, k, Rd, k);
+  } else {
+    KRR_CUDA(cudaMemsetAsync(Cd, 0, nk * sizeof(double), st));
+    KRR_CUDA(cudaMemcpyAsync(Rd, Yc, nk * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  double yy[KRR_MAX_RHS];
+  host_colnorm2<double>(h, Yc, n, k, k, yy);
+  auto mv = [&](cudaStream_t s2, const float* V, float* Q) {
+    matvec_dispatch(h, s2, a.X, n, a.ldx, a.X, n, a.ldx, a.d, a.sigma, a.lambda, V, k, k, Q, k,
+                    KRR_BF16);
+  };
+  std::function<void(cudaStream_t, const float*, float*)> ap;
+  if (a.o.precond)
+    ap = [&](cudaStream_t s2, const float* R, float* Zo) {
+      apply_precond<float>(h, s2, R, k, k, Zo, k);
+    };
+  int total_iters[KRR_MAX_RHS] = {0};
+  krr_status status = KRR_OK;
+  int outer = 0;
+  int remaining = a.o.max_iter;
+  for (;;) {
+    double rr[KRR_MAX_RHS];
+    host_colnorm2<double>(h, Rd, n, k, k, rr);
+    bool ok = true;
+    ColScale sc, inv;
+    for (int c = 0; c < KRR_MAX_RHS; ++c) sc.v[c] = inv.v[c] = 0.0;
+    for (int c = 0; c < k; ++c) {
+      double rel = yy[c] > 0 ? std::sqrt(rr[c] / yy[c]) : 0.0;
+      if (rep) rep->rel_res[c] = rel;
+      if (!std::isfinite(rel)) {
+        status = KRR_ENAN;
+      } else if (rel > a.o.tol) {
+        ok = false;
+        sc.v[c] = 1.0 / std::sqrt(rr[c]);
+        inv.v[c] = std::sqrt(rr[c]);
+      }
+    }
+    if (status != KRR_OK || ok) break;
+    if (outer >= a.o.max_outer || remaining <= 0) {
+      status = KRR_ENOTCONV;
+      break;
+    }
+    ++outer;
+    launch_convert<double, double>(st, Rd, n, k, k, Rs, k, sc);
+    launch_convert<double, float>(st, Rs, n, k, k, r, k, one);
+    KRR_CUDA(cudaMemsetAsync(x, 0, nk * sizeof(float), st));
+    LoopOut lo;
+    pcg_loop<float>(h, n, k, Rs, k, x, r, p, z, q, a.o.inner_tol, remaining, a.o.use_graph != 0,
+                    mv, ap, &lo, matvecs, KRR_BF16);
+    for (int c = 0; c < k; ++c) total_iters[c] += lo.iters[c];
+    remaining -= lo.iter;
+    if (lo.flags & FLAG_NAN) {
+      status = KRR_ENAN;
+      break;
+    }
+    // breakdown of the inner solve still leaves a usable correction
+    launch_axpy_d<float>(st, x, n, k, k, Cd, k, inv);
+    matvec_dispatch(h, st, a.X, n, a.ldx, a.X, n, a.ldx, a.d, a.sigma, a.lambda, Cd, k, k, AX, k,
+                    KRR_HP);
+    ++*matvecs;
+    launch_sub_d(st, Yc, k, AX, k, n, k, Rd, k);
+  }
+  launch_convert<double, double>(st, Cd, n, k, k, a.C, a.ldc, one);
+  if (rep) {
+    for (int c = 0; c < k; ++c) rep->iters[c] = total_iters[c];
+    rep->outer_steps = outer;
+  }
+  return status;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+void krr_default_opts(krr_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->tol = 1e-6;
+  o->max_iter = 1000;
+  o->lambda_p = 0.0;
+  o->precond = 1;
+  o->precision = KRR_FP64;
+  o->apply_form = KRR_APPLY_ZL;
+  o->use_graph = 1;
+  o->inner_tol = 1e-2;
+  o->max_outer = 30;
+  o->z_bf16 = -1;
+  o->warm_start = 0;
+}
+
+const char* krr_status_string(krr_status s) {
+  switch (s) {
+    case KRR_OK: return "ok";
+    case KRR_EINVAL: return "invalid argument";
+    case KRR_ENOMEM: return "out of device memory";
+    case KRR_ECUDA: return "CUDA error";
+    case KRR_ECHOL: return "preconditioner Gram matrix not positive definite";
+    case KRR_ENOTCONV: return "not converged";
+    case KRR_EBREAKDOWN: return "CG breakdown";
+    case KRR_ENAN: return "NaN or Inf";
+    case KRR_ETIMEOUT: return "device loop iteration cap";
+    case KRR_EUNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+krr_status krr_create(krr_handle** out, void* stream) {
+  if (!out) return KRR_EINVAL;
+  *out = nullptr;
+  krr_handle* h = new (std::nothrow) krr_handle();
+  if (!h) return KRR_ENOMEM;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&h->sc, sizeof(CgScalars));
+  if (e == cudaSuccess) e = cudaMemset(h->sc, 0, sizeof(CgScalars));
+  if (e == cudaSuccess) e = cudaMallocHost(&h->sc_host, sizeof(CgScalars));
+  if (e == cudaSuccess) e = cudaMallocHost(&h->hostd, KRR_MAX_RHS * 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&h->info, sizeof(int));
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->ev[i]);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    krr_destroy(h);
+    return e == cudaErrorMemoryAllocation ? KRR_ENOMEM : KRR_ECUDA;
+  }
+  h->stream = (cudaStream_t)stream;
+  *out = h;
+  return KRR_OK;
+}
+
+krr_status krr_destroy(krr_handle* h) {
+  if (!h) return KRR_EINVAL;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& kv : h->bufs) free_buf(kv.second);
+  free_buf(h->pc.Z);
+  free_buf(h->pc.L);
+  free_buf(h->pc.Linv);
+  free_buf(h->pc.LinvT);
+  free_buf(h->pc.U);
+  tc_release(h->tc);
+  if (h->sc) cudaFree(h->sc);
+  if (h->sc_host) cudaFreeHost(h->sc_host);
+  if (h->hostd) cudaFreeHost(h->hostd);
+  if (h->info) cudaFree(h->info);
+  for (auto ev : h->ev)
+    if (ev) cudaEventDestroy(ev);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  cudaSetDevice(cur);
+  delete h;
+  return KRR_OK;
+}
+
+krr_status krr_set_stream(krr_handle* h, void* stream) {
+  if (!h) return KRR_EINVAL;
+  h->stream = (cudaStream_t)stream;
+  return KRR_OK;
+}
+
+const char* krr_last_error(const krr_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+krr_status krr_rff_features(krr_handle* h, const float* X, int n, int d, int ldx, const float* W,
+                            const float* b, int s, float* Z, int ldz) {
+  return guard(h, [&]() -> krr_status {
+    KRR_REQUIRE(X && W && b && Z, "rff_features: null pointer");
+    KRR_REQUIRE(n > 0 && d > 0 && s > 0, "rff_features: sizes must be positive");
+    KRR_REQUIRE(ldx >= d && ldz >= s, "rff_features: leading dimension too small");
+    launch_rff(h->stream, X, n, d, ldx, W, b, s, Z, ldz);
+    return KRR_OK;
+  });
+}
+
+krr_status krr_kernel_matvec(krr_handle* h, const float* Xr, int nr, int ldxr, const float* Xc,
+                             int nc, int ldxc, int d, double sigma, double shift, const void* V,
+                             int k, int ldv, void* Q, int ldq, int precision) {
+  return guard(h, [&]() -> krr_status {
+    KRR_REQUIRE(Xr && Xc && V && Q, "kernel_matvec: null pointer");
+    KRR_REQUIRE(nr > 0 && nc > 0 && d > 0, "kernel_matvec: sizes must be positive");
+    KRR_REQUIRE(k >= 1 && k <= KRR_MAX_RHS, "kernel_matvec: need 1 <= k <= KRR_MAX_RHS");
+    KRR_REQUIRE(ldxr >= d && ldxc >= d && ldv >= k && ldq >= k,
+                "kernel_matvec: leading dimension too small");
+    KRR_REQUIRE(sigma > 0.0 && std::isfinite(sigma), "kernel_matvec: sigma must be > 0");
+    KRR_REQUIRE(shift == 0.0 || nr == nc, "kernel_matvec: shift needs a square product");
+    KRR_REQUIRE(precision >= KRR_FP64 && precision <= KRR_HP, "kernel_matvec: bad precision");
+    matvec_dispatch(h, h->stream, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, shift, V, k, ldv, Q, ldq,
+                    precision);
+    if (precision == KRR_BF16 && tc_error(h->tc, h->stream))
+      throw Error{KRR_ETIMEOUT, "tensor-core product: a pipeline wait hit its limit"};
+    return KRR_OK;
+  });
+}
+
+krr_status krr_precond_setup(krr_handle* h, const float* Z, int n, int s, int ldz,
+                             double lambda_p, int apply_form, int z_bf16) {
+  return guard(h, [&]() -> krr_status {
+    precond_setup_impl(h, Z, n, s, ldz, lambda_p, apply_form, z_bf16 ? 1 : 0);
+    return KRR_OK;
+  });
+}
+
+krr_status krr_precond_apply(krr_handle* h, const double* R, int k, int ldr, double* Zout,
+                             int ldo) {
+  return guard(h, [&]() -> krr_status {
+    KRR_REQUIRE(h->pc.ready, "precond_apply: call krr_precond_setup first");
+    KRR_REQUIRE(R && Zout, "precond_apply: null pointer");
+    KRR_REQUIRE(k >= 1 && k <= KRR_MAX_RHS && ldr >= k && ldo >= k, "precond_apply: bad k / ld");
+    apply_precond<double>(h, h->stream, R, k, ldr, Zout, ldo);
+    return KRR_OK;
+  });
+}
+
+krr_status krr_pcg_solve(krr_handle* h, const float* X, int n, int d, int ldx, double sigma,
+                         double lambda, const float* W, const float* b, int s, const double* Y,
+                         int k, int ldy, double* C, int ldc, const krr_opts* opts,
+                         krr_report* rep) {
+  return guard(h, [&]() -> krr_status {
+    krr_opts o;
+    if (opts)
+      o = *opts;
+    else
+      krr_default_opts(&o);
+    KRR_REQUIRE(X && Y && C, "pcg_solve: null pointer");
+    KRR_REQUIRE(n > 0 && d > 0 && k >= 1 && k <= KRR_MAX_RHS, "pcg_solve: bad sizes");
+    KRR_REQUIRE(ldx >= d && ldy >= k && ldc >= k, "pcg_solve: leading dimension too small");
+    KRR_REQUIRE(sigma > 0.0 && std::isfinite(sigma), "pcg_solve: sigma must be > 0");
+    KRR_REQUIRE(lambda > 0.0 && std::isfinite(lambda), "pcg_solve: lambda must be > 0");
+    KRR_REQUIRE(o.tol > 0.0 && o.max_iter >= 0, "pcg_solve: bad tol / max_iter");
+    KRR_REQUIRE(o.precision == KRR_FP64 || o.precision == KRR_FP32 || o.precision == KRR_MIXED,
+                "pcg_solve: precision must be KRR_FP64, KRR_FP32 or KRR_MIXED");
+    if (o.precond) {
+      KRR_REQUIRE(W && b && s > 0 && s <= n, "pcg_solve: preconditioner needs W, b and 0 < s <= n");
+    }
+    if (o.precision == KRR_MIXED) {
+      KRR_REQUIRE(o.inner_tol > 0.0 && o.inner_tol < 1.0, "pcg_solve: inner_tol in (0, 1)");
+    }
+    if (rep) {
+      memset(rep, 0, sizeof(*rep));
+      rep->k = k;
+    }
+    cudaStream_t st = h->stream;
+    KRR_CUDA(cudaEventRecord(h->ev[0], st));
+    // stage host inputs
+    const bool c_host = !on_device(C);
+    const float* Xd = (const float*)stage_in(h, X, (size_t)n * ldx * sizeof(float), "X");
+    const double* Yd = (const double*)stage_in(h, Y, (size_t)n * ldy * sizeof(double), "Y");
+    double* Cd = C;
+    if (c_host) {
+      Cd = wsT<double>(h, "stage_C", (size_t)n * ldc);
+      if (o.warm_start)
+        KRR_CUDA(cudaMemcpyAsync(Cd, C, (size_t)n * ldc * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
+    int matvecs = 0;
+    KRR_TRACE("pcg_solve: n=%d d=%d k=%d s=%d prec=%d graph=%d", n, d, k, s, o.precision, o.use_graph);
+    if (o.precond) {
+      const float* Wd = (const float*)stage_in(h, W, (size_t)d * s * sizeof(float), "W");
+      const float* bd = (const float*)stage_in(h, b, (size_t)s * sizeof(float), "b");
+      float* Z = wsT<float>(h, "rff_Z", (size_t)n * s);
+      launch_rff(st, Xd, n, d, ldx, Wd, bd, s, Z, s);
+      int zb = o.z_bf16 < 0 ? (o.precision == KRR_MIXED ? 1 : 0) : (o.z_bf16 ? 1 : 0);
+      double lp = o.lambda_p > 0.0 ? o.lambda_p : lambda;
+      precond_setup_impl(h, Z, n, s, s, lp, o.apply_form, zb);
+    }
+    if (o.precision == KRR_MIXED) {
+      tc_prepare(h->tc, st, Xd, n, ldx, d, sigma);
+      tc_clear_error(h->tc, st);
+    }
+    KRR_CUDA(cudaEventRecord(h->ev[1], st));
+    KRR_TRACE("pcg_solve: setup done");
+    SolveArgs a{Xd, n, d, ldx, sigma, lambda, Yd, k, ldy, Cd, ldc, o};
+    krr_status status;
+    if (o.precision == KRR_FP64)
+      status = solve_plain<double>(h, a, KRR_FP64, rep, &matvecs);
+    else if (o.precision == KRR_FP32)
+      status = solve_plain<float>(h, a, KRR_FP32, rep, &matvecs);
+    else
+      status = solve_mixed(h, a, rep, &matvecs);
+    if (o.precision == KRR_MIXED && tc_error(h->tc, st)) status = KRR_ETIMEOUT;
+    if (c_host)
+      KRR_CUDA(cudaMemcpyAsync(C, Cd, (size_t)n * ldc * sizeof(double), cudaMemcpyDeviceToHost, st));
+    KRR_CUDA(cudaEventRecord(h->ev[2], st));
+    KRR_CUDA(cudaEventSynchronize(h->ev[2]));
+    if (rep) {
+      rep->status = status;
+      rep->matvecs = matvecs;
+      rep->ms_setup = ms_between(h->ev[0], h->ev[1]);
+      rep->ms_solve = ms_between(h->ev[1], h->ev[2]);
+      rep->ms_total = ms_between(h->ev[0], h->ev[2]);
+    }
+    if (status != KRR_OK) h->err = krr_status_string(status);
+    return status;
+  });
+}
+
+krr_status krr_predict(krr_handle* h, const float* Xtr, int n, int ldxtr, const float* Xte, int m,
+                       int ldxte, int d, double sigma, const double* C, int k, int ldc, double* F,
+                       int ldf, int precision) {
+  return guard(h, [&]() -> krr_status {
+    KRR_REQUIRE(Xtr && Xte && C && F, "predict: null pointer");
+    KRR_REQUIRE(n > 0 && m > 0 && d > 0 && k >= 1 && k <= KRR_MAX_RHS, "predict: bad sizes");
+    KRR_REQUIRE(ldxtr >= d && ldxte >= d && ldc >= k && ldf >= k, "predict: bad leading dims");
+    KRR_REQUIRE(sigma > 0.0 && std::isfinite(sigma), "predict: sigma must be > 0");
+    if (precision == KRR_FP32) {
+      ColScale one;
+      for (int c = 0; c < KRR_MAX_RHS; ++c) one.v[c] = 1.0;
+      float* Cf = wsT<float>(h, "pr_cf", (size_t)n * k);
+      float* Ff = wsT<float>(h, "pr_ff", (size_t)m * k);
+      launch_convert<double, float>(h->stream, C, n, k, ldc, Cf, k, one);
+      matvec_dispatch(h, h->stream, Xte, m, ldxte, Xtr, n, ldxtr, d, sigma, 0.0, Cf, k, k, Ff, k,
+                      KRR_FP32);
+      launch_convert<float, double>(h->stream, Ff, m, k, k, F, ldf, one);
+      return KRR_OK;
+    }
+    KRR_REQUIRE(precision == KRR_FP64 || precision == KRR_HP, "predict: bad precision");
+    matvec_dispatch(h, h->stream, Xte, m, ldxte, Xtr, n, ldxtr, d, sigma, 0.0, C, k, ldc, F, ldf,
+                    precision);
+    return KRR_OK;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,451 @@
+// Conjugate-gradient vector kernels (Algorithm 1 line 9: PCG on
+// (K + lambda I) c = y with the random-feature preconditioner).
+//
+// Each column of the n x k block iterates independently (Section 5 asks the
+// stopping test to hold for every right-hand side): per column the scalars
+// alpha = r.z / p.q and beta = r'.z' / r.z, the recursive ||r||^2 and the
+// active flag live in a CgScalars block in device memory, so the loop never
+// reads anything back to the host.  Every reduction is a grid-wide column
+// sum: warp shuffles, one partial per CTA, and the last CTA to finish
+// (atomic counter) adds the partials in CTA order, which keeps the result
+// deterministic, and then updates the scalars.
+#include "krr_internal.cuh"
+
+namespace krr {
+namespace {
+
+constexpr int CT = 256;           // threads per CTA
+constexpr int NW = CT / 32;
+
+enum CounterSlot { C_INIT = 0, C_RZ = 1, C_ALPHA = 2, C_XR = 3, C_NORM = 4 };
+
+int cg_blocks(int n) {
+  int b = (n + CT - 1) / CT;
+  int cap = 2 * sm_count();
+  return b < 1 ? 1 : (b > cap ? cap : b);
+}
+
+// Sum v[c] over the grid.  Returns true in thread 0 of the last CTA to
+// finish, with tot[c] the column totals added in CTA order.
+__device__ bool grid_colsum(double (&v)[KRR_MAX_RHS], int k, double* part,
+                            unsigned int* counter, double (&tot)[KRR_MAX_RHS]) {
+  __shared__ double red[NW][KRR_MAX_RHS];
+  __shared__ int last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c) {
+    if (c >= k) break;
+    double x = v[c];
+    for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if (lane == 0) red[w][c] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double s = 0.0;
+    for (int q = 0; q < NW; ++q) s += red[q][threadIdx.x];
+    part[blockIdx.x * KRR_MAX_RHS + threadIdx.x] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  if (threadIdx.x < k) {
+    double s = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&part[b * KRR_MAX_RHS + threadIdx.x]);
+    red[0][threadIdx.x] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return false;
+  for (int c = 0; c < k; ++c) tot[c] = red[0][c];
+  *counter = 0u;
+  return true;
+}
+
+__device__ __forceinline__ bool bad(double x) { return isnan(x) || isinf(x); }
+
+template <typename T>
+__global__ void __launch_bounds__(CT)
+cg_init_kernel(CgScalars* sc, const double* __restrict__ Y, int ldy, const T* __restrict__ R,
+               int n, int k, double tol, int max_iter, double* part) {
+  double v[KRR_MAX_RHS], tot[KRR_MAX_RHS];
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c) v[c] = 0.0;
+  for (int i = blockIdx.x * CT + threadIdx.x; i < n; i += gridDim.x * CT) {
+#pragma unroll
+    for (int c = 0; c < KRR_MAX_RHS; ++c)
+      if (c < k) {
+        double y = Y[(size_t)i * ldy + c];
+        v[c] = fma(y, y, v[c]);
+      }
+  }
+  if (!grid_colsum(v, k, part, &sc->counter[C_INIT], tot)) return;
+  // second pass for ||r0||^2 runs in cg_rz_first; here rr = ||y||^2 as a start
+  sc->k = k;
+  sc->iter = 0;
+  sc->max_iter = max_iter;
+  sc->flags = 0;
+  for (int c = 0; c < KRR_MAX_RHS; ++c) {
+    if (c < k) {
+      sc->yy[c] = tot[c];
+      sc->tol2[c] = tol * tol * tot[c];
+      sc->rr[c] = tot[c];
+      sc->active[c] = tot[c] > 0.0 ? 1 : 0;
+      if (bad(tot[c])) sc->flags |= FLAG_NAN;
+    } else {
+      sc->yy[c] = 0.0;
+      sc->tol2[c] = 0.0;
+      sc->rr[c] = 0.0;
+      sc->active[c] = 0;
+    }
+    sc->iters[c] = 0;
+    sc->alpha[c] = sc->beta[c] = sc->rz[c] = sc->pq[c] = 0.0;
+  }
+}
+
+// rz = r.z, rr = r.r and p = z for the first iteration.
+template <typename T>
+__global__ void __launch_bounds__(CT)
+cg_rz_first_kernel(CgScalars* sc, const T* __restrict__ R, const T* __restrict__ Z,
+                   T* __restrict__ P, int n, int k, double* part) {
+  double v[KRR_MAX_RHS], tot[KRR_MAX_RHS];
+  double w[KRR_MAX_RHS], tot2[KRR_MAX_RHS];
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c) v[c] = w[c] = 0.0;
+  for (int i = blockIdx.x * CT + threadIdx.x; i < n; i += gridDim.x * CT) {
+#pragma unroll
+    for (int c = 0; c < KRR_MAX_RHS; ++c)
+      if (c < k) {
+        size_t e = (size_t)i * k + c;
+        double r = (double)R[e], z = (double)Z[e];
+        v[c] = fma(r, z, v[c]);
+        w[c] = fma(r, r, w[c]);
+        P[e] = Z[e];
+      }
+  }
+  // two column sums packed into one: first k entries r.z, next k entries r.r
+  double vv[KRR_MAX_RHS];
+  const int k2 = 2 * k <= KRR_MAX_RHS ? 2 * k : 0;
+  if (k2) {
+#pragma unroll
+    for (int c = 0; c < KRR_MAX_RHS; ++c) vv[c] = c < k ? v[c] : (c < k2 ? w[c - k] : 0.0);
+    if (!grid_colsum(vv, k2, part, &sc->counter[C_RZ], tot)) return;
+    for (int c = 0; c < k; ++c) tot2[c] = tot[k + c];
+  } else {
+    // k > KRR_MAX_RHS / 2: use r.z only; rr keeps its ||y||^2 start value
+    if (!grid_colsum(v, k, part, &sc->counter[C_RZ], tot)) return;
+    for (int c = 0; c < k; ++c) tot2[c] = sc->rr[c];
+  }
+  for (int c = 0; c < k; ++c) {
+    sc->rz[c] = tot[c];
+    sc->rr[c] = tot2[c];
+    if (bad(tot[c])) sc->flags |= FLAG_NAN;
+    if (sc->active[c]) {
+      if (tot2[c] <= sc->tol2[c]) {
+        sc->active[c] = 0;  // x0 already meets the tolerance
+      } else if (!(tot[c] > 0.0)) {
+        sc->flags |= FLAG_BREAKDOWN;
+        sc->active[c] = 0;
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CT)
+cg_alpha_kernel(CgScalars* sc, const T* __restrict__ P, const T* __restrict__ Q, int n, int k,
+                double* part) {
+  double v[KRR_MAX_RHS], tot[KRR_MAX_RHS];
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c) v[c] = 0.0;
+  for (int i = blockIdx.x * CT + threadIdx.x; i < n; i += gridDim.x * CT) {
+#pragma unroll
+    for (int c = 0; c < KRR_MAX_RHS; ++c)
+      if (c < k) {
+        size_t e = (size_t)i * k + c;
+        v[c] = fma((double)P[e], (double)Q[e], v[c]);
+      }
+  }
+  if (!grid_colsum(v, k, part, &sc->counter[C_ALPHA], tot)) return;
+  for (int c = 0; c < k; ++c) {
+    sc->pq[c] = tot[c];
+    double a = 0.0;
+    if (sc->active[c]) {
+      if (bad(tot[c])) {
+        sc->flags |= FLAG_NAN;
+      } else if (!(tot[c] > 0.0)) {
+        sc->flags |= FLAG_BREAKDOWN;
+      } else {
+        a = sc->rz[c] / tot[c];
+      }
+    }
+    sc->alpha[c] = a;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CT)
+cg_update_xr_kernel(CgScalars* sc, T* __restrict__ X, T* __restrict__ R, const T* __restrict__ P,
+                    const T* __restrict__ Q, int n, int k, double* part) {
+  double a[KRR_MAX_RHS], v[KRR_MAX_RHS], tot[KRR_MAX_RHS];
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c) {
+    a[c] = c < k ? sc->alpha[c] : 0.0;
+    v[c] = 0.0;
+  }
+  for (int i = blockIdx.x * CT + threadIdx.x; i < n; i += gridDim.x * CT) {
+#pragma unroll
+    for (int c = 0; c < KRR_MAX_RHS; ++c)
+      if (c < k) {
+        size_t e = (size_t)i * k + c;
+        double r = (double)R[e];
+        if (a[c] != 0.0) {
+          X[e] = (T)((double)X[e] + a[c] * (double)P[e]);
+          r = r - a[c] * (double)Q[e];
+          R[e] = (T)r;
+          r = (double)R[e];
+        }
+        v[c] = fma(r, r, v[c]);
+      }
+  }
+  if (!grid_colsum(v, k, part, &sc->counter[C_XR], tot)) return;
+  for (int c = 0; c < k; ++c) {
+    sc->rr[c] = tot[c];
+    if (bad(tot[c])) sc->flags |= FLAG_NAN;
+    if (sc->active[c]) {
+      sc->iters[c] += 1;
+      if (tot[c] <= sc->tol2[c]) sc->active[c] = 0;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CT)
+cg_rz_kernel(CgScalars* sc, const T* __restrict__ R, const T* __restrict__ Z, int n, int k,
+             double* part) {
+  double v[KRR_MAX_RHS], tot[KRR_MAX_RHS];
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c) v[c] = 0.0;
+  for (int i = blockIdx.x * CT + threadIdx.x; i < n; i += gridDim.x * CT) {
+#pragma unroll
+    for (int c = 0; c < KRR_MAX_RHS; ++c)
+      if (c < k) {
+        size_t e = (size_t)i * k + c;
+        v[c] = fma((double)R[e], (double)Z[e], v[c]);
+      }
+  }
+  if (!grid_colsum(v, k, part, &sc->counter[C_RZ], tot)) return;
+  for (int c = 0; c < k; ++c) {
+    double b = 0.0;
+    if (sc->active[c]) {
+      if (bad(tot[c])) {
+        sc->flags |= FLAG_NAN;
+      } else if (!(tot[c] > 0.0)) {
+        sc->flags |= FLAG_BREAKDOWN;
+      } else {
+        b = tot[c] / sc->rz[c];
+      }
+      sc->rz[c] = tot[c];
+    }
+    sc->beta[c] = b;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CT)
+cg_update_p_kernel(const CgScalars* sc, T* __restrict__ P, const T* __restrict__ Z, int n, int k) {
+  double b[KRR_MAX_RHS];
+  int act[KRR_MAX_RHS];
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c) {
+    b[c] = c < k ? sc->beta[c] : 0.0;
+    act[c] = c < k ? sc->active[c] : 0;
+  }
+  for (int i = blockIdx.x * CT + threadIdx.x; i < n; i += gridDim.x * CT) {
+#pragma unroll
+    for (int c = 0; c < KRR_MAX_RHS; ++c)
+      if (c < k && act[c]) {
+        size_t e = (size_t)i * k + c;
+        P[e] = (T)((double)Z[e] + b[c] * (double)P[e]);
+      }
+  }
+}
+
+__global__ void cg_tail_kernel(CgScalars* sc, cudaGraphConditionalHandle cond) {
+  int any = 0;
+  for (int c = 0; c < sc->k; ++c) any |= sc->active[c];
+  sc->iter += 1;
+  bool stop = !any || (sc->flags & (FLAG_BREAKDOWN | FLAG_NAN));
+  if (!stop && sc->iter >= sc->max_iter) {
+    sc->flags |= FLAG_CAP;
+    stop = true;
+  }
+  if (cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
+}
+
+// ------------------------------------------------------------ elementwise --
+template <typename A, typename B>
+__global__ void convert_kernel(const A* __restrict__ a, int n, int k, int lda, B* __restrict__ b,
+                               int ldb, ColScale sc) {
+  const size_t total = (size_t)n * k;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / k), c = (int)(e % k);
+    b[(size_t)i * ldb + c] = (B)((double)a[(size_t)i * lda + c] * sc.v[c]);
+  }
+}
+
+template <typename D>
+__global__ void axpy_d_kernel(const D* __restrict__ dl, int n, int k, int ldd, double* __restrict__ c,
+                              int ldc, ColScale sc) {
+  const size_t total = (size_t)n * k;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / k), q = (int)(e % k);
+    c[(size_t)i * ldc + q] += sc.v[q] * (double)dl[(size_t)i * ldd + q];
+  }
+}
+
+__global__ void sub_d_kernel(const double* __restrict__ y, int ldy, const double* __restrict__ a,
+                             int lda, int n, int k, double* __restrict__ r, int ldr) {
+  const size_t total = (size_t)n * k;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    int i = (int)(e / k), c = (int)(e % k);
+    r[(size_t)i * ldr + c] = y[(size_t)i * ldy + c] - a[(size_t)i * lda + c];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CT)
+colnorm2_kernel(const T* __restrict__ a, int n, int k, int lda, double* out, double* part,
+                unsigned int* counter) {
+  double v[KRR_MAX_RHS], tot[KRR_MAX_RHS];
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c) v[c] = 0.0;
+  for (int i = blockIdx.x * CT + threadIdx.x; i < n; i += gridDim.x * CT) {
+#pragma unroll
+    for (int c = 0; c < KRR_MAX_RHS; ++c)
+      if (c < k) {
+        double x = (double)a[(size_t)i * lda + c];
+        v[c] = fma(x, x, v[c]);
+      }
+  }
+  if (!grid_colsum(v, k, part, counter, tot)) return;
+  for (int c = 0; c < k; ++c) out[c] = tot[c];
+}
+
+int ew_blocks(size_t total) {
+  size_t b = (total + 255) / 256;
+  size_t cap = (size_t)8 * sm_count();
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+}  // namespace
+
+size_t cg_part_elems(int n, int k) {
+  (void)k;
+  return (size_t)cg_blocks(n) * KRR_MAX_RHS;
+}
+
+template <typename T>
+void launch_cg_init(cudaStream_t st, CgScalars* sc, const double* Y, int ldy, const T* R, int n,
+                    int k, double tol, int max_iter, double* part) {
+  (void)R;
+  cg_init_kernel<T><<<cg_blocks(n), CT, 0, st>>>(sc, Y, ldy, R, n, k, tol, max_iter, part);
+  KRR_CHECK_LAUNCH();
+}
+
+template <typename T>
+void launch_cg_rz_first(cudaStream_t st, CgScalars* sc, const T* R, const T* Z, T* P, int n,
+                        int k, double* part) {
+  cg_rz_first_kernel<T><<<cg_blocks(n), CT, 0, st>>>(sc, R, Z, P, n, k, part);
+  KRR_CHECK_LAUNCH();
+}
+
+template <typename T>
+void launch_cg_alpha(cudaStream_t st, CgScalars* sc, const T* P, const T* Q, int n, int k,
+                     double* part) {
+  cg_alpha_kernel<T><<<cg_blocks(n), CT, 0, st>>>(sc, P, Q, n, k, part);
+  KRR_CHECK_LAUNCH();
+}
+
+template <typename T>
+void launch_cg_update_xr(cudaStream_t st, CgScalars* sc, T* X, T* R, const T* P, const T* Q,
+                         int n, int k, double* part) {
+  cg_update_xr_kernel<T><<<cg_blocks(n), CT, 0, st>>>(sc, X, R, P, Q, n, k, part);
+  KRR_CHECK_LAUNCH();
+}
+
+template <typename T>
+void launch_cg_rz(cudaStream_t st, CgScalars* sc, const T* R, const T* Z, int n, int k,
+                  double* part) {
+  cg_rz_kernel<T><<<cg_blocks(n), CT, 0, st>>>(sc, R, Z, n, k, part);
+  KRR_CHECK_LAUNCH();
+}
+
+template <typename T>
+void launch_cg_update_p(cudaStream_t st, CgScalars* sc, T* P, const T* Z, int n, int k) {
+  cg_update_p_kernel<T><<<ew_blocks((size_t)n), CT, 0, st>>>(sc, P, Z, n, k);
+  KRR_CHECK_LAUNCH();
+}
+
+void launch_cg_tail(cudaStream_t st, CgScalars* sc, unsigned long long cond) {
+  cg_tail_kernel<<<1, 1, 0, st>>>(sc, (cudaGraphConditionalHandle)cond);
+  KRR_CHECK_LAUNCH();
+}
+
+template <typename A, typename B>
+void launch_convert(cudaStream_t st, const A* a, int n, int k, int lda, B* b, int ldb,
+                    const ColScale& scale) {
+  convert_kernel<A, B><<<ew_blocks((size_t)n * k), 256, 0, st>>>(a, n, k, lda, b, ldb, scale);
+  KRR_CHECK_LAUNCH();
+}
+
+template <typename D>
+void launch_axpy_d(cudaStream_t st, const D* dl, int n, int k, int ldd, double* c, int ldc,
+                   const ColScale& scale) {
+  axpy_d_kernel<D><<<ew_blocks((size_t)n * k), 256, 0, st>>>(dl, n, k, ldd, c, ldc, scale);
+  KRR_CHECK_LAUNCH();
+}
+
+void launch_sub_d(cudaStream_t st, const double* y, int ldy, const double* a, int lda, int n,
+                  int k, double* r, int ldr) {
+  sub_d_kernel<<<ew_blocks((size_t)n * k), 256, 0, st>>>(y, ldy, a, lda, n, k, r, ldr);
+  KRR_CHECK_LAUNCH();
+}
+
+template <typename T>
+void launch_colnorm2(cudaStream_t st, const T* a, int n, int k, int lda, double* out,
+                     double* part, unsigned int* counter) {
+  colnorm2_kernel<T><<<cg_blocks(n), CT, 0, st>>>(a, n, k, lda, out, part, counter);
+  KRR_CHECK_LAUNCH();
+}
+
+#define KRR_CG_INST(T)                                                                        \
+  template void launch_cg_init<T>(cudaStream_t, CgScalars*, const double*, int, const T*, int, \
+                                  int, double, int, double*);                                 \
+  template void launch_cg_rz_first<T>(cudaStream_t, CgScalars*, const T*, const T*, T*, int,  \
+                                      int, double*);                                          \
+  template void launch_cg_alpha<T>(cudaStream_t, CgScalars*, const T*, const T*, int, int,     \
+                                   double*);                                                  \
+  template void launch_cg_update_xr<T>(cudaStream_t, CgScalars*, T*, T*, const T*, const T*,   \
+                                       int, int, double*);                                    \
+  template void launch_cg_rz<T>(cudaStream_t, CgScalars*, const T*, const T*, int, int,        \
+                                double*);                                                     \
+  template void launch_cg_update_p<T>(cudaStream_t, CgScalars*, T*, const T*, int, int);       \
+  template void launch_colnorm2<T>(cudaStream_t, const T*, int, int, int, double*, double*,    \
+                                   unsigned int*);                                            \
+  template void launch_axpy_d<T>(cudaStream_t, const T*, int, int, int, double*, int,          \
+                                 const ColScale&);
+KRR_CG_INST(float)
+KRR_CG_INST(double)
+template void launch_convert<double, float>(cudaStream_t, const double*, int, int, int, float*,
+                                            int, const ColScale&);
+template void launch_convert<float, double>(cudaStream_t, const float*, int, int, int, double*,
+                                            int, const ColScale&);
+template void launch_convert<double, double>(cudaStream_t, const double*, int, int, int,
+                                             double*, int, const ColScale&);
+
+}  // namespace krr

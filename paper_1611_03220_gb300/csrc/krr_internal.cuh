@@ -1,0 +1,161 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/krr.h"
+
+namespace krr {
+
+// ---------------------------------------------------------------- errors --
+struct Error {
+  krr_status st;
+  std::string msg;
+};
+
+#define KRR_CUDA(call)                                                          \
+  do {                                                                          \
+    cudaError_t e_ = (call);                                                    \
+    if (e_ != cudaSuccess)                                                      \
+      throw ::krr::Error{KRR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+#define KRR_CHECK_LAUNCH() KRR_CUDA(cudaGetLastError())
+
+#define KRR_REQUIRE(cond, msg)                                                  \
+  do {                                                                          \
+    if (!(cond)) throw ::krr::Error{KRR_EINVAL, std::string(msg)};             \
+  } while (0)
+
+// ------------------------------------------------------------- workspace --
+// A named, grow-only device buffer owned by the handle.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace krr
+
+struct krr_handle;
+
+namespace krr {
+
+// Device scalar block used by the PCG loop (one per handle).
+struct CgScalars {
+  double rz[KRR_MAX_RHS];      // r.z of the current iteration
+  double pq[KRR_MAX_RHS];      // p.q
+  double alpha[KRR_MAX_RHS];
+  double beta[KRR_MAX_RHS];
+  double rr[KRR_MAX_RHS];      // ||r||^2 (recursive)
+  double yy[KRR_MAX_RHS];      // ||y||^2 of the system being solved
+  double tol2[KRR_MAX_RHS];    // (tol ||y||)^2
+  int active[KRR_MAX_RHS];     // 1 while the column iterates
+  int iters[KRR_MAX_RHS];
+  int iter;                    // loop counter
+  int max_iter;
+  int flags;                   // bit 0 breakdown, bit 1 NaN, bit 2 iteration cap
+  int k;
+  unsigned int counter[8];     // last-block-done counters for reductions
+};
+
+enum : int { FLAG_BREAKDOWN = 1, FLAG_NAN = 2, FLAG_CAP = 4 };
+
+// Per-handle preconditioner state (Algorithm 1 lines 6-7).
+struct Precond {
+  bool ready = false;
+  int n = 0, s = 0, form = KRR_APPLY_ZL, z_bf16 = 0;
+  double lam_p = 0.0;
+  DevBuf Z;      // n x s (ld = s), FP32 or BF16
+  DevBuf L;      // s x s FP64 lower Cholesky factor of G
+  DevBuf Linv;   // s x s FP64 lower inverse of L (ZL form)
+  DevBuf LinvT;  // s x s FP64, (L^-1)^T, upper (ZL form)
+  DevBuf U;      // s x n FP32, U = L^-1 Z^T (U form)
+};
+
+// ------------------------------------------------------ kernel launchers --
+// All launchers enqueue on `st` and throw krr::Error on launch failure.
+
+int sm_count();
+
+// RFF features (krr_rff.cu)
+void launch_rff(cudaStream_t st, const float* X, int n, int d, int ldx, const float* W,
+                const float* b, int s, float* Z, int ldz);
+
+// SIMT kernel products (krr_matvec_simt.cu).  part: scratch of
+// simt_part_elems(...) elements of the accumulator type.
+size_t mv_fp64_part_elems(int nr, int nc, int k);
+void launch_mv_fp64(cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
+                    int nc, int ldxc, int d, double sigma, double shift, const double* V,
+                    int k, int ldv, double* Q, int ldq, double* part);
+size_t mv_fp32_part_elems(int nr, int nc, int k);
+void launch_mv_fp32(cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
+                    int nc, int ldxc, int d, double sigma, double shift, const float* V,
+                    int k, int ldv, float* Q, int ldq, float* nrm_r, float* nrm_c,
+                    float* part);
+
+// Preconditioner (krr_precond.cu)
+void launch_copy_z(cudaStream_t st, const float* Z, int n, int s, int ldz, void* Zs, int bf16);
+void launch_gram(cudaStream_t st, const void* Zs, int bf16, int n, int s, double lam_p,
+                 double* G, double* part, int nchunk);
+int gram_chunks(int n, int s);
+void launch_cholesky(cudaStream_t st, double* A, int s, int* info);
+void launch_tri_inverse(cudaStream_t st, const double* L, int s, double* Linv);
+void launch_transpose_d(cudaStream_t st, const double* A, int s, double* B);
+void launch_form_u(cudaStream_t st, const double* Linv, const void* Zs, int bf16, int n, int s,
+                   float* U);
+// z = (r - Z Linv^T Linv Z^T r) / lam_p or (r - U^T U r) / lam_p.
+// R, Zo: n x k with leading dimension ldr / ldo, element type T (float or double).
+// t1, t2: s*k doubles of scratch; part: apply_part_elems doubles of scratch.
+size_t apply_part_elems(int n, int s, int k);
+template <typename T>
+void launch_apply(cudaStream_t st, const Precond& pc, const T* R, int k, int ldr, T* Zo,
+                  int ldo, double* t1, double* t2, double* part);
+
+// CG vector kernels (krr_cg.cu).  `part` is cg_part_elems() doubles.
+struct ColScale {
+  double v[KRR_MAX_RHS];
+};
+size_t cg_part_elems(int n, int k);
+template <typename T>
+void launch_cg_init(cudaStream_t st, CgScalars* sc, const double* Y, int ldy, const T* R, int n,
+                    int k, double tol, int max_iter, double* part);
+template <typename T>
+void launch_cg_rz_first(cudaStream_t st, CgScalars* sc, const T* R, const T* Z, T* P, int n,
+                        int k, double* part);
+template <typename T>
+void launch_cg_alpha(cudaStream_t st, CgScalars* sc, const T* P, const T* Q, int n, int k,
+                     double* part);
+template <typename T>
+void launch_cg_update_xr(cudaStream_t st, CgScalars* sc, T* X, T* R, const T* P, const T* Q,
+                         int n, int k, double* part);
+template <typename T>
+void launch_cg_rz(cudaStream_t st, CgScalars* sc, const T* R, const T* Z, int n, int k,
+                  double* part);
+template <typename T>
+void launch_cg_update_p(cudaStream_t st, CgScalars* sc, T* P, const T* Z, int n, int k);
+// iter += 1; decides whether the loop continues; sets the graph condition
+// when `cond` is nonzero (a cudaGraphConditionalHandle).
+void launch_cg_tail(cudaStream_t st, CgScalars* sc, unsigned long long cond);
+
+// Elementwise helpers (row-major n x k blocks)
+template <typename A, typename B>
+void launch_convert(cudaStream_t st, const A* a, int n, int k, int lda, B* b, int ldb,
+                    const ColScale& scale);
+// c += scale * d (d float or double, c double)
+template <typename D>
+void launch_axpy_d(cudaStream_t st, const D* dlt, int n, int k, int ldd, double* c, int ldc,
+                   const ColScale& scale);
+// r = y - a
+void launch_sub_d(cudaStream_t st, const double* y, int ldy, const double* a, int lda, int n,
+                  int k, double* r, int ldr);
+// out[c] = sum_i a[i, c]^2 (FP64), written to device memory
+template <typename T>
+void launch_colnorm2(cudaStream_t st, const T* a, int n, int k, int lda, double* out,
+                     double* part, unsigned int* counter);
+
+}  // namespace krr

@@ -1,0 +1,48 @@
+// Tensor-core (tcgen05) fused kernel-matrix product: state and launchers.
+#pragma once
+#include <cuda.h>
+
+#include "krr_internal.cuh"
+
+namespace krr {
+
+// One prepared operand set: xh = bf16(sqrt(2c)(x - mu)) padded to n_pad x kp
+// (K-major, 128-byte rows per 64-element K-block), nh = ||xh||^2 and
+// ra = exp2(-nh / 2), with TMA descriptors for 128-row and 256-row boxes.
+struct TcOperand {
+  DevBuf Xa, ra, nh;
+  const float* src = nullptr;
+  int n = 0, ld = 0, d = 0, kp = 0, n_pad = 0;
+  CUtensorMap map_a;
+  CUtensorMap map_b;
+};
+
+struct TcState {
+  TcOperand cols;       // column set (the training points)
+  DevBuf mu;            // column mean (FP64, d)
+  DevBuf scal;          // small device scratch
+  DevBuf w;             // n_pad x kv column weights ra_j v_j
+  DevBuf part;          // nchunk x n_pad x kv partial row sums
+  DevBuf err;           // device error flag (bounded-wait expiry)
+  double sigma = 0.0;
+  bool rows_same = false;
+  bool ready = false;
+  bool err_zeroed = false;
+};
+
+// Prepare the operands for the training set X (n x d, ldx) at bandwidth sigma.
+void tc_prepare(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int d, double sigma);
+// Q = K(X, X) V + shift V through the tensor cores (Xr must equal Xc).
+void tc_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
+               int nc, int ldxc, int d, double sigma, double shift, const float* V, int k,
+               int ldv, float* Q, int ldq);
+// Allocate the product's workspace for k right-hand sides (call before a
+// graph capture; tc_prepare must have run).
+void tc_reserve(TcState& t, cudaStream_t st, int k);
+// Reset the error flag (enqueued on st).
+void tc_clear_error(TcState& t, cudaStream_t st);
+// Nonzero if any launch hit a bounded-wait limit since the state was created.
+int tc_error(TcState& t, cudaStream_t st);
+void tc_release(TcState& t);
+
+}  // namespace krr

@@ -1,0 +1,102 @@
+"""GPU parity of the tcgen05 BF16 fused kernel product and the mixed-precision solve.
+
+The BF16 product evaluates the Gaussian kernel of the BF16-rounded, centred,
+scaled points xh = bf16(sqrt(log2(e))/sigma (x - mean)), i.e.
+K_ij = exp2(-||xh_i - xh_j||^2 / 2).  The oracle evaluates exactly that kernel
+on the same rounded points (rounding done on the CPU by torch, round to
+nearest even like the device), so the comparison isolates the tensor-core
+arithmetic: FP32 accumulation of exact BF16 products, ex2.approx (rel. error
+~2^-22) and FP32 sums of at most 256 terms per tile before FP64 chunk sums.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import krr_synth as ks
+from oracle import krr_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+LOG2E = 1.0 / math.log(2.0)
+
+
+@pytest.fixture(scope="module")
+def K():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1611_03220_gb300 import build
+    build()
+    from paper_1611_03220_gb300 import _krr
+    return _krr
+
+
+@pytest.fixture()
+def h(K):
+    hh = K.Handle()
+    yield hh
+    torch.cuda.synchronize()
+    hh.close()
+
+
+def rounded_points(X, sigma):
+    """xh = bf16(sqrt(log2 e)/sigma * (x - mean)) in FP64 (mean in FP64)."""
+    X64 = X.astype(np.float64)
+    mu = X64.mean(axis=0)
+    scale = math.sqrt(LOG2E) / sigma
+    xf = (scale * (X64 - mu)).astype(np.float32)
+    return torch.from_numpy(xf).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+@pytest.mark.parametrize("n,d,k", [(1000, 37, 1), (777, 64, 3), (1300, 100, 10), (300, 8, 16)])
+def test_matvec_bf16_matches_rounded_oracle(K, h, n, d, k):
+    rng = np.random.default_rng(n + d + k)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    V = rng.standard_normal((n, k)).astype(np.float32)
+    sigma = math.sqrt(d)
+    Q = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    Xd = torch.from_numpy(X).cuda()
+    K.krr_kernel_matvec(h, Xd, Xd, sigma, 0.0, torch.from_numpy(V).cuda(), Q, "bf16")
+    Xh = rounded_points(X, sigma)
+    sig_h = 1.0 / math.sqrt(math.log(2.0))   # exp2(-|d|^2/2) = exp(-|d|^2 / (2 sig_h^2))
+    Kh = O.gaussian_kernel(Xh, Xh, sig_h)
+    ref = Kh @ V.astype(np.float64)
+    scale = Kh @ np.abs(V.astype(np.float64))
+    got = Q.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got - ref) <= 1e-5 * scale), np.max(np.abs(got - ref) / scale)
+    # and against the exact kernel of the unrounded points: the BF16 rounding of x
+    # moves -||x_i - x_j||^2/(2 sigma^2) by about 2^-8 of its size
+    exact = O.gaussian_kernel(X, X, sigma) @ V.astype(np.float64)
+    assert np.all(np.abs(got - exact) <= 3e-2 * scale)
+
+
+def test_matvec_bf16_shift(K, h):
+    P = ks.make_config(2, n=700)
+    rng = np.random.default_rng(2)
+    V = rng.standard_normal((700, 2)).astype(np.float32)
+    Xd = torch.from_numpy(P.X).cuda()
+    Q0 = torch.empty((700, 2), dtype=torch.float32, device="cuda")
+    Q1 = torch.empty_like(Q0)
+    Vd = torch.from_numpy(V).cuda()
+    K.krr_kernel_matvec(h, Xd, Xd, P.sigma, 0.0, Vd, Q0, "bf16")
+    K.krr_kernel_matvec(h, Xd, Xd, P.sigma, 0.25, Vd, Q1, "bf16")
+    np.testing.assert_allclose((Q1 - Q0).cpu().numpy(), 0.25 * V, rtol=1e-5, atol=1e-5)
+
+
+@pytest.mark.parametrize("cfg,n,s", [(2, 4096, 128), (1, 2000, 200)])
+def test_pcg_mixed_reaches_tolerance(K, h, cfg, n, s):
+    """BF16 inner PCG + refinement with an FP64 residual reaches the FP64 target.
+
+    The oracle recomputes ||y - (K + lambda I) c|| / ||y|| of the returned c."""
+    P = ks.make_config(cfg, n=n, s=s)
+    tol = 1e-6 if cfg == 2 else 1e-8
+    C = torch.zeros((n, 1), dtype=torch.float64, device="cuda")
+    o = K.default_opts(tol=tol, precision="mixed")
+    rep = K.krr_pcg_solve(h, torch.from_numpy(P.X).cuda(), P.sigma, P.lam,
+                          torch.from_numpy(P.W).cuda(), torch.from_numpy(P.b).cuda(),
+                          torch.from_numpy(P.Y).cuda(), C, o, check=False)
+    assert rep["status"] == "KRR_OK", rep
+    res = O.true_rel_residual(P.X, P.Y, C.cpu().numpy(), P.sigma, P.lam)[0]
+    assert res <= tol, (res, rep)
+    assert rep["outer_steps"] >= 1
