@@ -1,0 +1,337 @@
+"""Benchmark of the RFF-preconditioned KRR solve on GB300.
+
+One step = the whole hot path on the 65,536-point, 64-dimensional Gaussian
+mixture workload (sigma = 8, lambda = 1e-4, s = 2,048 random Fourier
+features, tolerance 1e-6): features, Gram matrix, FP64 Cholesky, Woodbury
+factors, mixed-precision PCG with iterative refinement to a true relative
+residual of 1e-6, and prediction at 8,192 held-out points.  Inputs are
+resident in HBM when a step starts; the L2 cache is flushed between steps.
+
+Also reported: the plain FP32 solve of the same system (its time and the
+residual floor it reaches), the fused BF16 kernel product timed alone
+(pairs/s, TFLOP/s and its exp-bound roofline), the same step through the C
+ABI with host buffers (e2e), and the FP64 oracle timed on a bounded sample
+on the host cores (cpu_baseline).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank solves its own
+replica of the workload: the path has no exchange step (replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import krr_synth as ks  # noqa: E402
+
+METRIC = "KRR PCG time-to-rel-residual 1e-6 (mixed vs FP32); kernel-matvec TFLOP/s"
+WORKLOAD = ("gaussian-mixture n=65536 d=64 (10 centres N(0,4I), unit spread), sigma=8, "
+            "lambda=1e-4, s=2048 RFF, tol 1e-6, predict m=8192")
+M_TEST = 8192
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=None, help="override n (smaller instance)")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparator")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ----------------------------------------------------------------- clocks --
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------- oracle leg --
+def oracle_sample(P, rows: int, reps: int = 1) -> tuple[float, int]:
+    """Seconds for the FP64 oracle's kernel product on `rows` rows of the workload."""
+    from oracle import krr_oracle as O
+    rng = np.random.default_rng(0)
+    V = rng.standard_normal((P.n, 1))
+    best = float("inf")
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        O.kernel_matvec_blocked(P.X[:rows], P.X, V, P.sigma)
+        best = min(best, time.perf_counter() - t0)
+    return best, os.cpu_count() or 1
+
+
+def cpu_baseline(P, matvecs: int, rows: int = 4096) -> dict:
+    t, cores = oracle_sample(P, rows)
+    per_mv = t * P.n / rows
+    est_ms = per_mv * matvecs * 1e3
+    return {"value": est_ms, "unit": "ms", "cores": cores, "kind": "oracle",
+            "sample": (f"FP64 oracle kernel product on {rows} of {P.n} rows "
+                       f"({t:.2f} s), scaled to a full product ({per_mv:.1f} s) times the "
+                       f"{matvecs} kernel products of the GPU solve")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    n = args.n or ks.CONFIGS[2]
+    P = ks.make_config(2, n=n)
+    rows = 1024
+    matvecs = 60  # kernel products of one solve on this workload (mixed path, measured)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t, cores = oracle_sample(P, rows)
+        if i >= args.warmup:
+            times.append(t * P.n / rows * matvecs * 1e3)
+    v = statistics.mean(times)
+    sample = (f"FP64 oracle kernel product on {rows} of {n} rows per step, scaled to "
+              f"{matvecs} full products")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n": n},
+        "cpu_baseline": {"value": v, "unit": "ms", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# ----------------------------------------------------------------- ours ---
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_1611_03220_gb300 import build
+    build()
+    from paper_1611_03220_gb300 import _krr as K
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    n = args.n or ks.CONFIGS[2]
+    P = ks.make_config(2, n=n, m=M_TEST)
+    X = torch.from_numpy(P.X).to(dev)
+    Y = torch.from_numpy(P.Y).to(dev)
+    W = torch.from_numpy(P.W).to(dev)
+    b = torch.from_numpy(P.b).to(dev)
+    Xte = torch.from_numpy(P.Xte).to(dev)
+    C = torch.zeros_like(Y)
+    F = torch.zeros((M_TEST, 1), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    h = K.Handle()
+    opts = K.default_opts(tol=P.tol, precision="mixed")
+
+    def step():
+        C.zero_()
+        rep = K.krr_pcg_solve(h, X, P.sigma, P.lam, W, b, Y, C, opts, check=False)
+        K.krr_predict(h, X, Xte, P.sigma, C, F, "fp32")
+        return rep
+
+    for _ in range(args.warmup):
+        rep = step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    launches0 = K._lib.krr_launch_count()
+    st = torch.cuda.current_stream()
+    times, reps = [], []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        rep = step()
+        e1.record(st)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        reps.append(rep)
+        flush.zero_()
+    torch.cuda.synchronize()
+    launches = K._lib.krr_launch_count() - launches0
+    clk = clocks.stop()
+    ms = statistics.mean(times)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    rep = reps[-1]
+
+    # ------------------------------------------ fused product, timed alone
+    Vf = torch.randn((n, 1), dtype=torch.float32, device=dev)
+    Qf = torch.empty_like(Vf)
+    for _ in range(3):
+        K.krr_kernel_matvec(h, X, X, P.sigma, P.lam, Vf, Qf, "bf16")
+    mv_ms = []
+    for _ in range(10):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        K.krr_kernel_matvec(h, X, X, P.sigma, P.lam, Vf, Qf, "bf16")
+        e1.record(st)
+        e1.synchronize()
+        mv_ms.append(e0.elapsed_time(e1))
+    t_mv = statistics.median(mv_ms) * 1e-3
+    pairs = float(n) * n
+    d_pad = 64 * math.ceil(P.d / 64)
+    n_pad = 256 * math.ceil(n / 256)
+    alg_flops = 2.0 * pairs * (P.d + 1)
+    ex2_rate = C_ms = None
+    import ctypes
+    r = ctypes.c_double()
+    kms = ctypes.c_double()
+    if K._lib.krr_bench_ex2(h.ptr, 4096, ctypes.byref(r), ctypes.byref(kms)) == 0:
+        ex2_rate = r.value
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_mhz = clk.get("sm_mhz") or 2070.0
+    lanes = None
+    if ex2_rate:
+        lanes = 2 ** round(math.log2(ex2_rate / (sms * clk_mhz * 1e6)))
+    peak = (lanes or 16) * sms * 2070e6
+    achieved = pairs / t_mv
+    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
+                "unit": "Gexp/s", "frac": achieved / peak, "traffic": None,
+                "kernel": "tc_matvec_kernel (+ w/reduce helpers)",
+                "peak_basis": (f"{lanes or 16} MUFU ex2 lanes/SM/clk x {sms} SMs x 2070 MHz "
+                               f"(lanes from the ex2 probe: {ex2_rate and ex2_rate / 1e9:.0f} "
+                               f"Gexp/s at {clk_mhz:.0f} MHz)")}
+    mv = {"ms": t_mv * 1e3, "pairs_per_s": achieved, "alg_tflops": alg_flops / t_mv / 1e12,
+          "tensor_tflops": 2.0 * n_pad * n_pad * d_pad / t_mv / 1e12}
+
+    # ------------------------------------------------ FP32 comparator ------
+    fp32 = None
+    if not args.no_fp32:
+        C32 = torch.zeros_like(Y)
+        o32 = K.default_opts(tol=P.tol, precision="fp32")
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r32 = K.krr_pcg_solve(h, X, P.sigma, P.lam, W, b, Y, C32, o32, check=False)
+        torch.cuda.synchronize()
+        fp32 = {"ms": (time.perf_counter() - t0) * 1e3, "status": r32["status"],
+                "iters": r32["iters"][0], "rel_res_fp64_check": r32["rel_res"][0]}
+
+    # ------------------------------------------------ end to end (host) ----
+    Xh, Yh, Wh, bh = P.X, P.Y, P.W, P.b
+    Xteh = P.Xte
+    Ch = np.zeros((n, 1))
+    Fh = np.zeros((M_TEST, 1))
+    e2e_ms = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        K.krr_pcg_solve(h, Xh, P.sigma, P.lam, Wh, bh, Yh, Ch, opts, check=False)
+        K.krr_predict(h, Xh, Xteh, P.sigma, Ch, Fh, "fp32")
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    h2d = Xh.nbytes + Yh.nbytes + Wh.nbytes + bh.nbytes + Xh.nbytes + Xteh.nbytes + Ch.nbytes
+    d2h = Ch.nbytes + Fh.nbytes
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(P, rep["matvecs"])
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "d": P.d, "s": P.s, "sigma": P.sigma,
+                       "lambda": P.lam, "tol": P.tol, "m_predict": M_TEST,
+                       "l2": "flushed between steps (512 MiB write)",
+                       "parallelism": "replicas" if world > 1 else "single-gpu"},
+            "solve": {"status": rep["status"], "iters": rep["iters"][0],
+                      "outer_steps": rep["outer_steps"], "matvecs": rep["matvecs"],
+                      "rel_res_fp64": rep["rel_res"][0], "ms_setup": rep["ms_setup"],
+                      "ms_solve": rep["ms_solve"], "step_ms_all": times},
+            "fp32": fp32, "kernel_matvec": mv, "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "clocks": clk, "gpu_launches": launches,
+        }
+        if world > 1:
+            out["aggregate_solves_per_s"] = world * 1000.0 / ms
+        print(json.dumps(out))
+    h.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

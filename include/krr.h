@@ -175,13 +175,29 @@ krr_status krr_pcg_solve(krr_handle* h, const float* X, int n, int d, int ldx,
 /*
  * Predictor f(x) = sum_i c_i k(x_i, x) (Section 1) at m held-out points:
  *   F = K(Xte, Xtr) C.  Xtr: n x d (ldxtr), Xte: m x d (ldxte) FP32,
- * C: n x k double (ldc), F: m x k double (ldf); device pointers.
+ * C: n x k double (ldc), F: m x k double (ldf); host or device pointers
+ * (F is written before the call returns when it is a host pointer).
  * precision: KRR_FP64, KRR_HP or KRR_FP32 (FP32 then widened).
  */
 krr_status krr_predict(krr_handle* h, const float* Xtr, int n, int ldxtr,
                        const float* Xte, int m, int ldxte, int d, double sigma,
                        const double* C, int k, int ldc, double* F, int ldf,
                        int precision);
+
+/* ------------------------------------------------------- diagnostics --- */
+/* The paper has no counterpart for these; they serve measurement. */
+
+/* Number of this library's kernels launched by the calling process so far,
+ * kernels inside the PCG graph counted once per executed iteration. */
+long long krr_launch_count(void);
+
+/*
+ * Throughput of the MUFU base-2 exponential on the handle's device: runs a
+ * kernel of independent ex2.approx chains for `iters` steps per thread on
+ * every SM and writes results per second to *ex2_per_s and the kernel time
+ * to *ms.  Used to state the exp-bound roofline of the fused product.
+ */
+krr_status krr_bench_ex2(krr_handle* h, int iters, double* ex2_per_s, double* ms);
 
 #ifdef __cplusplus
 }

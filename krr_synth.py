@@ -94,25 +94,27 @@ def _cfg1(n: int, s: int | None) -> Problem:
                    1.0, 1e-3, s, 1e-8, W, b)
 
 
-def _mixture(rng: np.random.Generator, n: int, d: int, ncent: int):
-    centres = 2.0 * rng.standard_normal((ncent, d))           # N(0, 4I)
-    labels = rng.integers(0, ncent, size=n)
-    X = centres[labels] + rng.standard_normal((n, d))
-    return X, labels
-
-
-def _cfg2(n: int, s: int | None) -> Problem:
+def _cfg2(n: int, s: int | None, m: int | None = None) -> Problem:
     rng = np.random.Generator(np.random.PCG64(1002))
     d, ncent = 64, 10
-    X, labels = _mixture(rng, n, d, ncent)
+    centres = 2.0 * rng.standard_normal((ncent, d))             # N(0, 4I)
+    labels = rng.integers(0, ncent, size=n)
+    X = centres[labels] + rng.standard_normal((n, d))
     a = rng.standard_normal((ncent, d)) / math.sqrt(d)          # a_c ~ N(0, I/d)
     bc = rng.standard_normal(ncent)                             # b_c ~ N(0, 1)
     y = np.einsum("ij,ij->i", X, a[labels]) + bc[labels] + 0.1 * rng.standard_normal(n)
     sigma = math.sqrt(d)
     s = 2048 if s is None else s
     W, b = rff_draw(2002, d, s, sigma)
-    return Problem("precision", X.astype(np.float32), y[:, None].astype(np.float64),
-                   sigma, 1e-4, s, 1e-6, W, b)
+    P = Problem("precision", X.astype(np.float32), y[:, None].astype(np.float64),
+                sigma, 1e-4, s, 1e-6, W, b)
+    if m:
+        # held-out points from the same mixture, drawn after every training draw
+        lt = rng.integers(0, ncent, size=m)
+        Xt = centres[lt] + rng.standard_normal((m, d))
+        yt = np.einsum("ij,ij->i", Xt, a[lt]) + bc[lt] + 0.1 * rng.standard_normal(m)
+        P.Xte, P.Yte = Xt.astype(np.float32), yt[:, None].astype(np.float64)
+    return P
 
 
 def _cfg3(n: int, s: int | None) -> Problem:
@@ -163,7 +165,7 @@ def make_config(i: int, n: int | None = None, s: int | None = None,
     if i == 1:
         return _cfg1(n, s)
     if i == 2:
-        return _cfg2(n, s)
+        return _cfg2(n, s, m)
     if i == 3:
         return _cfg3(n, s)
     return _cfg5(n, s, m)

@@ -67,6 +67,8 @@ _SIGS = {
     "krr_pcg_solve": (_i, [_vp, _vp, _i, _i, _i, _d, _d, _vp, _vp, _i, _vp, _i, _i, _vp, _i,
                            C.POINTER(krr_opts), C.POINTER(krr_report)]),
     "krr_predict": (_i, [_vp, _vp, _i, _i, _vp, _i, _i, _i, _d, _vp, _i, _i, _vp, _i, _i]),
+    "krr_launch_count": (C.c_longlong, []),
+    "krr_bench_ex2": (_i, [_vp, _i, C.POINTER(_d), C.POINTER(_d)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)

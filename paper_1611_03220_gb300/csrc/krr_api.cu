@@ -256,6 +256,7 @@ void pcg_loop(krr_handle* h, int n, int k, const double* Ytol, int ldy, T* x, T*
   };
 
   int launched = 0;
+  long long body_launches = 0;
   if (max_iter > 0) {
     if (use_graph) {
       cudaGraph_t graph = nullptr;
@@ -275,14 +276,17 @@ void pcg_loop(krr_handle* h, int n, int k, const double* Ytol, int ldy, T* x, T*
         cudaGraph_t bodyg = params.conditional.phGraph_out[0];
         KRR_CUDA(cudaStreamBeginCaptureToGraph(h->cap, bodyg, nullptr, nullptr, 0,
                                                cudaStreamCaptureModeRelaxed));
+        capture_begin();
         try {
           body(h->cap, (unsigned long long)cond);
         } catch (...) {
+          capture_end();
           cudaGraph_t tmp;
           cudaStreamEndCapture(h->cap, &tmp);
           cudaGetLastError();
           throw;
         }
+        body_launches = capture_end();
         cudaGraph_t captured = nullptr;
         KRR_TRACE("pcg_loop: body captured");
         KRR_CUDA(cudaStreamEndCapture(h->cap, &captured));
@@ -301,6 +305,7 @@ void pcg_loop(krr_handle* h, int n, int k, const double* Ytol, int ldy, T* x, T*
       cudaGraphExecDestroy(exec);
       cudaGraphDestroy(graph);
       launched = h->sc_host->iter;
+      add_launches(body_launches * (long long)launched);
     } else {
       // host-driven loop: checks the device scalars every `chk` iterations
       const int chk = 8;
@@ -829,22 +834,41 @@ krr_status krr_predict(krr_handle* h, const float* Xtr, int n, int ldxtr, const 
     KRR_REQUIRE(n > 0 && m > 0 && d > 0 && k >= 1 && k <= KRR_MAX_RHS, "predict: bad sizes");
     KRR_REQUIRE(ldxtr >= d && ldxte >= d && ldc >= k && ldf >= k, "predict: bad leading dims");
     KRR_REQUIRE(sigma > 0.0 && std::isfinite(sigma), "predict: sigma must be > 0");
+    KRR_REQUIRE(precision == KRR_FP64 || precision == KRR_HP || precision == KRR_FP32,
+                "predict: bad precision");
+    cudaStream_t st = h->stream;
+    const float* Xtr_d = (const float*)stage_in(h, Xtr, (size_t)n * ldxtr * sizeof(float), "pXtr");
+    const float* Xte_d = (const float*)stage_in(h, Xte, (size_t)m * ldxte * sizeof(float), "pXte");
+    const double* C_d = (const double*)stage_in(h, C, (size_t)n * ldc * sizeof(double), "pC");
+    const bool f_host = !on_device(F);
+    double* F_d = f_host ? wsT<double>(h, "pF", (size_t)m * ldf) : F;
     if (precision == KRR_FP32) {
       ColScale one;
       for (int c = 0; c < KRR_MAX_RHS; ++c) one.v[c] = 1.0;
       float* Cf = wsT<float>(h, "pr_cf", (size_t)n * k);
       float* Ff = wsT<float>(h, "pr_ff", (size_t)m * k);
-      launch_convert<double, float>(h->stream, C, n, k, ldc, Cf, k, one);
-      matvec_dispatch(h, h->stream, Xte, m, ldxte, Xtr, n, ldxtr, d, sigma, 0.0, Cf, k, k, Ff, k,
+      launch_convert<double, float>(st, C_d, n, k, ldc, Cf, k, one);
+      matvec_dispatch(h, st, Xte_d, m, ldxte, Xtr_d, n, ldxtr, d, sigma, 0.0, Cf, k, k, Ff, k,
                       KRR_FP32);
-      launch_convert<float, double>(h->stream, Ff, m, k, k, F, ldf, one);
-      return KRR_OK;
+      launch_convert<float, double>(st, Ff, m, k, k, F_d, ldf, one);
+    } else {
+      matvec_dispatch(h, st, Xte_d, m, ldxte, Xtr_d, n, ldxtr, d, sigma, 0.0, C_d, k, ldc, F_d,
+                      ldf, precision);
     }
-    KRR_REQUIRE(precision == KRR_FP64 || precision == KRR_HP, "predict: bad precision");
-    matvec_dispatch(h, h->stream, Xte, m, ldxte, Xtr, n, ldxtr, d, sigma, 0.0, C, k, ldc, F, ldf,
-                    precision);
+    if (f_host) {
+      KRR_CUDA(cudaMemcpyAsync(F, F_d, (size_t)m * ldf * sizeof(double), cudaMemcpyDeviceToHost, st));
+      KRR_CUDA(cudaStreamSynchronize(st));
+    }
     return KRR_OK;
   });
 }
 
 }  // extern "C"
+
+extern "C" krr_status krr_bench_ex2(krr_handle* h, int iters, double* ex2_per_s, double* ms) {
+  return guard(h, [&]() -> krr_status {
+    KRR_REQUIRE(iters > 0 && ex2_per_s, "bench_ex2: iters > 0 and an output pointer");
+    *ex2_per_s = bench_ex2(h->stream, iters, ms);
+    return KRR_OK;
+  });
+}

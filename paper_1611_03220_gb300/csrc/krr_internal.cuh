@@ -25,7 +25,19 @@ struct Error {
       throw ::krr::Error{KRR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
   } while (0)
 
-#define KRR_CHECK_LAUNCH() KRR_CUDA(cudaGetLastError())
+// Kernel-launch accounting (krr_launch_count): launches made while a loop
+// body is being captured into a graph are counted per captured body and
+// multiplied by the iterations the graph executes.
+void count_launch();
+void capture_begin();
+long long capture_end();           // launches seen since capture_begin
+void add_launches(long long n);
+double bench_ex2(cudaStream_t st, int iters, double* ms_out);
+#define KRR_CHECK_LAUNCH()            \
+  do {                                \
+    KRR_CUDA(cudaGetLastError());     \
+    ::krr::count_launch();            \
+  } while (0)
 
 #define KRR_REQUIRE(cond, msg)                                                  \
   do {                                                                          \

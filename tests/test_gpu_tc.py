@@ -84,15 +84,16 @@ def test_matvec_bf16_shift(K, h):
     np.testing.assert_allclose((Q1 - Q0).cpu().numpy(), 0.25 * V, rtol=1e-5, atol=1e-5)
 
 
-@pytest.mark.parametrize("cfg,n,s", [(2, 4096, 128), (1, 2000, 200)])
-def test_pcg_mixed_reaches_tolerance(K, h, cfg, n, s):
+@pytest.mark.parametrize("cfg,n,s,tol", [(2, 4096, 128, 1e-6), (5, 3000, 256, 1e-6),
+                                         (1, 2000, 200, 1e-8)])
+def test_pcg_mixed_reaches_tolerance(K, h, cfg, n, s, tol):
     """BF16 inner PCG + refinement with an FP64 residual reaches the FP64 target.
 
-    The oracle recomputes ||y - (K + lambda I) c|| / ||y|| of the returned c."""
+    The oracle recomputes ||y - (K + lambda I) c|| / ||y|| of the returned c.
+    Workload 1's weak preconditioner needs ~1800 iterations in all (cap 6000)."""
     P = ks.make_config(cfg, n=n, s=s)
-    tol = 1e-6 if cfg == 2 else 1e-8
     C = torch.zeros((n, 1), dtype=torch.float64, device="cuda")
-    o = K.default_opts(tol=tol, precision="mixed")
+    o = K.default_opts(tol=tol, precision="mixed", max_iter=6000)
     rep = K.krr_pcg_solve(h, torch.from_numpy(P.X).cuda(), P.sigma, P.lam,
                           torch.from_numpy(P.W).cuda(), torch.from_numpy(P.b).cuda(),
                           torch.from_numpy(P.Y).cuda(), C, o, check=False)
