@@ -184,6 +184,34 @@ krr_status krr_predict(krr_handle* h, const float* Xtr, int n, int ldxtr,
                        const double* C, int k, int ldc, double* F, int ldf,
                        int precision);
 
+/*
+ * Kernel-matrix product that allocates nothing.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc when
+ * they need the product -- code that runs while a stream is captured into
+ * a CUDA graph (an allocation there breaks the capture), code inside a
+ * framework whose caching allocator already holds the GPU's memory, and
+ * loops that must avoid the device synchronisation an allocation may cause.
+ *
+ * Computes the same FP64 product as krr_kernel_matvec(..., KRR_FP64):
+ *   Q[i, :] = sum_j k(xr_i, xc_j) V[j, :] + shift * V[i, :]
+ * with the same argument meaning and layout (device pointers), enqueued on
+ * `stream` (a cudaStream_t, NULL = legacy default stream); no handle.
+ * Its partial sums live in a fixed device array of 2^20 doubles (8 MiB)
+ * that every GPU loading the library keeps until the process exits, so
+ * nr * k must be at most 1048576; larger requests return KRR_EINVAL without
+ * launching.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the array: calls whose kernels may overlap on
+ * the GPU (other streams, other threads) race and must be serialised by
+ * the caller.  Returns KRR_EINVAL for bad arguments, KRR_ECUDA if the
+ * lookup or a launch fails.
+ */
+krr_status krr_kernel_matvec_fp64_noalloc(const float* Xr, int nr, int ldxr,
+                                          const float* Xc, int nc, int ldxc, int d,
+                                          double sigma, double shift,
+                                          const double* V, int k, int ldv,
+                                          double* Q, int ldq, void* stream);
+
 /* ------------------------------------------------------- diagnostics --- */
 /* The paper has no counterpart for these; they serve measurement. */
 

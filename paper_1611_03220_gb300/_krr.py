@@ -67,6 +67,8 @@ _SIGS = {
     "krr_pcg_solve": (_i, [_vp, _vp, _i, _i, _i, _d, _d, _vp, _vp, _i, _vp, _i, _i, _vp, _i,
                            C.POINTER(krr_opts), C.POINTER(krr_report)]),
     "krr_predict": (_i, [_vp, _vp, _i, _i, _vp, _i, _i, _i, _d, _vp, _i, _i, _vp, _i, _i]),
+    "krr_kernel_matvec_fp64_noalloc": (_i, [_vp, _i, _i, _vp, _i, _i, _i, _d, _d, _vp, _i, _i,
+                                            _vp, _i, _vp]),
     "krr_launch_count": (C.c_longlong, []),
     "krr_bench_ex2": (_i, [_vp, _i, C.POINTER(_d), C.POINTER(_d)]),
 }
@@ -176,6 +178,19 @@ def krr_kernel_matvec(h: Handle, Xr, Xc, sigma: float, shift: float, V, Q, preci
                                     float(sigma), float(shift), _ptr(V), k, _ld(V), _ptr(Q),
                                     _ld(Q), prec))
     return Q
+
+
+def krr_kernel_matvec_fp64_noalloc(Xr, Xc, sigma: float, shift: float, V, Q, stream=None) -> int:
+    """FP64 Q = K(Xr, Xc) V + shift V without any device allocation; returns the status.
+
+    For callers that cannot allocate (see include/krr.h); no handle needed.
+    """
+    nr, d = Xr.shape
+    nc = Xc.shape[0]
+    k = V.shape[1]
+    return _lib.krr_kernel_matvec_fp64_noalloc(_ptr(Xr), nr, _ld(Xr), _ptr(Xc), nc, _ld(Xc), d,
+                                               float(sigma), float(shift), _ptr(V), k, _ld(V),
+                                               _ptr(Q), _ld(Q), _stream_ptr(stream))
 
 
 def krr_precond_setup(h: Handle, Z, lambda_p: float, apply_form="zl", z_bf16: bool = False):

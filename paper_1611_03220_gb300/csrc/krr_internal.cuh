@@ -104,6 +104,9 @@ size_t mv_fp64_part_elems(int nr, int nc, int k);
 void launch_mv_fp64(cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
                     int nc, int ldxc, int d, double sigma, double shift, const double* V,
                     int k, int ldv, double* Q, int ldq, double* part);
+void launch_mv_fp64_capped(cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
+                           int nc, int ldxc, int d, double sigma, double shift, const double* V,
+                           int k, int ldv, double* Q, int ldq, double* part, size_t cap);
 size_t mv_fp32_part_elems(int nr, int nc, int k);
 void launch_mv_fp32(cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
                     int nc, int ldxc, int d, double sigma, double shift, const float* V,

@@ -247,6 +247,28 @@ void launch_mv_fp64(cudaStream_t st, const float* Xr, int nr, int ldxr, const fl
   KRR_CHECK_LAUNCH();
 }
 
+// Same product with the split count limited so the partial sums fit in a
+// caller-provided scratch of `cap` doubles (nr * k <= cap is required).
+void launch_mv_fp64_capped(cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
+                           int nc, int ldxc, int d, double sigma, double shift, const double* V,
+                           int k, int ldv, double* Q, int ldq, double* part, size_t cap) {
+  int rb = (nr + M64_ROWS - 1) / M64_ROWS;
+  int ct = (nc + M64_TJ - 1) / M64_TJ;
+  int ns = choose_split(rb, ct);
+  const size_t per = (size_t)nr * k;
+  if (per == 0 || per > cap) throw Error{KRR_EINVAL, "product too large for the scratch"};
+  if ((size_t)ns * per > cap) ns = (int)(cap / per);
+  int tps = (ct + ns - 1) / ns;
+  ns = (ct + tps - 1) / tps;
+  double g = -1.0 / (2.0 * sigma * sigma);
+  mv_fp64_kernel<<<dim3(rb, ns), M64_ROWS, 0, st>>>(Xr, nr, ldxr, Xc, nc, ldxc, d, g, V, k, ldv,
+                                                     part, tps);
+  KRR_CHECK_LAUNCH();
+  int nb = (int)std::min<size_t>(((size_t)nr * k + 255) / 256, (size_t)8 * sm_count());
+  reduce_split_kernel<double, double><<<nb, 256, 0, st>>>(part, ns, nr, k, V, ldv, shift, Q, ldq);
+  KRR_CHECK_LAUNCH();
+}
+
 size_t mv_fp32_part_elems(int nr, int nc, int k) {
   int rb = (nr + M32_BM - 1) / M32_BM;
   int ct = (nc + M32_BN - 1) / M32_BN;
