@@ -35,6 +35,7 @@ struct krr_handle {
   int* info = nullptr;          // device int
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   TcState tc;
+  HpState hp;
 };
 
 namespace krr {
@@ -170,6 +171,11 @@ double ms_between(cudaEvent_t a, cudaEvent_t b) {
 void matvec_dispatch(krr_handle* h, cudaStream_t st, const float* Xr, int nr, int ldxr,
                      const float* Xc, int nc, int ldxc, int d, double sigma, double shift,
                      const void* V, int k, int ldv, void* Q, int ldq, int prec) {
+  const bool same = (Xr == Xc && nr == nc && ldxr == ldxc);
+  if (prec == KRR_HP && same && hp_supported(d)) {
+    hp_matvec(h->hp, st, Xr, nr, ldxr, d, sigma, shift, (const double*)V, k, ldv, (double*)Q, ldq);
+    return;
+  }
   switch (prec) {
     case KRR_FP64:
     case KRR_HP: {
@@ -674,6 +680,7 @@ krr_status krr_destroy(krr_handle* h) {
   free_buf(h->pc.LinvT);
   free_buf(h->pc.U);
   tc_release(h->tc);
+  hp_release(h->hp);
   if (h->sc) cudaFree(h->sc);
   if (h->sc_host) cudaFreeHost(h->sc_host);
   if (h->hostd) cudaFreeHost(h->hostd);
@@ -719,7 +726,8 @@ krr_status krr_kernel_matvec(krr_handle* h, const float* Xr, int nr, int ldxr, c
     KRR_REQUIRE(precision >= KRR_FP64 && precision <= KRR_HP, "kernel_matvec: bad precision");
     matvec_dispatch(h, h->stream, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, shift, V, k, ldv, Q, ldq,
                     precision);
-    if (precision == KRR_BF16 && tc_error(h->tc, h->stream))
+    if ((precision == KRR_BF16 && tc_error(h->tc, h->stream)) ||
+        (precision == KRR_HP && hp_error(h->hp, h->stream)))
       throw Error{KRR_ETIMEOUT, "tensor-core product: a pipeline wait hit its limit"};
     return KRR_OK;
   });
@@ -798,6 +806,10 @@ krr_status krr_pcg_solve(krr_handle* h, const float* X, int n, int d, int ldx, d
     if (o.precision == KRR_MIXED) {
       tc_prepare(h->tc, st, Xd, n, ldx, d, sigma);
       tc_clear_error(h->tc, st);
+      if (hp_supported(d)) {
+        hp_prepare(h->hp, st, Xd, n, ldx, d, sigma);
+        hp_clear_error(h->hp, st);
+      }
     }
     KRR_CUDA(cudaEventRecord(h->ev[1], st));
     KRR_TRACE("pcg_solve: setup done");
@@ -809,7 +821,8 @@ krr_status krr_pcg_solve(krr_handle* h, const float* X, int n, int d, int ldx, d
       status = solve_plain<float>(h, a, KRR_FP32, rep, &matvecs);
     else
       status = solve_mixed(h, a, rep, &matvecs);
-    if (o.precision == KRR_MIXED && tc_error(h->tc, st)) status = KRR_ETIMEOUT;
+    if (o.precision == KRR_MIXED && (tc_error(h->tc, st) || hp_error(h->hp, st)))
+      status = KRR_ETIMEOUT;
     if (c_host)
       KRR_CUDA(cudaMemcpyAsync(C, Cd, (size_t)n * ldc * sizeof(double), cudaMemcpyDeviceToHost, st));
     KRR_CUDA(cudaEventRecord(h->ev[2], st));

@@ -1,0 +1,362 @@
+// Woodbury apply of the random-feature preconditioner (Section 3.1,
+// Algorithm 1 line 9):
+//   ZL form:  z = (r - Z L^-T L^-1 Z^T r) / lambda_p
+//   U form:   z = (r - U^T U r) / lambda_p,   U = L^-1 Z^T
+// The ZL form is four steps, each one pass over its operand:
+//   zt_kernel    t = Z^T r      GEMV-T over the n x s matrix Z (split over
+//                               row slabs; FP32/FP64 slab sums, FP64 merge)
+//   sum_kernel   merge the slab partials in FP64
+//   trmv_kernel  u = L^-1 t, w = L^-T u   (FP64, explicit inverse from set-up)
+//   zw_kernel    z = (r - Z w) / lambda_p GEMV over Z with w staged in
+//                               shared memory
+// Both GEMVs stream Z once with 16-byte loads (8 BF16 or 4 FP32 values), so
+// the apply is bound by HBM: about 2 n s b_Z bytes per application.
+#include <type_traits>
+
+#include "krr_internal.cuh"
+
+namespace krr {
+namespace {
+
+constexpr int AT = 256;        // threads per CTA
+constexpr int ZT_ROWS = 64;    // R rows staged per slab step
+
+int kv_of(int k) {
+  if (k <= 1) return 1;
+  if (k <= 2) return 2;
+  if (k <= 4) return 4;
+  if (k <= 8) return 8;
+  if (k <= 12) return 12;
+  return 16;
+}
+
+// Eight consecutive Z values starting at element `off` (n_ok of them valid).
+template <int BF16>
+__device__ __forceinline__ void load8(const void* Zs, size_t off, int n_ok, bool vec,
+                                      float (&z)[8]) {
+  if (vec && n_ok >= 8) {
+    if (BF16) {
+      uint4 v = *reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(Zs) + off);
+      const __nv_bfloat162* p = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float2 f = __bfloat1622float2(p[q]);
+        z[2 * q] = f.x;
+        z[2 * q + 1] = f.y;
+      }
+    } else {
+      const float4* p = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(Zs) + off);
+      float4 a = p[0], b = p[1];
+      z[0] = a.x; z[1] = a.y; z[2] = a.z; z[3] = a.w;
+      z[4] = b.x; z[5] = b.y; z[6] = b.z; z[7] = b.w;
+    }
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    if (q < n_ok) {
+      z[q] = BF16 ? __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(Zs)[off + q])
+                  : reinterpret_cast<const float*>(Zs)[off + q];
+    } else {
+      z[q] = 0.f;
+    }
+  }
+}
+
+// part[chunk, col, c] = sum_{i in chunk} Z[i, col] R[i, c]; 8 columns per thread.
+template <int BF16, typename T, typename ACC, int KV>
+__global__ void __launch_bounds__(AT)
+zt_kernel(const void* __restrict__ Zs, int n, int s, const T* __restrict__ R, int ldr, int k,
+          ACC* __restrict__ part, int rpc, int vec) {
+  __shared__ ACC rs[ZT_ROWS][KV];
+  const int col0 = (blockIdx.x * AT + threadIdx.x) * 8;
+  const int r0 = blockIdx.y * rpc, r1 = min(n, r0 + rpc);
+  ACC acc[8][KV];
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+#pragma unroll
+    for (int c = 0; c < KV; ++c) acc[q][c] = (ACC)0;
+  const int n_ok = s - col0;
+  for (int base = r0; base < r1; base += ZT_ROWS) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < ZT_ROWS * KV; e += AT) {
+      const int rr = e / KV, c = e % KV, i = base + rr;
+      rs[rr][c] = (i < r1 && c < k) ? (ACC)R[(size_t)i * ldr + c] : (ACC)0;
+    }
+    __syncthreads();
+    if (n_ok > 0) {
+      const int nrow = min(ZT_ROWS, r1 - base);
+#pragma unroll 4
+      for (int rr = 0; rr < nrow; ++rr) {
+        float z[8];
+        load8<BF16>(Zs, (size_t)(base + rr) * s + col0, n_ok, vec != 0, z);
+#pragma unroll
+        for (int c = 0; c < KV; ++c) {
+          const ACC rv = rs[rr][c];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) acc[q][c] = fma((ACC)z[q], rv, acc[q][c]);
+        }
+      }
+    }
+  }
+  if (n_ok <= 0) return;
+  ACC* out = part + (size_t)blockIdx.y * s * KV;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    if (q >= n_ok) break;
+#pragma unroll
+    for (int c = 0; c < KV; ++c) out[(size_t)(col0 + q) * KV + c] = acc[q][c];
+  }
+}
+
+// t[col, c] = sum over chunks (FP64), for c < k (t has leading dimension k).
+template <typename P>
+__global__ void sum_kernel(const P* __restrict__ part, int nchunk, int s, int kv, int k,
+                           double* __restrict__ t) {
+  const size_t total = (size_t)s * k;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t col = e / k, c = e % k;
+    double v = 0.0;
+    for (int ch = 0; ch < nchunk; ++ch) v += (double)part[((size_t)ch * s + col) * kv + c];
+    t[e] = v;
+  }
+}
+
+// y[a, c] = sum_b A[a, b] x[b, c], b <= a (lower) or b >= a (upper); one warp per row.
+template <int UPPER, int KV>
+__global__ void __launch_bounds__(AT)
+trmv_kernel(const double* __restrict__ A, int s, const double* __restrict__ x, int k,
+            double* __restrict__ y) {
+  const int warp = (blockIdx.x * AT + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= s) return;
+  const int a = warp;
+  const int lo = UPPER ? a : 0, hi = UPPER ? s : a + 1;
+  double acc[KV];
+#pragma unroll
+  for (int c = 0; c < KV; ++c) acc[c] = 0.0;
+  const double* row = A + (size_t)a * s;
+#pragma unroll 4
+  for (int b = lo + lane; b < hi; b += 32) {
+    const double av = __ldg(row + b);
+#pragma unroll
+    for (int c = 0; c < KV; ++c)
+      if (c < k) acc[c] = fma(av, __ldg(x + (size_t)b * k + c), acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < KV; ++c) {
+    if (c >= k) break;
+    double v = acc[c];
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) y[(size_t)a * k + c] = v;
+  }
+}
+
+// Zo[i, c] = (R[i, c] - sum_b Z[i, b] w[b, c]) / lambda_p.  Each warp owns 4
+// rows; w is staged in shared memory in column chunks of `sch` (transposed,
+// [c][b]), lanes take 8 consecutive columns.
+constexpr int ZW_ROWS_PER_WARP = 4;
+constexpr int ZW_ROWS = ZW_ROWS_PER_WARP * (AT / 32);
+
+template <int BF16, typename T, typename ACC, int KV>
+__global__ void __launch_bounds__(AT)
+zw_kernel(const void* __restrict__ Zs, int n, int s, const double* __restrict__ w, int k,
+          const T* __restrict__ R, int ldr, double inv_lam, T* __restrict__ Zo, int ldo, int sch,
+          int vec) {
+  extern __shared__ __align__(16) uint8_t zw_smem[];
+  ACC* wsm = reinterpret_cast<ACC*>(zw_smem);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row0 = blockIdx.x * ZW_ROWS + warp * ZW_ROWS_PER_WARP;
+  ACC acc[ZW_ROWS_PER_WARP][KV];
+#pragma unroll
+  for (int r = 0; r < ZW_ROWS_PER_WARP; ++r)
+#pragma unroll
+    for (int c = 0; c < KV; ++c) acc[r][c] = (ACC)0;
+  for (int b0 = 0; b0 < s; b0 += sch) {
+    const int nb = min(sch, s - b0);
+    __syncthreads();
+    // the whole chunk is written (zeros past nb) so no lane reads stale values
+    for (int e = threadIdx.x; e < sch * KV; e += AT) {
+      const int b = e / KV, c = e % KV;
+      wsm[c * sch + b] = (c < k && b < nb) ? (ACC)w[(size_t)(b0 + b) * k + c] : (ACC)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < ZW_ROWS_PER_WARP; ++r) {
+      const int i = row0 + r;
+      if (i >= n) break;
+      for (int bb = lane * 8; bb < nb; bb += 256) {
+        float z[8];
+        load8<BF16>(Zs, (size_t)i * s + b0 + bb, min(8, nb - bb), vec != 0, z);
+#pragma unroll
+        for (int c = 0; c < KV; ++c) {
+          const ACC* wc = wsm + c * sch + bb;
+          ACC a = acc[r][c];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) a = fma((ACC)z[q], wc[q], a);
+          acc[r][c] = a;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < ZW_ROWS_PER_WARP; ++r) {
+    const int i = row0 + r;
+    if (i >= n) break;
+#pragma unroll
+    for (int c = 0; c < KV; ++c) {
+      if (c >= k) break;
+      double v = (double)acc[r][c];
+      for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (lane == 0)
+        Zo[(size_t)i * ldo + c] = (T)(((double)R[(size_t)i * ldr + c] - v) * inv_lam);
+    }
+  }
+}
+
+// U form: t[a, c] = sum_i U[a, i] R[i, c]; one warp per row of U.
+template <typename T>
+__global__ void ur_kernel(const float* __restrict__ U, int n, int s, const T* __restrict__ R,
+                          int k, int ldr, double* __restrict__ t) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= s) return;
+  double acc[KRR_MAX_RHS];
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c) acc[c] = 0.0;
+  for (int i = lane; i < n; i += 32) {
+    double u = (double)U[(size_t)warp * n + i];
+#pragma unroll
+    for (int c = 0; c < KRR_MAX_RHS; ++c)
+      if (c < k) acc[c] = fma(u, (double)R[(size_t)i * ldr + c], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c) {
+    if (c >= k) break;
+    double v = acc[c];
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) t[(size_t)warp * k + c] = v;
+  }
+}
+
+// U form: Zo[i, c] = (R[i, c] - sum_a U[a, i] t[a, c]) / lambda_p; thread per row i.
+template <typename T>
+__global__ void utt_kernel(const float* __restrict__ U, int n, int s, const double* __restrict__ t,
+                           int k, const T* __restrict__ R, int ldr, double inv_lam,
+                           T* __restrict__ Zo, int ldo) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc[KRR_MAX_RHS];
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c) acc[c] = 0.0;
+  for (int a = 0; a < s; ++a) {
+    double u = (double)U[(size_t)a * n + i];
+#pragma unroll
+    for (int c = 0; c < KRR_MAX_RHS; ++c)
+      if (c < k) acc[c] = fma(u, __ldg(&t[(size_t)a * k + c]), acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c)
+    if (c < k) Zo[(size_t)i * ldo + c] = (T)(((double)R[(size_t)i * ldr + c] - acc[c]) * inv_lam);
+}
+
+struct ApplyPlan {
+  int colblocks, nchunk, rpc, kv, sch;
+  size_t zw_smem;
+};
+
+template <typename ACC>
+ApplyPlan plan(int n, int s, int k) {
+  ApplyPlan p;
+  p.kv = kv_of(k);
+  p.colblocks = (s + AT * 8 - 1) / (AT * 8);
+  int nch = (4 * sm_count() + p.colblocks - 1) / p.colblocks;
+  const int maxch = (n + ZT_ROWS - 1) / ZT_ROWS;
+  if (nch > maxch) nch = maxch;
+  if (nch < 1) nch = 1;
+  p.rpc = (n + nch - 1) / nch;
+  p.rpc = (p.rpc + ZT_ROWS - 1) / ZT_ROWS * ZT_ROWS;
+  p.nchunk = (n + p.rpc - 1) / p.rpc;
+  // w chunk in shared memory: at most 96 KiB, a multiple of 256 columns
+  int sch = (int)((96 * 1024) / (p.kv * sizeof(ACC)));
+  sch = sch / 256 * 256;
+  if (sch < 256) sch = 256;
+  const int s256 = (s + 255) / 256 * 256;
+  p.sch = sch < s256 ? sch : s256;
+  p.zw_smem = (size_t)p.sch * p.kv * sizeof(ACC);
+  return p;
+}
+
+template <int BF16, typename T, typename ACC, int KV>
+void apply_zl(cudaStream_t st, const Precond& pc, const ApplyPlan& pl, const T* R, int k, int ldr,
+              T* Zo, int ldo, double* t1, double* t2, void* part) {
+  const int n = pc.n, s = pc.s;
+  const int vec = (s % 8 == 0) ? 1 : 0;
+  zt_kernel<BF16, T, ACC, KV><<<dim3(pl.colblocks, pl.nchunk), AT, 0, st>>>(
+      pc.Z.p, n, s, R, ldr, k, reinterpret_cast<ACC*>(part), pl.rpc, vec);
+  KRR_CHECK_LAUNCH();
+  const int sb = (int)std::min<size_t>(((size_t)s * k + 255) / 256, (size_t)4 * sm_count());
+  sum_kernel<ACC><<<sb, 256, 0, st>>>(reinterpret_cast<const ACC*>(part), pl.nchunk, s, KV, k, t1);
+  KRR_CHECK_LAUNCH();
+  const int tb = (s * 32 + AT - 1) / AT;
+  trmv_kernel<0, KV><<<tb, AT, 0, st>>>(reinterpret_cast<const double*>(pc.Linv.p), s, t1, k, t2);
+  KRR_CHECK_LAUNCH();
+  trmv_kernel<1, KV><<<tb, AT, 0, st>>>(reinterpret_cast<const double*>(pc.LinvT.p), s, t2, k, t1);
+  KRR_CHECK_LAUNCH();
+  auto kern = zw_kernel<BF16, T, ACC, KV>;
+  if (pl.zw_smem > 48 * 1024)
+    KRR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)pl.zw_smem));
+  kern<<<(n + ZW_ROWS - 1) / ZW_ROWS, AT, pl.zw_smem, st>>>(pc.Z.p, n, s, t1, k, R, ldr,
+                                                            1.0 / pc.lam_p, Zo, ldo, pl.sch, vec);
+  KRR_CHECK_LAUNCH();
+}
+
+template <typename T, typename ACC, int KV>
+void apply_zl_kv(cudaStream_t st, const Precond& pc, const ApplyPlan& pl, const T* R, int k,
+                 int ldr, T* Zo, int ldo, double* t1, double* t2, void* part) {
+  if (pc.z_bf16)
+    apply_zl<1, T, ACC, KV>(st, pc, pl, R, k, ldr, Zo, ldo, t1, t2, part);
+  else
+    apply_zl<0, T, ACC, KV>(st, pc, pl, R, k, ldr, Zo, ldo, t1, t2, part);
+}
+
+}  // namespace
+
+size_t apply_part_elems(int n, int s, int k) {
+  // in doubles (large enough for either accumulator type)
+  ApplyPlan p = plan<double>(n, s, k);
+  return (size_t)p.nchunk * s * p.kv;
+}
+
+template <typename T>
+void launch_apply(cudaStream_t st, const Precond& pc, const T* R, int k, int ldr, T* Zo,
+                  int ldo, double* t1, double* t2, double* part) {
+  const int n = pc.n, s = pc.s;
+  const double inv_lam = 1.0 / pc.lam_p;
+  if (pc.form == KRR_APPLY_U) {
+    const float* U = reinterpret_cast<const float*>(pc.U.p);
+    ur_kernel<T><<<(s + 7) / 8, 256, 0, st>>>(U, n, s, R, k, ldr, t1);
+    KRR_CHECK_LAUNCH();
+    utt_kernel<T><<<(n + 127) / 128, 128, 0, st>>>(U, n, s, t1, k, R, ldr, inv_lam, Zo, ldo);
+    KRR_CHECK_LAUNCH();
+    return;
+  }
+  // FP32 slab sums for single-precision vectors, FP64 for the FP64 solve
+  typedef typename std::conditional<std::is_same<T, float>::value, float, double>::type ACC;
+  const ApplyPlan pl = plan<ACC>(n, s, k);
+  switch (pl.kv) {
+    case 1: apply_zl_kv<T, ACC, 1>(st, pc, pl, R, k, ldr, Zo, ldo, t1, t2, part); break;
+    case 2: apply_zl_kv<T, ACC, 2>(st, pc, pl, R, k, ldr, Zo, ldo, t1, t2, part); break;
+    case 4: apply_zl_kv<T, ACC, 4>(st, pc, pl, R, k, ldr, Zo, ldo, t1, t2, part); break;
+    case 8: apply_zl_kv<T, ACC, 8>(st, pc, pl, R, k, ldr, Zo, ldo, t1, t2, part); break;
+    case 12: apply_zl_kv<T, ACC, 12>(st, pc, pl, R, k, ldr, Zo, ldo, t1, t2, part); break;
+    default: apply_zl_kv<T, ACC, 16>(st, pc, pl, R, k, ldr, Zo, ldo, t1, t2, part); break;
+  }
+}
+
+template void launch_apply<float>(cudaStream_t, const Precond&, const float*, int, int, float*,
+                                  int, double*, double*, double*);
+template void launch_apply<double>(cudaStream_t, const Precond&, const double*, int, int,
+                                   double*, int, double*, double*, double*);
+
+}  // namespace krr

@@ -336,6 +336,29 @@ colnorm2_kernel(const T* __restrict__ a, int n, int k, int lda, double* out, dou
   for (int c = 0; c < k; ++c) out[c] = tot[c];
 }
 
+// Column mean in two deterministic passes: per-slab column sums, then the
+// slabs added in order.
+constexpr int MEAN_ROWS = 128;
+
+__global__ void colsum_slab_kernel(const float* __restrict__ X, int n, int ld, int d,
+                                   double* __restrict__ part) {
+  const int r0 = blockIdx.x * MEAN_ROWS, r1 = min(n, r0 + MEAN_ROWS);
+  for (int t = threadIdx.x; t < d; t += blockDim.x) {
+    double s = 0.0;
+    for (int i = r0; i < r1; ++i) s += (double)X[(size_t)i * ld + t];
+    part[(size_t)blockIdx.x * d + t] = s;
+  }
+}
+
+__global__ void colmean_finish_kernel(const double* __restrict__ part, int nslab, int n, int d,
+                                      double* __restrict__ mu) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d) return;
+  double s = 0.0;
+  for (int b = 0; b < nslab; ++b) s += part[(size_t)b * d + t];
+  mu[t] = s / (double)n;
+}
+
 int ew_blocks(size_t total) {
   size_t b = (total + 255) / 256;
   size_t cap = (size_t)8 * sm_count();
@@ -393,6 +416,15 @@ void launch_cg_update_p(cudaStream_t st, CgScalars* sc, T* P, const T* Z, int n,
 
 void launch_cg_tail(cudaStream_t st, CgScalars* sc, unsigned long long cond) {
   cg_tail_kernel<<<1, 1, 0, st>>>(sc, (cudaGraphConditionalHandle)cond);
+  KRR_CHECK_LAUNCH();
+}
+
+void launch_colmean(cudaStream_t st, const float* X, int n, int ld, int d, double* mu,
+                    double* slab) {
+  const int nslab = (n + MEAN_ROWS - 1) / MEAN_ROWS;
+  colsum_slab_kernel<<<nslab, 128, 0, st>>>(X, n, ld, d, slab);
+  KRR_CHECK_LAUNCH();
+  colmean_finish_kernel<<<(d + 127) / 128, 128, 0, st>>>(slab, nslab, n, d, mu);
   KRR_CHECK_LAUNCH();
 }
 

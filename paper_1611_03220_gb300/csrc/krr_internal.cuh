@@ -157,6 +157,10 @@ void launch_cg_update_p(cudaStream_t st, CgScalars* sc, T* P, const T* Z, int n,
 // when `cond` is nonzero (a cudaGraphConditionalHandle).
 void launch_cg_tail(cudaStream_t st, CgScalars* sc, unsigned long long cond);
 
+// mu[t] = mean_i X[i, t] in FP64, deterministic (slab scratch: ceil(n/128) x d doubles)
+void launch_colmean(cudaStream_t st, const float* X, int n, int ld, int d, double* mu,
+                    double* slab);
+
 // Elementwise helpers (row-major n x k blocks)
 template <typename A, typename B>
 void launch_convert(cudaStream_t st, const A* a, int n, int k, int lda, B* b, int ldb,

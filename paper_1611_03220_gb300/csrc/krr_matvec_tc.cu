@@ -407,16 +407,6 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 }
 
 // ------------------------------------------------------------ helpers ----
-// Column mean of X (FP64), one thread per coordinate.
-__global__ void colmean_kernel(const float* __restrict__ X, int n, int ld, int d,
-                               double* __restrict__ mu) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= d) return;
-  double s = 0.0;
-  for (int i = 0; i < n; ++i) s += (double)X[(size_t)i * ld + t];
-  mu[t] = s / (double)n;
-}
-
 // xh = bf16(scale (x - mu)) padded to n_pad x kp, nh = ||xh||^2, ra = exp2(-nh/2).
 __global__ void prep_rows_kernel(const float* __restrict__ X, int n, int ld, int d,
                                  const double* __restrict__ mu, double scale, int n_pad, int kp,
@@ -619,8 +609,8 @@ void tc_prepare(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int
       t.sigma == sigma && t.rows_same)
     return;
   ensure(t.mu, (size_t)d * sizeof(double));
-  colmean_kernel<<<(d + 127) / 128, 128, 0, st>>>(X, n, ldx, d, (double*)t.mu.p);
-  KRR_CHECK_LAUNCH();
+  ensure(t.w, (size_t)((n + 127) / 128) * d * sizeof(double));  // w doubles as the slab scratch
+  launch_colmean(st, X, n, ldx, d, (double*)t.mu.p, (double*)t.w.p);
   prep_operand(t.cols, st, X, n, ldx, d, (const double*)t.mu.p, scale);
   ensure(t.scal, 16);
   KRR_CUDA(cudaMemsetAsync(t.scal.p, 0, 16, st));

@@ -411,165 +411,6 @@ form_u_kernel(const double* __restrict__ Linv, const void* __restrict__ Zs, int 
   }
 }
 
-// -------------------------------------------------------------- apply ----
-// t[col, c] = sum_i Zs[i, col] R[i, c]  (partial per row chunk, FP64)
-constexpr int ZT_THREADS = 256, ZT_CPT = 2;
-
-template <int BF16, typename T>
-__global__ void __launch_bounds__(ZT_THREADS)
-zt_r_kernel(const void* __restrict__ Zs, int n, int s, const T* __restrict__ R, int k, int ldr,
-            double* __restrict__ part, int rows_per_chunk) {
-  const int col0 = (blockIdx.x * ZT_THREADS + threadIdx.x) * ZT_CPT;
-  const int r0 = blockIdx.y * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
-  double acc[ZT_CPT][KRR_MAX_RHS];
-#pragma unroll
-  for (int q = 0; q < ZT_CPT; ++q)
-#pragma unroll
-    for (int c = 0; c < KRR_MAX_RHS; ++c) acc[q][c] = 0.0;
-  if (col0 < s) {
-    for (int i = r0; i < r1; ++i) {
-      double z[ZT_CPT];
-#pragma unroll
-      for (int q = 0; q < ZT_CPT; ++q)
-        z[q] = (col0 + q < s) ? (double)zload<BF16>(Zs, (size_t)i * s + col0 + q) : 0.0;
-#pragma unroll
-      for (int c = 0; c < KRR_MAX_RHS; ++c) {
-        if (c < k) {
-          double rv = (double)R[(size_t)i * ldr + c];
-#pragma unroll
-          for (int q = 0; q < ZT_CPT; ++q) acc[q][c] = fma(z[q], rv, acc[q][c]);
-        }
-      }
-    }
-  }
-  double* out = part + (size_t)blockIdx.y * s * k;
-#pragma unroll
-  for (int q = 0; q < ZT_CPT; ++q) {
-    if (col0 + q >= s) continue;
-#pragma unroll
-    for (int c = 0; c < KRR_MAX_RHS; ++c)
-      if (c < k) out[(size_t)(col0 + q) * k + c] = acc[q][c];
-  }
-}
-
-__global__ void sum_chunks_kernel(const double* __restrict__ part, int nchunk, size_t len,
-                                  double* __restrict__ out) {
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len;
-       e += (size_t)gridDim.x * blockDim.x) {
-    double v = 0.0;
-    for (int c = 0; c < nchunk; ++c) v += part[(size_t)c * len + e];
-    out[e] = v;
-  }
-}
-
-// y[a, c] = sum_b A[a, b] x[b, c] over b in [lo(a), hi(a)) for a triangular A
-// (lower: b <= a; upper: b >= a); one warp per row.
-template <int UPPER>
-__global__ void trmv_kernel(const double* __restrict__ A, int s, const double* __restrict__ x,
-                            int k, double* __restrict__ y) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= s) return;
-  const int a = warp;
-  const int lo = UPPER ? a : 0, hi = UPPER ? s : a + 1;
-  double acc[KRR_MAX_RHS];
-#pragma unroll
-  for (int c = 0; c < KRR_MAX_RHS; ++c) acc[c] = 0.0;
-  for (int b = lo + lane; b < hi; b += 32) {
-    double av = A[(size_t)a * s + b];
-#pragma unroll
-    for (int c = 0; c < KRR_MAX_RHS; ++c)
-      if (c < k) acc[c] = fma(av, x[(size_t)b * k + c], acc[c]);
-  }
-#pragma unroll
-  for (int c = 0; c < KRR_MAX_RHS; ++c) {
-    if (c >= k) break;
-    double v = acc[c];
-    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) y[(size_t)a * k + c] = v;
-  }
-}
-
-// Zo[i, c] = (R[i, c] - sum_b Zs[i, b] w[b, c]) / lam_p; one warp per row.
-template <int BF16, typename T>
-__global__ void zw_kernel(const void* __restrict__ Zs, int n, int s, const double* __restrict__ w,
-                          int k, const T* __restrict__ R, int ldr, double inv_lam,
-                          T* __restrict__ Zo, int ldo) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= n) return;
-  const int i = warp;
-  double acc[KRR_MAX_RHS];
-#pragma unroll
-  for (int c = 0; c < KRR_MAX_RHS; ++c) acc[c] = 0.0;
-  for (int b = lane; b < s; b += 32) {
-    double z = (double)zload<BF16>(Zs, (size_t)i * s + b);
-#pragma unroll
-    for (int c = 0; c < KRR_MAX_RHS; ++c)
-      if (c < k) acc[c] = fma(z, __ldg(&w[(size_t)b * k + c]), acc[c]);
-  }
-#pragma unroll
-  for (int c = 0; c < KRR_MAX_RHS; ++c) {
-    if (c >= k) break;
-    double v = acc[c];
-    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) Zo[(size_t)i * ldo + c] = (T)(((double)R[(size_t)i * ldr + c] - v) * inv_lam);
-  }
-}
-
-// U form: t[a, c] = sum_i U[a, i] R[i, c]; one warp per row of U.
-template <typename T>
-__global__ void ur_kernel(const float* __restrict__ U, int n, int s, const T* __restrict__ R,
-                          int k, int ldr, double* __restrict__ t) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= s) return;
-  double acc[KRR_MAX_RHS];
-#pragma unroll
-  for (int c = 0; c < KRR_MAX_RHS; ++c) acc[c] = 0.0;
-  for (int i = lane; i < n; i += 32) {
-    double u = (double)U[(size_t)warp * n + i];
-#pragma unroll
-    for (int c = 0; c < KRR_MAX_RHS; ++c)
-      if (c < k) acc[c] = fma(u, (double)R[(size_t)i * ldr + c], acc[c]);
-  }
-#pragma unroll
-  for (int c = 0; c < KRR_MAX_RHS; ++c) {
-    if (c >= k) break;
-    double v = acc[c];
-    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) t[(size_t)warp * k + c] = v;
-  }
-}
-
-// U form: Zo[i, c] = (R[i, c] - sum_a U[a, i] t[a, c]) / lam_p; thread per row i.
-template <typename T>
-__global__ void utt_kernel(const float* __restrict__ U, int n, int s, const double* __restrict__ t,
-                           int k, const T* __restrict__ R, int ldr, double inv_lam,
-                           T* __restrict__ Zo, int ldo) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double acc[KRR_MAX_RHS];
-#pragma unroll
-  for (int c = 0; c < KRR_MAX_RHS; ++c) acc[c] = 0.0;
-  for (int a = 0; a < s; ++a) {
-    double u = (double)U[(size_t)a * n + i];
-#pragma unroll
-    for (int c = 0; c < KRR_MAX_RHS; ++c)
-      if (c < k) acc[c] = fma(u, __ldg(&t[(size_t)a * k + c]), acc[c]);
-  }
-#pragma unroll
-  for (int c = 0; c < KRR_MAX_RHS; ++c)
-    if (c < k) Zo[(size_t)i * ldo + c] = (T)(((double)R[(size_t)i * ldr + c] - acc[c]) * inv_lam);
-}
-
-int apply_chunks(int n, int s) {
-  int colblocks = (s + ZT_THREADS * ZT_CPT - 1) / (ZT_THREADS * ZT_CPT);
-  int target = 2 * sm_count();
-  int nch = (target + colblocks - 1) / colblocks;
-  int maxch = (n + 63) / 64;
-  if (nch > maxch) nch = maxch;
-  if (nch < 1) nch = 1;
-  return nch;
-}
-
 }  // namespace
 
 int gram_chunks(int n, int s) {
@@ -659,52 +500,5 @@ void launch_form_u(cudaStream_t st, const double* Linv, const void* Zs, int bf16
   KRR_CHECK_LAUNCH();
 }
 
-size_t apply_part_elems(int n, int s, int k) {
-  return (size_t)apply_chunks(n, s) * s * k;
-}
-
-template <typename T>
-void launch_apply(cudaStream_t st, const Precond& pc, const T* R, int k, int ldr, T* Zo,
-                  int ldo, double* t1, double* t2, double* part) {
-  const int n = pc.n, s = pc.s;
-  const double inv_lam = 1.0 / pc.lam_p;
-  const int wpb = 8;  // warps per block for warp-per-row kernels
-  if (pc.form == KRR_APPLY_U) {
-    const float* U = reinterpret_cast<const float*>(pc.U.p);
-    ur_kernel<T><<<(s + wpb - 1) / wpb, wpb * 32, 0, st>>>(U, n, s, R, k, ldr, t1);
-    KRR_CHECK_LAUNCH();
-    utt_kernel<T><<<(n + 127) / 128, 128, 0, st>>>(U, n, s, t1, k, R, ldr, inv_lam, Zo, ldo);
-    KRR_CHECK_LAUNCH();
-    return;
-  }
-  const int nch = apply_chunks(n, s);
-  int rpc = (n + nch - 1) / nch;
-  dim3 g1((s + ZT_THREADS * ZT_CPT - 1) / (ZT_THREADS * ZT_CPT), nch);
-  if (pc.z_bf16)
-    zt_r_kernel<1, T><<<g1, ZT_THREADS, 0, st>>>(pc.Z.p, n, s, R, k, ldr, part, rpc);
-  else
-    zt_r_kernel<0, T><<<g1, ZT_THREADS, 0, st>>>(pc.Z.p, n, s, R, k, ldr, part, rpc);
-  KRR_CHECK_LAUNCH();
-  sum_chunks_kernel<<<(s * k + 255) / 256, 256, 0, st>>>(part, nch, (size_t)s * k, t1);
-  KRR_CHECK_LAUNCH();
-  const double* Li = reinterpret_cast<const double*>(pc.Linv.p);
-  const double* LiT = reinterpret_cast<const double*>(pc.LinvT.p);
-  trmv_kernel<0><<<(s + wpb - 1) / wpb, wpb * 32, 0, st>>>(Li, s, t1, k, t2);
-  KRR_CHECK_LAUNCH();
-  trmv_kernel<1><<<(s + wpb - 1) / wpb, wpb * 32, 0, st>>>(LiT, s, t2, k, t1);
-  KRR_CHECK_LAUNCH();
-  if (pc.z_bf16)
-    zw_kernel<1, T><<<(n + wpb - 1) / wpb, wpb * 32, 0, st>>>(pc.Z.p, n, s, t1, k, R, ldr,
-                                                               inv_lam, Zo, ldo);
-  else
-    zw_kernel<0, T><<<(n + wpb - 1) / wpb, wpb * 32, 0, st>>>(pc.Z.p, n, s, t1, k, R, ldr,
-                                                               inv_lam, Zo, ldo);
-  KRR_CHECK_LAUNCH();
-}
-
-template void launch_apply<float>(cudaStream_t, const Precond&, const float*, int, int, float*,
-                                  int, double*, double*, double*);
-template void launch_apply<double>(cudaStream_t, const Precond&, const double*, int, int,
-                                   double*, int, double*, double*, double*);
 
 }  // namespace krr

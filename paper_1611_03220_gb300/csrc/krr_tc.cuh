@@ -30,6 +30,29 @@ struct TcState {
   bool err_zeroed = false;
 };
 
+// High-precision product state (krr_matvec_hp.cu): four base-512 fixed-point
+// digit slices of the centred, scaled points (BF16, (4 n_pad) x 64), per-row
+// (a_hi, a_lo, 2^(E-8)), per-call column records and partial sums.
+struct HpState {
+  DevBuf mu, slab, slices, rowd, cold, part, err;
+  const float* src = nullptr;
+  int n = 0, ld = 0, d = 0, n_pad = 0;
+  double sigma = 0.0;
+  bool ready = false;
+  CUtensorMap map_a;
+  CUtensorMap map_b;
+};
+
+bool hp_supported(int d);
+void hp_prepare(HpState& t, cudaStream_t st, const float* X, int n, int ldx, int d, double sigma);
+void hp_reserve(HpState& t, cudaStream_t st, int k);
+// Q = K(X, X) V + shift V with V, Q in FP64 and K_ij to ~1e-9 relative (d <= 64).
+void hp_matvec(HpState& t, cudaStream_t st, const float* X, int n, int ldx, int d, double sigma,
+               double shift, const double* V, int k, int ldv, double* Q, int ldq);
+void hp_clear_error(HpState& t, cudaStream_t st);
+int hp_error(HpState& t, cudaStream_t st);
+void hp_release(HpState& t);
+
 // Prepare the operands for the training set X (n x d, ldx) at bandwidth sigma.
 void tc_prepare(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int d, double sigma);
 // Q = K(X, X) V + shift V through the tensor cores (Xr must equal Xc).
