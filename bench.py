@@ -52,6 +52,11 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="override n (smaller instance)")
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--profile", default=None, choices=["step", "bf16", "hp", "fp32", "apply"],
+                    help="short run for ncu: 'step' = one mixed and one FP32 solve of "
+                         "--profile-iters PCG iterations with the host-driven loop (every "
+                         "launch listed); otherwise 3 launches of that kernel product / apply")
+    ap.add_argument("--profile-iters", type=int, default=12)
     return ap.parse_args()
 
 
@@ -160,6 +165,47 @@ def run_reference(args, rank, world):
         "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+# --------------------------------------------------------------- profile --
+def run_profile(args):
+    """Short, launch-bounded runs for Nsight Compute (no timing is reported)."""
+    import torch
+    from paper_1611_03220_gb300 import build
+    build()
+    from paper_1611_03220_gb300 import _krr as K
+
+    n = args.n or ks.CONFIGS[2]
+    P = ks.make_config(2, n=n)
+    X = torch.from_numpy(P.X).cuda()
+    Y = torch.from_numpy(P.Y).cuda()
+    W = torch.from_numpy(P.W).cuda()
+    b = torch.from_numpy(P.b).cuda()
+    h = K.Handle()
+    if args.profile == "step":
+        C = torch.zeros_like(Y)
+        for prec in ("mixed", "fp32"):
+            o = K.default_opts(tol=P.tol, precision=prec, max_iter=args.profile_iters,
+                               use_graph=0)
+            rep = K.krr_pcg_solve(h, X, P.sigma, P.lam, W, b, Y, C, o, check=False)
+            torch.cuda.synchronize()
+            print(prec, rep["status"], rep["iters"], rep["matvecs"], flush=True)
+    elif args.profile == "apply":
+        Z = torch.empty((n, P.s), dtype=torch.float32, device="cuda")
+        K.krr_rff_features(h, X, W, b, Z)
+        K.krr_precond_setup(h, Z, P.lam, "zl", z_bf16=True)
+        R = torch.randn((n, 1), dtype=torch.float64, device="cuda")
+        Zo = torch.empty_like(R)
+        for _ in range(3):
+            K.krr_precond_apply(h, R, Zo)
+    else:
+        dt = torch.float64 if args.profile == "hp" else torch.float32
+        V = torch.randn((n, 1), dtype=dt, device="cuda")
+        Q = torch.empty_like(V)
+        for _ in range(3):
+            K.krr_kernel_matvec(h, X, X, P.sigma, P.lam, V, Q, args.profile)
+    torch.cuda.synchronize()
+    h.close()
+
+
 # ----------------------------------------------------------------- ours ---
 def run_ours(args, rank, world, local):
     import torch
@@ -183,7 +229,9 @@ def run_ours(args, rank, world, local):
     F = torch.zeros((M_TEST, 1), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     h = K.Handle()
-    opts = K.default_opts(tol=P.tol, precision="mixed")
+    # Algorithm 1 needs a few thousand PCG iterations on this workload (the
+    # preconditioner is weak here, see the plain-CG entry), hence the budget.
+    opts = K.default_opts(tol=P.tol, precision="mixed", max_iter=20000, max_outer=60)
 
     def step():
         C.zero_()
@@ -277,6 +325,20 @@ def run_ours(args, rank, world, local):
         fp32 = {"ms": (time.perf_counter() - t0) * 1e3, "status": r32["status"],
                 "iters": r32["iters"][0], "rel_res_fp64_check": r32["rel_res"][0]}
 
+    # ---------------------------------- plain CG (M = I, Table 4's comparator)
+    plain_cg = {}
+    for prec in ("mixed",) + (() if args.no_fp32 else ("fp32",)):
+        Cc = torch.zeros_like(Y)
+        oc = K.default_opts(tol=P.tol, precision=prec, precond=0)
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc = K.krr_pcg_solve(h, X, P.sigma, P.lam, W, b, Y, Cc, oc, check=False)
+        torch.cuda.synchronize()
+        plain_cg[prec] = {"ms": (time.perf_counter() - t0) * 1e3, "status": rc["status"],
+                          "iters": rc["iters"][0], "outer_steps": rc["outer_steps"],
+                          "rel_res_fp64_check": rc["rel_res"][0]}
+
     # ------------------------------------------------ end to end (host) ----
     Xh, Yh, Wh, bh = P.X, P.Y, P.W, P.b
     Xteh = P.Xte
@@ -310,7 +372,7 @@ def run_ours(args, rank, world, local):
                       "outer_steps": rep["outer_steps"], "matvecs": rep["matvecs"],
                       "rel_res_fp64": rep["rel_res"][0], "ms_setup": rep["ms_setup"],
                       "ms_solve": rep["ms_solve"], "step_ms_all": times},
-            "fp32": fp32, "kernel_matvec": mv, "roofline": roofline,
+            "fp32": fp32, "plain_cg": plain_cg, "kernel_matvec": mv, "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -329,6 +391,9 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.profile:
+        run_profile(args)
         return
     run_ours(args, rank, world, local)
 

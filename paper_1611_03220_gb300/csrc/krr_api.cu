@@ -481,7 +481,7 @@ krr_status solve_plain(krr_handle* h, const SolveArgs& a, int prec, krr_report* 
     double* xd = wsT<double>(h, "v_xd", nk);
     launch_convert<T, double>(st, x, n, k, k, xd, k, one2);
     matvec_dispatch(h, st, a.X, n, a.ldx, a.X, n, a.ldx, a.d, a.sigma, a.lambda, xd, k, k, AX, k,
-                    prec == KRR_FP64 ? KRR_FP64 : (prec == KRR_FP32 ? KRR_FP64 : KRR_HP));
+                    prec == KRR_FP64 ? KRR_FP64 : KRR_HP);
     ++*matvecs;
     launch_sub_d(st, Yc, k, AX, k, n, k, Rd, k);
     double rr[KRR_MAX_RHS];

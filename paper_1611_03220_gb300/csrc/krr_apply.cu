@@ -110,16 +110,27 @@ zt_kernel(const void* __restrict__ Zs, int n, int s, const T* __restrict__ R, in
 }
 
 // t[col, c] = sum over chunks (FP64), for c < k (t has leading dimension k).
+// A CTA owns 32 consecutive (col, c) entries of the partial rows; its 8
+// warps take the chunks round-robin (coalesced 128-byte reads), and the 8
+// per-warp sums are added in a fixed order.
 template <typename P>
-__global__ void sum_kernel(const P* __restrict__ part, int nchunk, int s, int kv, int k,
-                           double* __restrict__ t) {
-  const size_t total = (size_t)s * k;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const size_t col = e / k, c = e % k;
-    double v = 0.0;
-    for (int ch = 0; ch < nchunk; ++ch) v += (double)part[((size_t)ch * s + col) * kv + c];
-    t[e] = v;
+__global__ void __launch_bounds__(256)
+sum_kernel(const P* __restrict__ part, int nchunk, int s, int kv, int k, double* __restrict__ t) {
+  __shared__ double red[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const size_t row_len = (size_t)s * kv;
+  const size_t e = (size_t)blockIdx.x * 32 + lane;  // index into a partial row
+  double v = 0.0;
+  if (e < row_len)
+    for (int ch = w; ch < nchunk; ch += 8) v += (double)part[(size_t)ch * row_len + e];
+  red[w][lane] = v;
+  __syncthreads();
+  if (w == 0 && e < row_len) {
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc += red[q][lane];
+    const size_t col = e / kv, c = e % kv;
+    if ((int)c < k) t[col * k + c] = acc;
   }
 }
 
@@ -294,7 +305,7 @@ void apply_zl(cudaStream_t st, const Precond& pc, const ApplyPlan& pl, const T* 
   zt_kernel<BF16, T, ACC, KV><<<dim3(pl.colblocks, pl.nchunk), AT, 0, st>>>(
       pc.Z.p, n, s, R, ldr, k, reinterpret_cast<ACC*>(part), pl.rpc, vec);
   KRR_CHECK_LAUNCH();
-  const int sb = (int)std::min<size_t>(((size_t)s * k + 255) / 256, (size_t)4 * sm_count());
+  const int sb = (int)(((size_t)s * KV + 31) / 32);
   sum_kernel<ACC><<<sb, 256, 0, st>>>(reinterpret_cast<const ACC*>(part), pl.nchunk, s, KV, k, t1);
   KRR_CHECK_LAUNCH();
   const int tb = (s * 32 + AT - 1) / AT;

@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/krr.h"
+#include "krr.h"
 
 namespace krr {
 

@@ -6,26 +6,31 @@
 // Gaussian kernel of its experiments (Section 5); K is never written.
 //
 // Arithmetic.  With c = log2(e) / (2 sigma^2) and xh_i = bf16(sqrt(2c)(x_i - mu))
-// (mu the column mean of the column set; the kernel is shift invariant),
+// (mu the column mean; the kernel is shift invariant),
 //   -c ||x_i - x_j||^2  ~=  xh_i.xh_j - nh_i/2 - nh_j/2,   nh_i = ||xh_i||^2,
 // so   K_ij = exp2(xh_i.xh_j) * ra_i * ra_j  with ra_i = exp2(-nh_i / 2).
 // The tensor core forms S_ij = xh_i.xh_j (BF16 x BF16 products are exact in
-// FP32; FP32 accumulation in TMEM), the epilogue evaluates exp2 on the MUFU
-// and contracts against w_j = ra_j v_j, and ra_i scales the finished row
-// sum.  This is the Gaussian kernel of the BF16-rounded points xh: the
-// product stays a (symmetric positive semi-definite) kernel matrix, and the
-// rounding error is what the outer refinement removes.  exp2(S) must not
-// overflow: the host requires max nh <= 120.
+// FP32; FP32 accumulation in TMEM), the epilogue evaluates exp2(S_ij) and
+// contracts against w_j = ra_j v_j, and ra_i scales the finished row sum.
+// This is the Gaussian kernel of the BF16-rounded points xh: the product
+// stays a (symmetric positive semi-definite) kernel matrix, and the rounding
+// error is what the outer refinement removes.  exp2(S) must not overflow:
+// the host requires max nh <= 120.
 //
-// Structure (one persistent CTA per SM, 320 threads):
+// exp2 is split between two pipes: most entries use the MUFU ex2, and EMU of
+// every 32 use a degree-5 polynomial for 2^f on [-1/2, 1/2] on the FMA pipe
+// (coefficients fitted for this file: near-minimax in relative error,
+// 7.5e-8 in exact arithmetic) with the integer part added to the exponent.
+//
+// Structure (one persistent CTA per SM):
 //   warp 0     TMA producer: per 128 x 256 tile, K-blocks of 64 BF16 of the
 //              row tile (A) and the column tile (B) into a ring of NS stages
 //              (128-byte swizzle), plus the tile's w block by bulk copy.
 //   warp 1     allocates 512 TMEM columns (two 128 x 256 FP32 accumulators)
 //              and one thread issues tcgen05.mma (M=128, N=256, K=16).
-//   warps 2-9  epilogue: tcgen05.ld 32 columns at a time, ex2, FMA with w.
-//              Warp w reads TMEM lanes 32*(w%4)..+31 (its row quadrant) and
-//              columns 128*((w-2)/4)..+127.
+//   warps 2..  NEPI epilogue warps: warp w reads TMEM lanes 32*(w%4)..+31
+//              (its row quadrant) and one of NEPI/4 column groups; each
+//              thread keeps CH independent accumulator chains per RHS.
 // Work items are (row tile, column chunk) pairs dealt round-robin; each item
 // writes one partial row sum per chunk, and a second kernel adds the chunks
 // in FP64, applies ra_i and the shift.  Every mbarrier wait is bounded: on
@@ -37,187 +42,97 @@
 #include <cstring>
 
 #include "krr_tc.cuh"
+#include "krr_tc_ptx.cuh"
 
 namespace krr {
 namespace {
 
+using namespace ptx;
+
 constexpr int BM = 128;
 constexpr int BN = 256;
+constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+constexpr int PAD = BM / gcd_c(BM, BN) * BN;  // rows are padded to a multiple of lcm(BM, BN)
 constexpr int BK = 64;
 constexpr int UK = 16;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int NUM_EPI = 8;
-constexpr int THREADS = 32 * (2 + NUM_EPI);
 constexpr int TMEM_COLS = 512;
-constexpr uint32_t WAIT_LIMIT = 1u << 24;
+constexpr uint32_t IDESC = idesc_bf16(BM, BN);
 
-constexpr uint32_t IDESC = (1u << 4)                       // D: FP32
-                           | (1u << 7)                     // A: BF16
-                           | (1u << 10)                    // B: BF16
-                           | ((uint32_t)(BN >> 3) << 17)   // N
-                           | ((uint32_t)(BM >> 4) << 24);  // M
+// Per-RHS-width configuration: epilogue warps, w-ring slots, accumulator
+// chains, FMA-pipe exponentials per 32 entries.  Chosen by a sweep at
+// n = 65536, d = 64 (tile width 128/192/256, 8/12/16 epilogue warps, 0/2/4
+// FMA-pipe exponentials per 32, 2/4/8 chains): the epilogue is issue- and
+// latency-bound, so moving exponentials to the FMA pipe costs more issue
+// slots than it saves MUFU cycles and EMU stays 0.
+template <int KV>
+struct Cfg {
+  static constexpr int NEPI = KV == 1 ? 16 : 8;
+  static constexpr int NW = KV <= 12 ? 4 : 3;
+  static constexpr int CH = KV <= 4 ? 2 : 1;
+  static constexpr int EMU = 0;
+  static constexpr int THREADS = 32 * (2 + NEPI);
+  static constexpr int COLS = BN / (NEPI / 4);  // columns per epilogue warp
+};
+constexpr int NS_MAX = 4;
 
 struct TcParams {
   int n_rt, n_ct, nchunk, cpc, nkb;
   int n_rpad;
+  int a_res;        // 1: one K-block, the row tile stays in shared memory per item
+  int ns;           // stages in the ring (<= NS_MAX)
   const float* w;   // n_ct*BN x KV
   float* part;      // nchunk x n_rpad x KV
   int* err;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(a), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait; false (and the CTA abort flag set) when the limit is hit.
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag,
-                                          int* err) {
-  for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
-    if (mbar_try(a, parity)) return true;
-    if ((it & 1023u) == 1023u && *abort_flag) return false;
-  }
-  *abort_flag = 1;
-  atomicOr(err, 1);
-  return false;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int x, int y,
-                                            uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"((uint64_t)tm), "r"(x), "r"(y), "r"(mbar)
-      : "memory");
-}
-
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
-                                          uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-      "l"((uint64_t)src), "r"(bytes), "r"(mbar)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
-  d |= (uint64_t)1 << 46;            // descriptor version
-  d |= (uint64_t)2 << 61;            // 128-byte swizzle
-  return d;
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
-      "l"(a), "l"(b), "r"(IDESC), "r"(accum)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-      : "memory");
-}
-
-__device__ __forceinline__ void fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-__device__ __forceinline__ float ex2(float x) {
+__device__ __forceinline__ float ex2_mufu(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 
-__device__ __forceinline__ void epi_bar() {
-  asm volatile("bar.sync 1, %0;" ::"n"(NUM_EPI * 32) : "memory");
+// 2^x on the FMA pipe: x = n + f with n = rint(x) (through the 1.5 * 2^23
+// rounding constant), f in [-1/2, 1/2], p(f) ~ 2^f, n added to the exponent.
+__device__ __forceinline__ float ex2_fma(float x) {
+  x = fmaxf(x, -125.f);
+  const float t = x + 12582912.f;
+  const float f = x - (t - 12582912.f);
+  float p = fmaf(0.0013278163969516754f, f, 0.009675555862486362f);
+  p = fmaf(p, f, 0.055507078766822815f);
+  p = fmaf(p, f, 0.24022118747234344f);
+  p = fmaf(p, f, 0.6931469440460205f);
+  p = fmaf(p, f, 1.0000001192092896f);
+  const int n = __float_as_int(t) - 0x4B400000;
+  return __int_as_float(__float_as_int(p) + (n << 23));
 }
 
-// Barrier over the epilogue warps that also ORs a predicate across them, so
-// every epilogue warp takes the same decision to leave the item loop.
-__device__ __forceinline__ int epi_bar_or(int pred) {
-  int out;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.s32 p, %1, 0;\n\t"
-      "bar.red.or.pred q, 1, %2, p;\n\t"
-      "selp.s32 %0, 1, 0, q;\n\t}\n"
-      : "=r"(out)
-      : "r"(pred), "n"(NUM_EPI * 32)
-      : "memory");
-  return out;
-}
-
-template <int KV, int NS>
-__global__ void __launch_bounds__(THREADS, 1)
+template <int KV>
+__global__ void __launch_bounds__(Cfg<KV>::THREADS, 1)
 tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  TcParams p) {
+  constexpr int NEPI = Cfg<KV>::NEPI, NW = Cfg<KV>::NW, CH = Cfg<KV>::CH;
+  constexpr int EMU = Cfg<KV>::EMU, COLS = Cfg<KV>::COLS, NG = NEPI / 4;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* stages = smem;
-  float* wbuf = (float*)(smem + NS * STAGE_BYTES);                // 2 x BN x KV
-  float* comb = wbuf + 2 * BN * KV;                               // BM x KV
-  uint64_t* bars = (uint64_t*)(comb + BM * KV);
+  const int NS = p.ns;
+  const int sbytes = p.a_res ? B_BYTES : STAGE_BYTES;   // bytes per stage
+  uint8_t* abuf = smem;                                  // A_BYTES when a_res
+  uint8_t* stages = smem + (p.a_res ? A_BYTES : 0);
+  float* wbuf = (float*)(stages + NS * sbytes);          // NW x BN x KV
+  float* comb = wbuf + NW * BN * KV;                     // (NG-1) x BM x KV
+  uint64_t* bars = (uint64_t*)(comb + (NG - 1) * BM * KV);
   uint64_t* full = bars;
-  uint64_t* empty = bars + NS;
-  uint64_t* tfull = bars + 2 * NS;
+  uint64_t* empty = full + NS_MAX;
+  uint64_t* tfull = empty + NS_MAX;
   uint64_t* tempty = tfull + 2;
   uint64_t* wfull = tempty + 2;
-  uint64_t* wempty = wfull + 2;
-  uint64_t* drain = wempty + 2;
+  uint64_t* wempty = wfull + NW;
+  uint64_t* afull = wempty + NW;
+  uint64_t* aempty = afull + 1;
+  uint64_t* drain = aempty + 1;
   uint32_t* tmem_slot = (uint32_t*)(drain + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
@@ -225,28 +140,26 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
   const int items = p.n_rt * p.nchunk;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NS; ++s) {
+    for (int s = 0; s < NS_MAX; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
       mbar_init(smem_u32(&empty[s]), 1);
     }
     for (int s = 0; s < 2; ++s) {
       mbar_init(smem_u32(&tfull[s]), 1);
-      mbar_init(smem_u32(&tempty[s]), NUM_EPI);
-      mbar_init(smem_u32(&wfull[s]), 1);
-      mbar_init(smem_u32(&wempty[s]), NUM_EPI);
+      mbar_init(smem_u32(&tempty[s]), NEPI);
     }
+    for (int s = 0; s < NW; ++s) {
+      mbar_init(smem_u32(&wfull[s]), 1);
+      mbar_init(smem_u32(&wempty[s]), NEPI);
+    }
+    mbar_init(smem_u32(afull), 1);
+    mbar_init(smem_u32(aempty), 1);
     mbar_init(smem_u32(drain), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
+  if (warp == 1) tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
   fence_before();
   __syncthreads();
   fence_after();
@@ -255,27 +168,40 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      uint32_t st = 0, ph = 0, ws = 0, wph = 0;
-      uint32_t issued = 0;
-      bool ok = true;
+      uint32_t st = 0, ph = 0, ws = 0, wph = 0, aph = 0, issued = 0;
+      bool ok = true, a_pending = false;
       for (int item = blockIdx.x; ok && item < items; item += gridDim.x) {
         const int rt = item / p.nchunk, ch = item % p.nchunk;
         const int ct0 = ch * p.cpc, ct1 = min(p.n_ct, ct0 + p.cpc);
+        if (p.a_res) {
+          if (!(ok = mbar_wait(smem_u32(aempty), aph ^ 1, abort_flag, p.err))) break;
+          mbar_expect_tx(smem_u32(afull), A_BYTES);
+          tma_load_2d(smem_u32(abuf), &tmA, 0, rt * BM, smem_u32(afull));
+          a_pending = true;
+          aph ^= 1;
+        }
         for (int ct = ct0; ok && ct < ct1; ++ct) {
           if (!(ok = mbar_wait(smem_u32(&wempty[ws]), wph ^ 1, abort_flag, p.err))) break;
           mbar_expect_tx(smem_u32(&wfull[ws]), BN * KV * 4);
           bulk_load(smem_u32(wbuf + ws * BN * KV), p.w + (size_t)ct * BN * KV, BN * KV * 4,
                     smem_u32(&wfull[ws]));
-          ws ^= 1;
-          if (ws == 0) wph ^= 1;
+          if (++ws == NW) {
+            ws = 0;
+            wph ^= 1;
+          }
           for (int kb = 0; kb < p.nkb; ++kb) {
             if (!(ok = mbar_wait(smem_u32(&empty[st]), ph ^ 1, abort_flag, p.err))) break;
-            const uint32_t sa = smem_u32(stages + st * STAGE_BYTES);
-            mbar_expect_tx(smem_u32(&full[st]), STAGE_BYTES);
-            tma_load_2d(sa, &tmA, kb * BK, rt * BM, smem_u32(&full[st]));
-            tma_load_2d(sa + A_BYTES, &tmB, kb * BK, ct * BN, smem_u32(&full[st]));
+            const uint32_t sa = smem_u32(stages + st * sbytes);
+            if (p.a_res) {
+              mbar_expect_tx(smem_u32(&full[st]), B_BYTES);
+              tma_load_2d(sa, &tmB, 0, ct * BN, smem_u32(&full[st]));
+            } else {
+              mbar_expect_tx(smem_u32(&full[st]), STAGE_BYTES);
+              tma_load_2d(sa, &tmA, kb * BK, rt * BM, smem_u32(&full[st]));
+              tma_load_2d(sa + A_BYTES, &tmB, kb * BK, ct * BN, smem_u32(&full[st]));
+            }
             ++issued;
-            if (++st == NS) {
+            if (++st == (uint32_t)NS) {
               st = 0;
               ph ^= 1;
             }
@@ -283,29 +209,34 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         }
       }
       if (!ok) {
-        // drain: wait for the copies of the last (up to NS) stages to land
+        // let the copies of the last (up to NS) stages and the row tile land
         uint32_t s2 = st, p2 = ph;
-        for (uint32_t q = 0; q < (issued < (uint32_t)NS ? issued : (uint32_t)NS); ++q) {
+        const uint32_t nout = issued < (uint32_t)NS ? issued : (uint32_t)NS;
+        for (uint32_t q = 0; q < nout; ++q) {
           if (s2 == 0) {
             s2 = NS - 1;
             p2 ^= 1;
           } else {
             --s2;
           }
-          for (uint32_t it = 0; it < WAIT_LIMIT && !mbar_try(smem_u32(&full[s2]), p2); ++it) {
-          }
+          mbar_drain(smem_u32(&full[s2]), p2);
         }
+        if (a_pending) mbar_drain(smem_u32(afull), aph ^ 1);
       }
     }
   } else if (warp == 1) {
     // ----------------------------------------------------------------- MMA
     if (lane == 0) {
-      uint32_t st = 0, ph = 0, acc = 0, aph = 0;
-      bool ok = true;
-      bool any = false;
+      uint32_t st = 0, ph = 0, acc = 0, aph = 0, afp = 0;
+      bool ok = true, any = false;
       for (int item = blockIdx.x; ok && item < items; item += gridDim.x) {
         const int ch = item % p.nchunk;
         const int ct0 = ch * p.cpc, ct1 = min(p.n_ct, ct0 + p.cpc);
+        if (p.a_res) {
+          if (!(ok = mbar_wait(smem_u32(afull), afp, abort_flag, p.err))) break;
+          afp ^= 1;
+          fence_after();
+        }
         for (int ct = ct0; ok && ct < ct1; ++ct) {
           if (!(ok = mbar_wait(smem_u32(&tempty[acc]), aph ^ 1, abort_flag, p.err))) break;
           fence_after();
@@ -313,15 +244,16 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
           for (int kb = 0; kb < p.nkb; ++kb) {
             if (!(ok = mbar_wait(smem_u32(&full[st]), ph, abort_flag, p.err))) break;
             fence_after();
-            const uint32_t sa = smem_u32(stages + st * STAGE_BYTES);
+            const uint32_t ss = smem_u32(stages + st * sbytes);
+            const uint32_t sa = p.a_res ? smem_u32(abuf) : ss;
+            const uint32_t sb = p.a_res ? ss : ss + A_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < BK / UK; ++kk) {
-              mma_bf16(d, sdesc(sa + kk * UK * 2), sdesc(sa + A_BYTES + kk * UK * 2),
+            for (int kk = 0; kk < BK / UK; ++kk)
+              mma_bf16(d, sdesc(sa + kk * UK * 2), sdesc(sb + kk * UK * 2), IDESC,
                        (kb > 0 || kk > 0) ? 1u : 0u);
-            }
             any = true;
             mma_commit(smem_u32(&empty[st]));
-            if (++st == NS) {
+            if (++st == (uint32_t)NS) {
               st = 0;
               ph ^= 1;
             }
@@ -331,79 +263,121 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
           acc ^= 1;
           if (acc == 0) aph ^= 1;
         }
+        if (!ok) break;
+        if (p.a_res) mma_commit(smem_u32(aempty));  // row tile free once the item's MMAs finish
       }
-      // make sure every issued MMA has finished before TMEM is released
+      // every issued MMA has finished before TMEM is released
       if (any) {
         mma_commit(smem_u32(drain));
-        for (uint32_t it = 0; it < WAIT_LIMIT && !mbar_try(smem_u32(drain), 0); ++it) {
-        }
+        mbar_drain(smem_u32(drain), 0);
       }
     }
   } else {
     // ------------------------------------------------------------ epilogue
+    const int e = warp - 2;
     const int quad = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int grp = e >> 2;
     const int row = quad * 32 + lane;
     uint32_t acc = 0, aph = 0, ws = 0, wph = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < items; item += gridDim.x) {
       const int rt = item / p.nchunk, ch = item % p.nchunk;
       const int ct0 = ch * p.cpc, ct1 = min(p.n_ct, ct0 + p.cpc);
-      float q[KV];
+      float q[CH][KV];
 #pragma unroll
-      for (int c = 0; c < KV; ++c) q[c] = 0.f;
+      for (int h = 0; h < CH; ++h)
+#pragma unroll
+        for (int c = 0; c < KV; ++c) q[h][c] = 0.f;
       for (int ct = ct0; ok && ct < ct1; ++ct) {
         if (!(ok = mbar_wait(smem_u32(&tfull[acc]), aph, abort_flag, p.err))) break;
         if (!(ok = mbar_wait(smem_u32(&wfull[ws]), wph, abort_flag, p.err))) break;
         fence_after();
         const float* wb = wbuf + ws * BN * KV;
+        // The accumulator slice is read in rounds of up to two 32-column chunks;
+        // the TMEM buffer goes back to the MMA warp right after the last round
+        // is loaded (with one round, before any math).
+        constexpr int NCH = COLS / 32;
+        constexpr int RB = NCH < 2 ? NCH : 2;
+        constexpr int PER = EMU > 0 ? 32 / EMU : 33;
 #pragma unroll 1
-        for (int cc = 0; cc < 4; ++cc) {
-          const int col0 = half * 128 + cc * 32;
-          float v[32];
-          tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + acc * BN + col0, v);
-          if (cc == 3) {
-            fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&tempty[acc]));
-          }
+        for (int r0 = 0; r0 < NCH; r0 += RB) {
+        uint32_t raw[RB][32];
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+          const uint32_t ta =
+              tmem + ((uint32_t)(quad * 32) << 16) + acc * BN + grp * COLS + (r0 + b) * 32;
+          tmem_ld16_nowait(ta, *reinterpret_cast<uint32_t(*)[16]>(&raw[b][0]));
+          tmem_ld16_nowait(ta + 16, *reinterpret_cast<uint32_t(*)[16]>(&raw[b][16]));
+        }
+        tmem_wait_ld();
+        if (r0 + RB >= NCH) {
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&tempty[acc]));
+        }
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+          // all exponentials of the chunk first (independent), then the contraction
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const float e = ex2(v[j]);
-            const float* wj = wb + (col0 + j) * KV;
-#pragma unroll
-            for (int c = 0; c < KV; ++c) q[c] = fmaf(e, wj[c], q[c]);
+            const float s = __uint_as_float(raw[b][j]);
+            raw[b][j] = __float_as_uint((j % PER == PER - 1) ? ex2_fma(s) : ex2_mufu(s));
           }
+          const float4* w4 =
+              reinterpret_cast<const float4*>(wb + (grp * COLS + (r0 + b) * 32) * KV);
+#pragma unroll
+          for (int j4 = 0; j4 < 32 * KV / 4; ++j4) {
+            const float4 wv = w4[j4];
+            const float wq[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int idx = j4 * 4 + u;  // = j * KV + c
+              const int j = idx / KV, c = idx % KV;
+              q[j % CH][c] = fmaf(__uint_as_float(raw[b][j]), wq[u], q[j % CH][c]);
+            }
+          }
+        }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&wempty[ws]));
         acc ^= 1;
         if (acc == 0) aph ^= 1;
-        ws ^= 1;
-        if (ws == 0) wph ^= 1;
+        if (++ws == NW) {
+          ws = 0;
+          wph ^= 1;
+        }
       }
-      // combine the two column halves and write this item's partial sums
-      if (half == 1) {
+      float qs[KV];
 #pragma unroll
-        for (int c = 0; c < KV; ++c) comb[row * KV + c] = q[c];
+      for (int c = 0; c < KV; ++c) {
+        float s = q[0][c];
+#pragma unroll
+        for (int h = 1; h < CH; ++h) s += q[h][c];
+        qs[c] = s;
       }
-      epi_bar();
-      if (half == 0 && ok) {
+      // combine the column groups (fixed order) and write the partial row sums
+      if (grp > 0) {
+#pragma unroll
+        for (int c = 0; c < KV; ++c) comb[((grp - 1) * BM + row) * KV + c] = qs[c];
+      }
+      bar_sync<NEPI * 32>();
+      if (grp == 0 && ok) {
         float* out = p.part + ((size_t)ch * p.n_rpad + (size_t)rt * BM + row) * KV;
 #pragma unroll
-        for (int c = 0; c < KV; ++c) out[c] = q[c] + comb[row * KV + c];
+        for (int c = 0; c < KV; ++c) {
+          float s = qs[c];
+#pragma unroll
+          for (int g = 1; g < NG; ++g) s += comb[((g - 1) * BM + row) * KV + c];
+          out[c] = s;
+        }
       }
-      if (epi_bar_or(!ok || *abort_flag)) break;
+      if (bar_or<NEPI * 32>(!ok || *abort_flag)) break;
     }
   }
   fence_before();
   __syncthreads();
   fence_after();
-  if (warp == 1) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(TMEM_COLS)
-                 : "memory");
-  }
+  if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
 }
 
 // ------------------------------------------------------------ helpers ----
@@ -484,13 +458,13 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 EncodeTiledFn encode_fn() {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    KRR_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                              cudaEnableDefault, &q));
-    if (q != cudaDriverEntryPointSuccess || !p)
+    void* q = nullptr;
+    cudaDriverEntryPointQueryResult r;
+    KRR_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &q, 12000,
+                                              cudaEnableDefault, &r));
+    if (r != cudaDriverEntryPointSuccess || !q)
       throw Error{KRR_ECUDA, "cuTensorMapEncodeTiled entry point not found"};
-    fn = (EncodeTiledFn)p;
+    fn = (EncodeTiledFn)q;
   }
   return fn;
 }
@@ -504,7 +478,8 @@ void make_map(CUtensorMap* m, const void* base, int rows, int kp, int box_rows) 
                            gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) throw Error{KRR_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r)};
+  if (r != CUDA_SUCCESS)
+    throw Error{KRR_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r)};
 }
 
 void ensure(DevBuf& b, size_t bytes) {
@@ -547,42 +522,44 @@ int choose_nchunk(int n_rt, int n_ct, int grid) {
   return best;
 }
 
-template <int KV, int NS>
-size_t smem_bytes() {
-  return 1024 + (size_t)NS * STAGE_BYTES + (size_t)2 * BN * KV * 4 + (size_t)BM * KV * 4 + 256;
+template <int KV>
+size_t smem_bytes(int a_res, int ns) {
+  constexpr int NW = Cfg<KV>::NW, NG = Cfg<KV>::NEPI / 4;
+  return 1024 + (a_res ? (size_t)A_BYTES + (size_t)ns * B_BYTES : (size_t)ns * STAGE_BYTES) +
+         (size_t)NW * BN * KV * 4 + (size_t)(NG - 1) * BM * KV * 4 + 256;
 }
 
-template <int KV, int NS>
+template <int KV>
 void launch_kernel(cudaStream_t st, const CUtensorMap& a, const CUtensorMap& b, const TcParams& p,
                    int grid) {
-  static bool attr = false;
-  const size_t sm = smem_bytes<KV, NS>();
-  if (!attr) {
-    KRR_CUDA(cudaFuncSetAttribute(tc_matvec_kernel<KV, NS>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    attr = true;
+  static size_t attr = 0;
+  const size_t sm = smem_bytes<KV>(p.a_res, p.ns);
+  if (attr < sm) {
+    KRR_CUDA(cudaFuncSetAttribute(tc_matvec_kernel<KV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm));
+    attr = sm;
   }
-  tc_matvec_kernel<KV, NS><<<grid, THREADS, sm, st>>>(a, b, p);
+  tc_matvec_kernel<KV><<<grid, Cfg<KV>::THREADS, sm, st>>>(a, b, p);
   KRR_CHECK_LAUNCH();
 }
 
 void dispatch(int kv, cudaStream_t st, const CUtensorMap& a, const CUtensorMap& b,
               const TcParams& p, int grid) {
   switch (kv) {
-    case 1: launch_kernel<1, 4>(st, a, b, p, grid); break;
-    case 2: launch_kernel<2, 4>(st, a, b, p, grid); break;
-    case 4: launch_kernel<4, 4>(st, a, b, p, grid); break;
-    case 8: launch_kernel<8, 3>(st, a, b, p, grid); break;
-    case 12: launch_kernel<12, 3>(st, a, b, p, grid); break;
-    default: launch_kernel<16, 3>(st, a, b, p, grid); break;
+    case 1: launch_kernel<1>(st, a, b, p, grid); break;
+    case 2: launch_kernel<2>(st, a, b, p, grid); break;
+    case 4: launch_kernel<4>(st, a, b, p, grid); break;
+    case 8: launch_kernel<8>(st, a, b, p, grid); break;
+    case 12: launch_kernel<12>(st, a, b, p, grid); break;
+    default: launch_kernel<16>(st, a, b, p, grid); break;
   }
 }
 
-// Prepare one operand set (rows or columns) into `op`.
+// Prepare one operand set into `op`.
 void prep_operand(TcOperand& op, cudaStream_t st, const float* X, int n, int ld, int d,
                   const double* mu, double scale) {
   const int kp = (d + BK - 1) / BK * BK;
-  const int n_pad = (n + BN - 1) / BN * BN;
+  const int n_pad = (n + PAD - 1) / PAD * PAD;
   ensure(op.Xa, (size_t)n_pad * kp * 2);
   ensure(op.ra, (size_t)n_pad * 4);
   ensure(op.nh, (size_t)n_pad * 4 + 16);
@@ -598,6 +575,21 @@ void prep_operand(TcOperand& op, cudaStream_t st, const float* X, int n, int ld,
   op.n_pad = n_pad;
   make_map(&op.map_a, op.Xa.p, n_pad, kp, BM);
   make_map(&op.map_b, op.Xa.p, n_pad, kp, BN);
+}
+
+struct Plan {
+  int kv, n_rt, n_ct, cpc, nchunk;
+};
+
+Plan plan_for(const TcOperand& op, int k) {
+  Plan pl;
+  pl.kv = kv_bucket(k);
+  pl.n_rt = op.n_pad / BM;
+  pl.n_ct = op.n_pad / BN;
+  const int req = choose_nchunk(pl.n_rt, pl.n_ct, sm_count());
+  pl.cpc = (pl.n_ct + req - 1) / req;
+  pl.nchunk = (pl.n_ct + pl.cpc - 1) / pl.cpc;
+  return pl;
 }
 
 }  // namespace
@@ -629,53 +621,11 @@ void tc_prepare(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int
   t.ready = true;
 }
 
-void tc_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
-               int nc, int ldxc, int d, double sigma, double shift, const float* V, int k,
-               int ldv, float* Q, int ldq) {
-  const bool same = (Xr == Xc && nr == nc && ldxr == ldxc);
-  if (!same) throw Error{KRR_EUNSUPPORTED, "BF16 product supports the training system (Xr == Xc)"};
-  tc_prepare(t, st, Xc, nc, ldxc, d, sigma);
-  TcOperand& op = t.cols;
-  const int kv = kv_bucket(k);
-  const int grid_max = sm_count();
-  const int n_rt = op.n_pad / BM, n_ct = op.n_pad / BN;
-  const int nchunk_req = choose_nchunk(n_rt, n_ct, grid_max);
-  const int cpc = (n_ct + nchunk_req - 1) / nchunk_req;
-  const int nchunk = (n_ct + cpc - 1) / cpc;
-  tc_reserve(t, st, k);
-  make_w_kernel<<<std::min(8 * sm_count(), (int)(((size_t)op.n_pad * kv + 255) / 256)), 256, 0,
-                  st>>>(V, nc, k, ldv, (const float*)op.ra.p, op.n_pad, kv, (float*)t.w.p);
-  KRR_CHECK_LAUNCH();
-  TcParams p;
-  p.n_rt = n_rt;
-  p.n_ct = n_ct;
-  p.nchunk = nchunk;
-  p.cpc = cpc;
-  p.nkb = op.kp / BK;
-  p.n_rpad = op.n_pad;
-  p.w = (const float*)t.w.p;
-  p.part = (float*)t.part.p;
-  p.err = (int*)t.err.p;
-  const int items = n_rt * nchunk;
-  const int grid = std::min(items, grid_max);
-  dispatch(kv, st, op.map_a, op.map_b, p, grid);
-  const size_t total = (size_t)nr * k;
-  tc_reduce_kernel<<<std::min(8 * sm_count(), (int)((total + 255) / 256)), 256, 0, st>>>(
-      (const float*)t.part.p, nchunk, op.n_pad, kv, (const float*)op.ra.p, nr, k, V, ldv, shift,
-      Q, ldq);
-  KRR_CHECK_LAUNCH();
-}
-
 void tc_reserve(TcState& t, cudaStream_t st, int k) {
-  const TcOperand& op = t.cols;
   if (!t.ready) throw Error{KRR_EINVAL, "tensor-core product used before tc_prepare"};
-  const int kv = kv_bucket(k);
-  const int n_rt = op.n_pad / BM, n_ct = op.n_pad / BN;
-  const int cpc = (n_ct + choose_nchunk(n_rt, n_ct, sm_count()) - 1) /
-                  choose_nchunk(n_rt, n_ct, sm_count());
-  const int nchunk = (n_ct + cpc - 1) / cpc;
-  ensure(t.w, (size_t)op.n_pad * kv * 4);
-  ensure(t.part, (size_t)nchunk * op.n_pad * kv * 4);
+  const Plan pl = plan_for(t.cols, k);
+  ensure(t.w, (size_t)t.cols.n_pad * pl.kv * 4);
+  ensure(t.part, (size_t)pl.nchunk * t.cols.n_pad * pl.kv * 4);
   if (!t.err.p) {
     ensure(t.err, 16);
     KRR_CUDA(cudaMemsetAsync(t.err.p, 0, 16, st));
@@ -684,6 +634,40 @@ void tc_reserve(TcState& t, cudaStream_t st, int k) {
 
 void tc_clear_error(TcState& t, cudaStream_t st) {
   if (t.err.p) KRR_CUDA(cudaMemsetAsync(t.err.p, 0, 16, st));
+}
+
+void tc_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
+               int nc, int ldxc, int d, double sigma, double shift, const float* V, int k,
+               int ldv, float* Q, int ldq) {
+  const bool same = (Xr == Xc && nr == nc && ldxr == ldxc);
+  if (!same) throw Error{KRR_EUNSUPPORTED, "BF16 product supports the training system (Xr == Xc)"};
+  tc_prepare(t, st, Xc, nc, ldxc, d, sigma);
+  tc_reserve(t, st, k);
+  TcOperand& op = t.cols;
+  const Plan pl = plan_for(op, k);
+  make_w_kernel<<<std::min(8 * sm_count(), (int)(((size_t)op.n_pad * pl.kv + 255) / 256)), 256,
+                  0, st>>>(V, nc, k, ldv, (const float*)op.ra.p, op.n_pad, pl.kv, (float*)t.w.p);
+  KRR_CHECK_LAUNCH();
+  TcParams p;
+  p.n_rt = pl.n_rt;
+  p.n_ct = pl.n_ct;
+  p.nchunk = pl.nchunk;
+  p.cpc = pl.cpc;
+  p.nkb = op.kp / BK;
+  p.a_res = p.nkb == 1 ? 1 : 0;
+  p.ns = p.a_res ? 4 : 3;
+  p.n_rpad = op.n_pad;
+  p.w = (const float*)t.w.p;
+  p.part = (float*)t.part.p;
+  p.err = (int*)t.err.p;
+  const int items = pl.n_rt * pl.nchunk;
+  const int grid = std::min(items, sm_count());
+  dispatch(pl.kv, st, op.map_a, op.map_b, p, grid);
+  const size_t total = (size_t)nr * k;
+  tc_reduce_kernel<<<std::min(8 * sm_count(), (int)((total + 255) / 256)), 256, 0, st>>>(
+      (const float*)t.part.p, pl.nchunk, op.n_pad, pl.kv, (const float*)op.ra.p, nr, k, V, ldv,
+      shift, Q, ldq);
+  KRR_CHECK_LAUNCH();
 }
 
 int tc_error(TcState& t, cudaStream_t st) {
