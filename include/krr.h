@@ -184,6 +184,54 @@ krr_status krr_predict(krr_handle* h, const float* Xtr, int n, int ldxtr,
                        const double* C, int k, int ldc, double* F, int ldf,
                        int precision);
 
+/* --------------------------------------- hyper-parameter gradient ------ */
+/*
+ * The paper fixes sigma and lambda and does not differentiate the solution.
+ * These two calls add the gradient of a held-out loss with respect to
+ * log sigma and log lambda, derived from Eq. (1) and the Gaussian kernel of
+ * Section 5 (k(x, z) = exp(-||x - z||^2 / (2 sigma^2))):
+ *   A = K + lambda I,  c = A^-1 y,  f = K(Xte, X) c,
+ *   dK/dlog(sigma) = D o K,  D_ij = ||x_i - x_j||^2 / sigma^2,
+ *   dA/dlog(lambda) = lambda I.
+ */
+
+/*
+ * Derivative product  Q = (D o K)(Xr, Xc) V  (the lambda I term has no
+ * sigma dependence, so there is no shift).  Xr: nr x d (ldxr), Xc: nc x d
+ * (ldxc) FP32; V: nc x k (ldv), Q: nr x k (ldq) double; device pointers.
+ * precision: KRR_FP64 (distances summed from differences, FP64 exp).
+ * 1 <= k <= KRR_MAX_RHS.  Returns KRR_EINVAL for bad arguments.
+ */
+krr_status krr_kernel_dsigma_matvec(krr_handle* h, const float* Xr, int nr, int ldxr,
+                                    const float* Xc, int nc, int ldxc, int d,
+                                    double sigma, const double* V, int k, int ldv,
+                                    double* Q, int ldq, int precision);
+
+/*
+ * Backward pass of  F = K(Xte, X) (K + lambda I)^-1 Y  for a scalar loss L
+ * whose gradient with respect to F is GF = dL/dF:
+ *   gbar = K(X, Xte) GF,  w = A^-1 gbar  (adjoint solve: A is symmetric, so
+ *   it is Algorithm 1 again with gbar as right-hand side, run with *opts),
+ *   grad[0] = dL/dlog(sigma)  = sum(GF o ((Dte o Kte) C)) - sum(w o ((D o K) C)),
+ *   grad[1] = dL/dlog(lambda) = -lambda sum(w o C).
+ * X: n x d (ldx), Xte: m x d (ldxte) FP32; W (d x s), b (s): the RFF draw
+ * for the adjoint solve's preconditioner (may be NULL when
+ * opts->precond == 0); C: n x k (ldc) the forward solution; GF: m x k (ldg).
+ * These may be host or device pointers.  grad: host array of 2 doubles.
+ * Wadj (may be NULL): receives w, n x k (ldw), host or device.  rep (may be
+ * NULL) reports the adjoint solve.  The products and the contractions run
+ * in FP64; the adjoint solve in opts->precision.  Returns the adjoint
+ * solve's status (grad is written in every case once the arguments pass).
+ * opts->warm_start must be 0.
+ */
+krr_status krr_hypergrad(krr_handle* h, const float* X, int n, int d, int ldx,
+                         const float* Xte, int m, int ldxte,
+                         double sigma, double lambda,
+                         const float* W, const float* b, int s,
+                         const double* C, int ldc, const double* GF, int k, int ldg,
+                         const krr_opts* opts, double* grad,
+                         double* Wadj, int ldw, krr_report* rep);
+
 /*
  * Kernel-matrix product that allocates nothing.  The paper has no
  * counterpart: this exists for callers that cannot call cudaMalloc when

@@ -24,6 +24,7 @@ Sketching and Preconditioning"):
                                  true relative residual (Section 5).
 * ``krr_pcg_solve``           -- Algorithm 1 end to end.
 * ``predict``                 -- f(x) = sum_i c_i k(x_i, x), Section 1.
+* ``kernel_dlogsigma``        -- D o K, the derivative of K in log sigma.
 * ``hypergrad``               -- gradient of a held-out MSE with respect to
                                  log sigma and log lambda (not in the paper;
                                  derived by implicit differentiation of Eq. (1)).
@@ -68,6 +69,16 @@ def sqdist_direct(Xa: np.ndarray, Xb: np.ndarray, block: int = 256) -> np.ndarra
 def gaussian_kernel(Xa: np.ndarray, Xb: np.ndarray, sigma: float) -> np.ndarray:
     """K_ij = exp(-||a_i - b_j||^2 / (2 sigma^2)) (the paper's Gaussian kernel, Section 5)."""
     return np.exp(-sqdist_direct(Xa, Xb) / (2.0 * sigma * sigma))
+
+
+def kernel_dlogsigma(Xa: np.ndarray, Xb: np.ndarray, sigma: float) -> np.ndarray:
+    """d K / d log(sigma) for the Gaussian kernel of Section 5 (not in the paper).
+
+    With D_ij = ||a_i - b_j||^2 / sigma^2 the kernel is exp(-D/2) and
+    d D / d log(sigma) = -2 D, so the derivative is D o K.
+    """
+    D = sqdist_direct(Xa, Xb) / (sigma * sigma)
+    return D * np.exp(-0.5 * D)
 
 
 def kernel_matrix_system(X: np.ndarray, sigma: float, lam: float) -> np.ndarray:

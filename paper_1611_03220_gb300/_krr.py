@@ -69,6 +69,11 @@ _SIGS = {
     "krr_predict": (_i, [_vp, _vp, _i, _i, _vp, _i, _i, _i, _d, _vp, _i, _i, _vp, _i, _i]),
     "krr_kernel_matvec_fp64_noalloc": (_i, [_vp, _i, _i, _vp, _i, _i, _i, _d, _d, _vp, _i, _i,
                                             _vp, _i, _vp]),
+    "krr_kernel_dsigma_matvec": (_i, [_vp, _vp, _i, _i, _vp, _i, _i, _i, _d, _vp, _i, _i, _vp,
+                                      _i, _i]),
+    "krr_hypergrad": (_i, [_vp, _vp, _i, _i, _i, _vp, _i, _i, _d, _d, _vp, _vp, _i, _vp, _i, _vp,
+                           _i, _i, C.POINTER(krr_opts), C.POINTER(_d), _vp, _i,
+                           C.POINTER(krr_report)]),
     "krr_launch_count": (C.c_longlong, []),
     "krr_bench_ex2": (_i, [_vp, _i, C.POINTER(_d), C.POINTER(_d)]),
 }
@@ -96,9 +101,9 @@ def _ptr(a) -> int:
 def _ld(a) -> int:
     """Leading dimension (elements) of a row-major 2-D array."""
     if isinstance(a, np.ndarray):
-        assert a.flags["C_CONTIGUOUS"] or a.strides[1] == a.itemsize, "inner stride must be 1"
+        assert a.shape[1] == 1 or a.strides[1] == a.itemsize, "inner stride must be 1"
         return a.strides[0] // a.itemsize
-    assert a.stride(1) == 1, "inner stride must be 1"
+    assert a.shape[1] == 1 or a.stride(1) == 1, "inner stride must be 1"
     return a.stride(0)
 
 
@@ -237,3 +242,40 @@ def krr_predict(h: Handle, Xtr, Xte, sigma: float, Cc, F, precision="fp64"):
     h._check(_lib.krr_predict(h.ptr, _ptr(Xtr), n, _ld(Xtr), _ptr(Xte), m, _ld(Xte), d,
                               float(sigma), _ptr(Cc), k, _ld(Cc), _ptr(F), _ld(F), prec))
     return F
+
+
+def krr_kernel_dsigma_matvec(h: Handle, Xr, Xc, sigma: float, V, Q, precision="fp64"):
+    """Q = (D o K)(Xr, Xc) V, the derivative of the product with respect to log sigma."""
+    nr, d = Xr.shape
+    nc = Xc.shape[0]
+    k = V.shape[1]
+    prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    h._check(_lib.krr_kernel_dsigma_matvec(h.ptr, _ptr(Xr), nr, _ld(Xr), _ptr(Xc), nc, _ld(Xc),
+                                           d, float(sigma), _ptr(V), k, _ld(V), _ptr(Q), _ld(Q),
+                                           prec))
+    return Q
+
+
+def krr_hypergrad(h: Handle, X, Xte, sigma: float, lam: float, W, b, Cc, GF,
+                  opts: krr_opts | None = None, Wadj=None, check: bool = True):
+    """(dL/dlog sigma, dL/dlog lambda) for dL/dF = GF at F = K(Xte, X) Cc.
+
+    Returns ``(grad, report)``: grad a 2-tuple, report the adjoint solve's dict.
+    """
+    n, d = X.shape
+    m = Xte.shape[0]
+    k = GF.shape[1]
+    s = W.shape[1] if W is not None else 0
+    rep = krr_report()
+    g = (_d * 2)()
+    o = opts if opts is not None else default_opts()
+    st = _lib.krr_hypergrad(h.ptr, _ptr(X), n, d, _ld(X), _ptr(Xte), m, _ld(Xte), float(sigma),
+                            float(lam), _ptr(W) if W is not None else None,
+                            _ptr(b) if b is not None else None, s, _ptr(Cc), _ld(Cc), _ptr(GF), k,
+                            _ld(GF), C.byref(o), g, _ptr(Wadj) if Wadj is not None else None,
+                            _ld(Wadj) if Wadj is not None else k, C.byref(rep))
+    if check:
+        h._check(st)
+    out = rep.as_dict()
+    out["status_code"] = st
+    return (g[0], g[1]), out

@@ -232,42 +232,77 @@ struct LoopOut {
   int iter;
 };
 
+// One PCG solve's operands: the loop vectors (n x k, ld = k), the right-hand
+// side whose norm sets the stopping test, and the two operators.
 template <typename T>
-void pcg_loop(krr_handle* h, int n, int k, const double* Ytol, int ldy, T* x, T* r, T* p, T* z,
-              T* q, double tol, int max_iter, bool use_graph,
-              const std::function<void(cudaStream_t, const T*, T*)>& matvec,
-              const std::function<void(cudaStream_t, const T*, T*)>& apply, LoopOut* out,
-              int* matvecs, int prec) {
+struct PcgSpec {
+  int n = 0, k = 0;
+  const double* Ytol = nullptr;
+  int ldy = 0;
+  T *x = nullptr, *r = nullptr, *p = nullptr, *z = nullptr, *q = nullptr;
+  double tol = 0.0;
+  int max_iter = 0;
+  std::function<void(cudaStream_t, const T*, T*)> matvec, apply;
+  int prec = KRR_FP64;
+};
+
+// Everything before the first iteration: ||y||, z0 = M^-1 r0, p0 = z0.
+template <typename T>
+void pcg_begin(krr_handle* h, const PcgSpec<T>& S) {
   cudaStream_t st = h->stream;
-  double* part = wsT<double>(h, "cg_part", cg_part_elems(n, k));
-  matvec_reserve(h, n, k, prec);
-  launch_cg_init<T>(st, h->sc, Ytol, ldy, r, n, k, tol, max_iter, part);
-  if (apply)
-    apply(st, r, z);
+  double* part = wsT<double>(h, "cg_part", cg_part_elems(S.n, S.k));
+  matvec_reserve(h, S.n, S.k, S.prec);
+  launch_cg_init<T>(st, h->sc, S.Ytol, S.ldy, S.r, S.n, S.k, S.tol, S.max_iter, part);
+  if (S.apply)
+    S.apply(st, S.r, S.z);
   else
-    KRR_CUDA(cudaMemcpyAsync(z, r, (size_t)n * k * sizeof(T), cudaMemcpyDeviceToDevice, st));
-  launch_cg_rz_first<T>(st, h->sc, r, z, p, n, k, part);
+    KRR_CUDA(cudaMemcpyAsync(S.z, S.r, (size_t)S.n * S.k * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  launch_cg_rz_first<T>(st, h->sc, S.r, S.z, S.p, S.n, S.k, part);
+}
 
-  auto body = [&](cudaStream_t s2, unsigned long long cond) {
-    matvec(s2, p, q);
-    launch_cg_alpha<T>(s2, h->sc, p, q, n, k, part);
-    launch_cg_update_xr<T>(s2, h->sc, x, r, p, q, n, k, part);
-    if (apply)
-      apply(s2, r, z);
-    else
-      KRR_CUDA(cudaMemcpyAsync(z, r, (size_t)n * k * sizeof(T), cudaMemcpyDeviceToDevice, s2));
-    launch_cg_rz<T>(s2, h->sc, r, z, n, k, part);
-    launch_cg_update_p<T>(s2, h->sc, p, z, n, k);
-    launch_cg_tail(s2, h->sc, cond);
-  };
+// One iteration (Algorithm 1 line 9): q = A p, alpha, x and r updates,
+// z = M^-1 r, beta and p; the tail kernel decides whether to continue.
+// Enqueues only (no allocation), so it can be captured into a graph.
+template <typename T>
+void pcg_body(krr_handle* h, const PcgSpec<T>& S, cudaStream_t s2, unsigned long long cond) {
+  double* part = wsT<double>(h, "cg_part", cg_part_elems(S.n, S.k));
+  S.matvec(s2, S.p, S.q);
+  launch_cg_alpha<T>(s2, h->sc, S.p, S.q, S.n, S.k, part);
+  launch_cg_update_xr<T>(s2, h->sc, S.x, S.r, S.p, S.q, S.n, S.k, part);
+  if (S.apply)
+    S.apply(s2, S.r, S.z);
+  else
+    KRR_CUDA(cudaMemcpyAsync(S.z, S.r, (size_t)S.n * S.k * sizeof(T), cudaMemcpyDeviceToDevice, s2));
+  launch_cg_rz<T>(s2, h->sc, S.r, S.z, S.n, S.k, part);
+  launch_cg_update_p<T>(s2, h->sc, S.p, S.z, S.n, S.k);
+  launch_cg_tail(s2, h->sc, cond);
+}
 
+// Reads the loop's device scalars back (synchronises the stream).
+void pcg_finish(krr_handle* h, int k, LoopOut* out) {
+  cudaStream_t st = h->stream;
+  KRR_CUDA(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+  KRR_CUDA(cudaStreamSynchronize(st));
+  for (int c = 0; c < k; ++c) {
+    out->iters[c] = h->sc_host->iters[c];
+    out->rr[c] = h->sc_host->rr[c];
+    out->yy[c] = h->sc_host->yy[c];
+  }
+  out->flags = h->sc_host->flags;
+  out->iter = h->sc_host->iter;
+}
+
+template <typename T>
+void pcg_loop(krr_handle* h, const PcgSpec<T>& S, bool use_graph, LoopOut* out, int* matvecs) {
+  cudaStream_t st = h->stream;
+  pcg_begin<T>(h, S);
   int launched = 0;
   long long body_launches = 0;
-  if (max_iter > 0) {
+  if (S.max_iter > 0) {
     if (use_graph) {
       cudaGraph_t graph = nullptr;
       cudaGraphExec_t exec = nullptr;
-      KRR_TRACE("pcg_loop: graph create n=%d k=%d max_iter=%d", n, k, max_iter);
+      KRR_TRACE("pcg_loop: graph create n=%d k=%d max_iter=%d", S.n, S.k, S.max_iter);
       KRR_CUDA(cudaGraphCreate(&graph, 0));
       try {
         cudaGraphConditionalHandle cond;
@@ -278,13 +313,12 @@ void pcg_loop(krr_handle* h, int n, int k, const double* Ytol, int ldy, T* x, T*
         params.conditional.size = 1;
         cudaGraphNode_t node;
         KRR_CUDA(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &params));
-        KRR_TRACE("pcg_loop: conditional node added, out=%p", (void*)params.conditional.phGraph_out);
         cudaGraph_t bodyg = params.conditional.phGraph_out[0];
         KRR_CUDA(cudaStreamBeginCaptureToGraph(h->cap, bodyg, nullptr, nullptr, 0,
                                                cudaStreamCaptureModeRelaxed));
         capture_begin();
         try {
-          body(h->cap, (unsigned long long)cond);
+          pcg_body<T>(h, S, h->cap, (unsigned long long)cond);
         } catch (...) {
           capture_end();
           cudaGraph_t tmp;
@@ -294,11 +328,8 @@ void pcg_loop(krr_handle* h, int n, int k, const double* Ytol, int ldy, T* x, T*
         }
         body_launches = capture_end();
         cudaGraph_t captured = nullptr;
-        KRR_TRACE("pcg_loop: body captured");
         KRR_CUDA(cudaStreamEndCapture(h->cap, &captured));
-        KRR_TRACE("pcg_loop: capture ended");
         KRR_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-        KRR_TRACE("pcg_loop: instantiated");
         KRR_CUDA(cudaGraphLaunch(exec, st));
         KRR_TRACE("pcg_loop: launched");
       } catch (...) {
@@ -315,30 +346,18 @@ void pcg_loop(krr_handle* h, int n, int k, const double* Ytol, int ldy, T* x, T*
     } else {
       // host-driven loop: checks the device scalars every `chk` iterations
       const int chk = 8;
-      for (int it = 0; it < max_iter; ++it) {
-        body(st, 0ull);
+      for (int it = 0; it < S.max_iter; ++it) {
+        pcg_body<T>(h, S, st, 0ull);
         ++launched;
-        if ((it + 1) % chk == 0 || it + 1 == max_iter) {
+        if ((it + 1) % chk == 0 || it + 1 == S.max_iter) {
           KRR_CUDA(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
           KRR_CUDA(cudaStreamSynchronize(st));
-          int any = 0;
-          for (int c = 0; c < k; ++c) any |= h->sc_host->active[c];
-          if (!any || (h->sc_host->flags & (FLAG_BREAKDOWN | FLAG_NAN)) ||
-              h->sc_host->iter >= max_iter)
-            break;
+          if (!h->sc_host->run) break;
         }
       }
     }
   }
-  KRR_CUDA(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
-  KRR_CUDA(cudaStreamSynchronize(st));
-  for (int c = 0; c < k; ++c) {
-    out->iters[c] = h->sc_host->iters[c];
-    out->rr[c] = h->sc_host->rr[c];
-    out->yy[c] = h->sc_host->yy[c];
-  }
-  out->flags = h->sc_host->flags;
-  out->iter = h->sc_host->iter;
+  pcg_finish(h, S.k, out);
   if (matvecs) *matvecs += launched;
 }
 
@@ -464,8 +483,11 @@ krr_status solve_plain(krr_handle* h, const SolveArgs& a, int prec, krr_report* 
   LoopOut lo;
   int remaining = a.o.max_iter;
   for (;;) {
-    pcg_loop<T>(h, n, k, Yc, k, x, r, p, z, q, a.o.tol, remaining, a.o.use_graph != 0, mv, ap,
-                &lo, matvecs, prec);
+    PcgSpec<T> S;
+    S.n = n; S.k = k; S.Ytol = Yc; S.ldy = k;
+    S.x = x; S.r = r; S.p = p; S.z = z; S.q = q;
+    S.tol = a.o.tol; S.max_iter = remaining; S.matvec = mv; S.apply = ap; S.prec = prec;
+    pcg_loop<T>(h, S, a.o.use_graph != 0, &lo, matvecs);
     for (int c = 0; c < k; ++c) total_iters[c] += lo.iters[c];
     remaining -= lo.iter;
     if (lo.flags & FLAG_NAN) {
@@ -584,8 +606,11 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
     launch_convert<double, float>(st, Rs, n, k, k, r, k, one);
     KRR_CUDA(cudaMemsetAsync(x, 0, nk * sizeof(float), st));
     LoopOut lo;
-    pcg_loop<float>(h, n, k, Rs, k, x, r, p, z, q, a.o.inner_tol, remaining, a.o.use_graph != 0,
-                    mv, ap, &lo, matvecs, KRR_BF16);
+    PcgSpec<float> S;
+    S.n = n; S.k = k; S.Ytol = Rs; S.ldy = k;
+    S.x = x; S.r = r; S.p = p; S.z = z; S.q = q;
+    S.tol = a.o.inner_tol; S.max_iter = remaining; S.matvec = mv; S.apply = ap; S.prec = KRR_BF16;
+    pcg_loop<float>(h, S, a.o.use_graph != 0, &lo, matvecs);
     for (int c = 0; c < k; ++c) total_iters[c] += lo.iters[c];
     remaining -= lo.iter;
     if (lo.flags & FLAG_NAN) {
@@ -605,6 +630,91 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
     rep->outer_steps = outer;
   }
   return status;
+}
+
+void check_solve_args(const krr_opts& o, int n, int d, int ldx, double sigma, double lambda,
+                      const float* W, const float* b, int s, int k, int ldy, int ldc) {
+  KRR_REQUIRE(n > 0 && d > 0 && k >= 1 && k <= KRR_MAX_RHS, "pcg_solve: bad sizes");
+  KRR_REQUIRE(ldx >= d && ldy >= k && ldc >= k, "pcg_solve: leading dimension too small");
+  KRR_REQUIRE(sigma > 0.0 && std::isfinite(sigma), "pcg_solve: sigma must be > 0");
+  KRR_REQUIRE(lambda > 0.0 && std::isfinite(lambda), "pcg_solve: lambda must be > 0");
+  KRR_REQUIRE(o.tol > 0.0 && o.max_iter >= 0, "pcg_solve: bad tol / max_iter");
+  KRR_REQUIRE(o.precision == KRR_FP64 || o.precision == KRR_FP32 || o.precision == KRR_MIXED,
+              "pcg_solve: precision must be KRR_FP64, KRR_FP32 or KRR_MIXED");
+  if (o.precond) {
+    KRR_REQUIRE(W && b && s > 0 && s <= n, "pcg_solve: preconditioner needs W, b and 0 < s <= n");
+  }
+  if (o.precision == KRR_MIXED) {
+    KRR_REQUIRE(o.inner_tol > 0.0 && o.inner_tol < 1.0, "pcg_solve: inner_tol in (0, 1)");
+  }
+}
+
+// Algorithm 1 lines 4-7 on device-resident operands: RFF features and the
+// preconditioner factors; for the mixed solve also the BF16 and HP operands.
+void setup_impl(krr_handle* h, const float* Xd, int n, int d, int ldx, double sigma,
+                double lambda, const float* Wd, const float* bd, int s, const krr_opts& o) {
+  cudaStream_t st = h->stream;
+  if (o.precond) {
+    float* Z = wsT<float>(h, "rff_Z", (size_t)n * s);
+    launch_rff(st, Xd, n, d, ldx, Wd, bd, s, Z, s);
+    int zb = o.z_bf16 < 0 ? (o.precision == KRR_MIXED ? 1 : 0) : (o.z_bf16 ? 1 : 0);
+    double lp = o.lambda_p > 0.0 ? o.lambda_p : lambda;
+    precond_setup_impl(h, Z, n, s, s, lp, o.apply_form, zb);
+  }
+  if (o.precision == KRR_MIXED) {
+    tc_prepare(h->tc, st, Xd, n, ldx, d, sigma);
+    tc_clear_error(h->tc, st);
+    if (hp_supported(d)) {
+      hp_prepare(h->hp, st, Xd, n, ldx, d, sigma);
+      hp_clear_error(h->hp, st);
+    }
+  }
+}
+
+// Algorithm 1 on device-resident operands: features and preconditioner
+// (lines 5-7), then PCG in the requested arithmetic.  Records `ev_setup`
+// once the set-up work is enqueued (null: not recorded).
+krr_status solve_impl(krr_handle* h, const float* Xd, int n, int d, int ldx, double sigma,
+                      double lambda, const float* Wd, const float* bd, int s, const double* Yd,
+                      int k, int ldy, double* Cd, int ldc, const krr_opts& o, krr_report* rep,
+                      int* matvecs, cudaEvent_t ev_setup) {
+  KRR_TRACE("pcg_solve: n=%d d=%d k=%d s=%d prec=%d graph=%d", n, d, k, s, o.precision,
+            o.use_graph);
+  setup_impl(h, Xd, n, d, ldx, sigma, lambda, Wd, bd, s, o);
+  cudaStream_t st = h->stream;
+  if (ev_setup) KRR_CUDA(cudaEventRecord(ev_setup, st));
+  KRR_TRACE("pcg_solve: setup done");
+  SolveArgs a{Xd, n, d, ldx, sigma, lambda, Yd, k, ldy, Cd, ldc, o};
+  krr_status status;
+  if (o.precision == KRR_FP64)
+    status = solve_plain<double>(h, a, KRR_FP64, rep, matvecs);
+  else if (o.precision == KRR_FP32)
+    status = solve_plain<float>(h, a, KRR_FP32, rep, matvecs);
+  else
+    status = solve_mixed(h, a, rep, matvecs);
+  if (o.precision == KRR_MIXED && (tc_error(h->tc, st) || hp_error(h->hp, st)))
+    status = KRR_ETIMEOUT;
+  return status;
+}
+
+// (D o K)(Xr, Xc) V in FP64 (direct differences).
+void dsigma_dispatch(krr_handle* h, cudaStream_t st, const float* Xr, int nr, int ldxr,
+                     const float* Xc, int nc, int ldxc, int d, double sigma, const double* V,
+                     int k, int ldv, double* Q, int ldq) {
+  double* part = wsT<double>(h, "mv_part64", mv_fp64_part_elems(nr, nc, k));
+  launch_mv_fp64(st, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, 0.0, V, k, ldv, Q, ldq, part, 1);
+}
+
+// sum_{i, c} A[i, c] B[i, c] read back to the host.
+double host_dot(krr_handle* h, const double* A, int lda, const double* B, int ldb, int n, int k) {
+  double* part = wsT<double>(h, "cg_part", cg_part_elems(n, k));
+  double* dout = wsT<double>(h, "dot_out", 1);
+  unsigned int* ctr = wsT<unsigned int>(h, "dot_ctr", 4);
+  KRR_CUDA(cudaMemsetAsync(ctr, 0, 4 * sizeof(unsigned int), h->stream));
+  launch_dot_d(h->stream, A, lda, B, ldb, n, k, dout, part, ctr);
+  KRR_CUDA(cudaMemcpyAsync(h->hostd, dout, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  KRR_CUDA(cudaStreamSynchronize(h->stream));
+  return h->hostd[0];
 }
 
 }  // namespace
@@ -763,19 +873,7 @@ krr_status krr_pcg_solve(krr_handle* h, const float* X, int n, int d, int ldx, d
     else
       krr_default_opts(&o);
     KRR_REQUIRE(X && Y && C, "pcg_solve: null pointer");
-    KRR_REQUIRE(n > 0 && d > 0 && k >= 1 && k <= KRR_MAX_RHS, "pcg_solve: bad sizes");
-    KRR_REQUIRE(ldx >= d && ldy >= k && ldc >= k, "pcg_solve: leading dimension too small");
-    KRR_REQUIRE(sigma > 0.0 && std::isfinite(sigma), "pcg_solve: sigma must be > 0");
-    KRR_REQUIRE(lambda > 0.0 && std::isfinite(lambda), "pcg_solve: lambda must be > 0");
-    KRR_REQUIRE(o.tol > 0.0 && o.max_iter >= 0, "pcg_solve: bad tol / max_iter");
-    KRR_REQUIRE(o.precision == KRR_FP64 || o.precision == KRR_FP32 || o.precision == KRR_MIXED,
-                "pcg_solve: precision must be KRR_FP64, KRR_FP32 or KRR_MIXED");
-    if (o.precond) {
-      KRR_REQUIRE(W && b && s > 0 && s <= n, "pcg_solve: preconditioner needs W, b and 0 < s <= n");
-    }
-    if (o.precision == KRR_MIXED) {
-      KRR_REQUIRE(o.inner_tol > 0.0 && o.inner_tol < 1.0, "pcg_solve: inner_tol in (0, 1)");
-    }
+    check_solve_args(o, n, d, ldx, sigma, lambda, W, b, s, k, ldy, ldc);
     if (rep) {
       memset(rep, 0, sizeof(*rep));
       rep->k = k;
@@ -793,36 +891,14 @@ krr_status krr_pcg_solve(krr_handle* h, const float* X, int n, int d, int ldx, d
         KRR_CUDA(cudaMemcpyAsync(Cd, C, (size_t)n * ldc * sizeof(double), cudaMemcpyHostToDevice, st));
     }
     int matvecs = 0;
-    KRR_TRACE("pcg_solve: n=%d d=%d k=%d s=%d prec=%d graph=%d", n, d, k, s, o.precision, o.use_graph);
+    const float* Wd = nullptr;
+    const float* bd = nullptr;
     if (o.precond) {
-      const float* Wd = (const float*)stage_in(h, W, (size_t)d * s * sizeof(float), "W");
-      const float* bd = (const float*)stage_in(h, b, (size_t)s * sizeof(float), "b");
-      float* Z = wsT<float>(h, "rff_Z", (size_t)n * s);
-      launch_rff(st, Xd, n, d, ldx, Wd, bd, s, Z, s);
-      int zb = o.z_bf16 < 0 ? (o.precision == KRR_MIXED ? 1 : 0) : (o.z_bf16 ? 1 : 0);
-      double lp = o.lambda_p > 0.0 ? o.lambda_p : lambda;
-      precond_setup_impl(h, Z, n, s, s, lp, o.apply_form, zb);
+      Wd = (const float*)stage_in(h, W, (size_t)d * s * sizeof(float), "W");
+      bd = (const float*)stage_in(h, b, (size_t)s * sizeof(float), "b");
     }
-    if (o.precision == KRR_MIXED) {
-      tc_prepare(h->tc, st, Xd, n, ldx, d, sigma);
-      tc_clear_error(h->tc, st);
-      if (hp_supported(d)) {
-        hp_prepare(h->hp, st, Xd, n, ldx, d, sigma);
-        hp_clear_error(h->hp, st);
-      }
-    }
-    KRR_CUDA(cudaEventRecord(h->ev[1], st));
-    KRR_TRACE("pcg_solve: setup done");
-    SolveArgs a{Xd, n, d, ldx, sigma, lambda, Yd, k, ldy, Cd, ldc, o};
-    krr_status status;
-    if (o.precision == KRR_FP64)
-      status = solve_plain<double>(h, a, KRR_FP64, rep, &matvecs);
-    else if (o.precision == KRR_FP32)
-      status = solve_plain<float>(h, a, KRR_FP32, rep, &matvecs);
-    else
-      status = solve_mixed(h, a, rep, &matvecs);
-    if (o.precision == KRR_MIXED && (tc_error(h->tc, st) || hp_error(h->hp, st)))
-      status = KRR_ETIMEOUT;
+    krr_status status = solve_impl(h, Xd, n, d, ldx, sigma, lambda, Wd, bd, s, Yd, k, ldy, Cd,
+                                   ldc, o, rep, &matvecs, h->ev[1]);
     if (c_host)
       KRR_CUDA(cudaMemcpyAsync(C, Cd, (size_t)n * ldc * sizeof(double), cudaMemcpyDeviceToHost, st));
     KRR_CUDA(cudaEventRecord(h->ev[2], st));
@@ -873,6 +949,99 @@ krr_status krr_predict(krr_handle* h, const float* Xtr, int n, int ldxtr, const 
       KRR_CUDA(cudaStreamSynchronize(st));
     }
     return KRR_OK;
+  });
+}
+
+krr_status krr_kernel_dsigma_matvec(krr_handle* h, const float* Xr, int nr, int ldxr,
+                                    const float* Xc, int nc, int ldxc, int d, double sigma,
+                                    const double* V, int k, int ldv, double* Q, int ldq,
+                                    int precision) {
+  return guard(h, [&]() -> krr_status {
+    KRR_REQUIRE(Xr && Xc && V && Q, "kernel_dsigma_matvec: null pointer");
+    KRR_REQUIRE(nr > 0 && nc > 0 && d > 0, "kernel_dsigma_matvec: sizes must be positive");
+    KRR_REQUIRE(k >= 1 && k <= KRR_MAX_RHS, "kernel_dsigma_matvec: need 1 <= k <= KRR_MAX_RHS");
+    KRR_REQUIRE(ldxr >= d && ldxc >= d && ldv >= k && ldq >= k,
+                "kernel_dsigma_matvec: leading dimension too small");
+    KRR_REQUIRE(sigma > 0.0 && std::isfinite(sigma), "kernel_dsigma_matvec: sigma must be > 0");
+    KRR_REQUIRE(precision == KRR_FP64, "kernel_dsigma_matvec: precision must be KRR_FP64");
+    dsigma_dispatch(h, h->stream, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, V, k, ldv, Q, ldq);
+    return KRR_OK;
+  });
+}
+
+krr_status krr_hypergrad(krr_handle* h, const float* X, int n, int d, int ldx, const float* Xte,
+                         int m, int ldxte, double sigma, double lambda, const float* W,
+                         const float* b, int s, const double* C, int ldc, const double* GF, int k,
+                         int ldg, const krr_opts* opts, double* grad, double* Wadj, int ldw,
+                         krr_report* rep) {
+  return guard(h, [&]() -> krr_status {
+    krr_opts o;
+    if (opts)
+      o = *opts;
+    else
+      krr_default_opts(&o);
+    KRR_REQUIRE(X && Xte && C && GF && grad, "hypergrad: null pointer");
+    KRR_REQUIRE(m > 0 && ldxte >= d && ldg >= k, "hypergrad: bad held-out sizes");
+    KRR_REQUIRE(!Wadj || ldw >= k, "hypergrad: ldw too small");
+    KRR_REQUIRE(!o.warm_start, "hypergrad: warm_start is not supported for the adjoint solve");
+    check_solve_args(o, n, d, ldx, sigma, lambda, W, b, s, k, ldc, ldc);
+    if (rep) {
+      memset(rep, 0, sizeof(*rep));
+      rep->k = k;
+    }
+    cudaStream_t st = h->stream;
+    KRR_CUDA(cudaEventRecord(h->ev[0], st));
+    const float* Xd = (const float*)stage_in(h, X, (size_t)n * ldx * sizeof(float), "X");
+    const float* Xted = (const float*)stage_in(h, Xte, (size_t)m * ldxte * sizeof(float), "hXte");
+    const double* Cd = (const double*)stage_in(h, C, (size_t)n * ldc * sizeof(double), "hC");
+    const double* Gd = (const double*)stage_in(h, GF, (size_t)m * ldg * sizeof(double), "hG");
+    const float* Wd = nullptr;
+    const float* bd = nullptr;
+    if (o.precond) {
+      Wd = (const float*)stage_in(h, W, (size_t)d * s * sizeof(float), "W");
+      bd = (const float*)stage_in(h, b, (size_t)s * sizeof(float), "b");
+    }
+    const size_t nk = (size_t)n * k, mk = (size_t)m * k;
+    double* gbar = wsT<double>(h, "hg_gbar", nk);
+    double* wadj = wsT<double>(h, "hg_w", nk);
+    double* t_tr = wsT<double>(h, "hg_ttr", nk);
+    double* t_te = wsT<double>(h, "hg_tte", mk);
+    // gbar = K(X, Xte) g_f: the held-out gradient pulled back to the training points
+    matvec_dispatch(h, st, Xd, n, ldx, Xted, m, ldxte, d, sigma, 0.0, Gd, k, ldg, gbar, k,
+                    KRR_FP64);
+    // adjoint system (K + lambda I) w = gbar, the same operator as Eq. (1)
+    int matvecs = 1;
+    krr_status status = solve_impl(h, Xd, n, d, ldx, sigma, lambda, Wd, bd, s, gbar, k, k, wadj,
+                                   k, o, rep, &matvecs, h->ev[1]);
+    // (D_te o K_te) c and (D o K) c, then the three contractions
+    dsigma_dispatch(h, st, Xted, m, ldxte, Xd, n, ldx, d, sigma, Cd, k, ldc, t_te, k);
+    dsigma_dispatch(h, st, Xd, n, ldx, Xd, n, ldx, d, sigma, Cd, k, ldc, t_tr, k);
+    matvecs += 2;
+    const double w_c = host_dot(h, wadj, k, Cd, ldc, n, k);
+    const double g_t = host_dot(h, Gd, ldg, t_te, k, m, k);
+    const double w_t = host_dot(h, wadj, k, t_tr, k, n, k);
+    grad[0] = g_t - w_t;
+    grad[1] = -lambda * w_c;
+    if (Wadj) {
+      if (on_device(Wadj)) {
+        KRR_CUDA(cudaMemcpy2DAsync(Wadj, (size_t)ldw * sizeof(double), wadj, k * sizeof(double),
+                                   k * sizeof(double), n, cudaMemcpyDeviceToDevice, st));
+      } else {
+        KRR_CUDA(cudaMemcpy2DAsync(Wadj, (size_t)ldw * sizeof(double), wadj, k * sizeof(double),
+                                   k * sizeof(double), n, cudaMemcpyDeviceToHost, st));
+      }
+    }
+    KRR_CUDA(cudaEventRecord(h->ev[2], st));
+    KRR_CUDA(cudaEventSynchronize(h->ev[2]));
+    if (rep) {
+      rep->status = status;
+      rep->matvecs = matvecs;
+      rep->ms_setup = ms_between(h->ev[0], h->ev[1]);
+      rep->ms_solve = ms_between(h->ev[1], h->ev[2]);
+      rep->ms_total = ms_between(h->ev[0], h->ev[2]);
+    }
+    if (status != KRR_OK) h->err = krr_status_string(status);
+    return status;
   });
 }
 

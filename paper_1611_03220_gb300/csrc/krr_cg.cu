@@ -86,12 +86,14 @@ cg_init_kernel(CgScalars* sc, const double* __restrict__ Y, int ldy, const T* __
   sc->iter = 0;
   sc->max_iter = max_iter;
   sc->flags = 0;
+  int any = 0;
   for (int c = 0; c < KRR_MAX_RHS; ++c) {
     if (c < k) {
       sc->yy[c] = tot[c];
       sc->tol2[c] = tol * tol * tot[c];
       sc->rr[c] = tot[c];
       sc->active[c] = tot[c] > 0.0 ? 1 : 0;
+      any |= sc->active[c];
       if (bad(tot[c])) sc->flags |= FLAG_NAN;
     } else {
       sc->yy[c] = 0.0;
@@ -102,6 +104,7 @@ cg_init_kernel(CgScalars* sc, const double* __restrict__ Y, int ldy, const T* __
     sc->iters[c] = 0;
     sc->alpha[c] = sc->beta[c] = sc->rz[c] = sc->pq[c] = 0.0;
   }
+  sc->run = (any && max_iter > 0 && !(sc->flags & FLAG_NAN)) ? 1 : 0;
 }
 
 // rz = r.z, rr = r.r and p = z for the first iteration.
@@ -281,7 +284,21 @@ __global__ void cg_tail_kernel(CgScalars* sc, cudaGraphConditionalHandle cond) {
     sc->flags |= FLAG_CAP;
     stop = true;
   }
+  sc->run = stop ? 0 : 1;
   if (cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
+}
+
+__global__ void batch_gate_kernel(CgScalars* const* scs, const unsigned long long* conds,
+                                  int nsolve) {
+  for (int i = threadIdx.x; i < nsolve; i += blockDim.x)
+    cudaGraphSetConditional((cudaGraphConditionalHandle)conds[i], scs[i]->run ? 1u : 0u);
+}
+
+__global__ void batch_tail_kernel(CgScalars* const* scs, int nsolve,
+                                  cudaGraphConditionalHandle cond) {
+  int any = 0;
+  for (int i = 0; i < nsolve; ++i) any |= scs[i]->run;
+  cudaGraphSetConditional(cond, any ? 1u : 0u);
 }
 
 // ------------------------------------------------------------ elementwise --
@@ -334,6 +351,22 @@ colnorm2_kernel(const T* __restrict__ a, int n, int k, int lda, double* out, dou
   }
   if (!grid_colsum(v, k, part, counter, tot)) return;
   for (int c = 0; c < k; ++c) out[c] = tot[c];
+}
+
+// out[0] = sum_{i,c} a[i, c] b[i, c], one grid-wide FP64 sum.
+__global__ void __launch_bounds__(CT)
+dot_d_kernel(const double* __restrict__ a, int lda, const double* __restrict__ b, int ldb, int n,
+             int k, double* out, double* part, unsigned int* counter) {
+  double v[KRR_MAX_RHS], tot[KRR_MAX_RHS];
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c) v[c] = 0.0;
+  for (int i = blockIdx.x * CT + threadIdx.x; i < n; i += gridDim.x * CT) {
+    double s = 0.0;
+    for (int c = 0; c < k; ++c) s = fma(a[(size_t)i * lda + c], b[(size_t)i * ldb + c], s);
+    v[0] += s;
+  }
+  if (!grid_colsum(v, 1, part, counter, tot)) return;
+  out[0] = tot[0];
 }
 
 // Column mean in two deterministic passes: per-slab column sums, then the
@@ -416,6 +449,24 @@ void launch_cg_update_p(cudaStream_t st, CgScalars* sc, T* P, const T* Z, int n,
 
 void launch_cg_tail(cudaStream_t st, CgScalars* sc, unsigned long long cond) {
   cg_tail_kernel<<<1, 1, 0, st>>>(sc, (cudaGraphConditionalHandle)cond);
+  KRR_CHECK_LAUNCH();
+}
+
+void launch_batch_gate(cudaStream_t st, CgScalars* const* scs, const unsigned long long* conds,
+                       int nsolve) {
+  batch_gate_kernel<<<1, 128, 0, st>>>(scs, conds, nsolve);
+  KRR_CHECK_LAUNCH();
+}
+
+void launch_batch_tail(cudaStream_t st, CgScalars* const* scs, int nsolve,
+                       unsigned long long cond) {
+  batch_tail_kernel<<<1, 1, 0, st>>>(scs, nsolve, (cudaGraphConditionalHandle)cond);
+  KRR_CHECK_LAUNCH();
+}
+
+void launch_dot_d(cudaStream_t st, const double* a, int lda, const double* b, int ldb, int n,
+                  int k, double* out, double* part, unsigned int* counter) {
+  dot_d_kernel<<<cg_blocks(n), CT, 0, st>>>(a, lda, b, ldb, n, k, out, part, counter);
   KRR_CHECK_LAUNCH();
 }
 

@@ -72,6 +72,7 @@ struct CgScalars {
   int max_iter;
   int flags;                   // bit 0 breakdown, bit 1 NaN, bit 2 iteration cap
   int k;
+  int run;                     // 1 while the loop should execute another iteration
   unsigned int counter[8];     // last-block-done counters for reductions
 };
 
@@ -101,9 +102,11 @@ void launch_rff(cudaStream_t st, const float* X, int n, int d, int ldx, const fl
 // SIMT kernel products (krr_matvec_simt.cu).  part: scratch of
 // simt_part_elems(...) elements of the accumulator type.
 size_t mv_fp64_part_elems(int nr, int nc, int k);
+// dsigma = 1: Q = (D o K) V + shift V with D_ij = ||xr_i - xc_j||^2 / sigma^2
+// (the derivative of K with respect to log sigma).
 void launch_mv_fp64(cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
                     int nc, int ldxc, int d, double sigma, double shift, const double* V,
-                    int k, int ldv, double* Q, int ldq, double* part);
+                    int k, int ldv, double* Q, int ldq, double* part, int dsigma = 0);
 void launch_mv_fp64_capped(cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
                            int nc, int ldxc, int d, double sigma, double shift, const double* V,
                            int k, int ldv, double* Q, int ldq, double* part, size_t cap);
@@ -156,6 +159,13 @@ void launch_cg_update_p(cudaStream_t st, CgScalars* sc, T* P, const T* Z, int n,
 // iter += 1; decides whether the loop continues; sets the graph condition
 // when `cond` is nonzero (a cudaGraphConditionalHandle).
 void launch_cg_tail(cudaStream_t st, CgScalars* sc, unsigned long long cond);
+// Lockstep loops over several independent solves (one CgScalars each):
+// gate sets the IF condition `conds[i]` of solve i to scs[i]->run; tail sets
+// the WHILE condition `cond` to whether any solve still runs.
+void launch_batch_gate(cudaStream_t st, CgScalars* const* scs, const unsigned long long* conds,
+                       int nsolve);
+void launch_batch_tail(cudaStream_t st, CgScalars* const* scs, int nsolve,
+                       unsigned long long cond);
 
 // mu[t] = mean_i X[i, t] in FP64, deterministic (slab scratch: ceil(n/128) x d doubles)
 void launch_colmean(cudaStream_t st, const float* X, int n, int ld, int d, double* mu,
@@ -176,5 +186,8 @@ void launch_sub_d(cudaStream_t st, const double* y, int ldy, const double* a, in
 template <typename T>
 void launch_colnorm2(cudaStream_t st, const T* a, int n, int k, int lda, double* out,
                      double* part, unsigned int* counter);
+// out[0] = sum_{i, c} a[i, c] b[i, c] (FP64), written to device memory
+void launch_dot_d(cudaStream_t st, const double* a, int lda, const double* b, int ldb, int n,
+                  int k, double* out, double* part, unsigned int* counter);
 
 }  // namespace krr

@@ -30,6 +30,9 @@ int choose_split(int row_blocks, int col_tiles) {
   return ns;
 }
 
+// DS = 1 evaluates the derivative dK/dlog(sigma) = D o K instead of K, with
+// D_ij = ||x_i - x_j||^2 / sigma^2 = -2 g ||x_i - x_j||^2 (g = -1 / (2 sigma^2)).
+template <int DS>
 __global__ void __launch_bounds__(M64_ROWS)
 mv_fp64_kernel(const float* __restrict__ Xr, int nr, int ldxr,
                const float* __restrict__ Xc, int nc, int ldxc, int d, double g,
@@ -85,6 +88,7 @@ mv_fp64_kernel(const float* __restrict__ Xr, int nr, int ldxr,
 #pragma unroll
     for (int jj = 0; jj < M64_TJ; ++jj) {
       double kv = exp(g * acc[jj]);
+      if (DS) kv *= -2.0 * g * acc[jj];
 #pragma unroll
       for (int c = 0; c < KRR_MAX_RHS; ++c)
         if (c < k) q[c] = fma(kv, vs[jj][c], q[c]);
@@ -232,15 +236,19 @@ size_t mv_fp64_part_elems(int nr, int nc, int k) {
 
 void launch_mv_fp64(cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
                     int nc, int ldxc, int d, double sigma, double shift, const double* V,
-                    int k, int ldv, double* Q, int ldq, double* part) {
+                    int k, int ldv, double* Q, int ldq, double* part, int dsigma) {
   int rb = (nr + M64_ROWS - 1) / M64_ROWS;
   int ct = (nc + M64_TJ - 1) / M64_TJ;
   int ns = choose_split(rb, ct);
   int tps = (ct + ns - 1) / ns;
   ns = (ct + tps - 1) / tps;
   double g = -1.0 / (2.0 * sigma * sigma);
-  mv_fp64_kernel<<<dim3(rb, ns), M64_ROWS, 0, st>>>(Xr, nr, ldxr, Xc, nc, ldxc, d, g, V, k, ldv,
-                                                     part, tps);
+  if (dsigma)
+    mv_fp64_kernel<1><<<dim3(rb, ns), M64_ROWS, 0, st>>>(Xr, nr, ldxr, Xc, nc, ldxc, d, g, V, k,
+                                                          ldv, part, tps);
+  else
+    mv_fp64_kernel<0><<<dim3(rb, ns), M64_ROWS, 0, st>>>(Xr, nr, ldxr, Xc, nc, ldxc, d, g, V, k,
+                                                          ldv, part, tps);
   KRR_CHECK_LAUNCH();
   int nb = (int)std::min<size_t>(((size_t)nr * k + 255) / 256, (size_t)8 * sm_count());
   reduce_split_kernel<double, double><<<nb, 256, 0, st>>>(part, ns, nr, k, V, ldv, shift, Q, ldq);
@@ -261,8 +269,8 @@ void launch_mv_fp64_capped(cudaStream_t st, const float* Xr, int nr, int ldxr, c
   int tps = (ct + ns - 1) / ns;
   ns = (ct + tps - 1) / tps;
   double g = -1.0 / (2.0 * sigma * sigma);
-  mv_fp64_kernel<<<dim3(rb, ns), M64_ROWS, 0, st>>>(Xr, nr, ldxr, Xc, nc, ldxc, d, g, V, k, ldv,
-                                                     part, tps);
+  mv_fp64_kernel<0><<<dim3(rb, ns), M64_ROWS, 0, st>>>(Xr, nr, ldxr, Xc, nc, ldxc, d, g, V, k,
+                                                        ldv, part, tps);
   KRR_CHECK_LAUNCH();
   int nb = (int)std::min<size_t>(((size_t)nr * k + 255) / 256, (size_t)8 * sm_count());
   reduce_split_kernel<double, double><<<nb, 256, 0, st>>>(part, ns, nr, k, V, ldv, shift, Q, ldq);

@@ -256,6 +256,27 @@ def test_predict_at_training_points():
     np.testing.assert_allclose(F, P.Y - P.lam * C, rtol=1e-9, atol=1e-10)
 
 
+def test_kernel_dlogsigma_central_differences():
+    """D o K against Richardson-extrapolated central differences of K in log sigma."""
+    rng = np.random.default_rng(31)
+    Xa = rng.standard_normal((9, 5))
+    Xb = rng.standard_normal((7, 5))
+    sig = 1.7
+    G = O.kernel_dlogsigma(Xa, Xb, sig)
+    fd = []
+    for h in (1e-3, 5e-4):
+        fd.append((O.gaussian_kernel(Xa, Xb, sig * math.exp(h))
+                   - O.gaussian_kernel(Xa, Xb, sig * math.exp(-h))) / (2 * h))
+    rich = (4 * fd[1] - fd[0]) / 3
+    np.testing.assert_allclose(G, rich, rtol=1e-7, atol=1e-12)
+    # zero on the diagonal of a square set and never negative
+    Gs = O.kernel_dlogsigma(Xa, Xa, sig)
+    assert np.all(np.diag(Gs) == 0.0) and np.all(Gs >= 0.0)
+    # maximum of r^2/s^2 exp(-r^2/(2 s^2)) over r is 2/e, at r^2 = 2 s^2
+    x = np.array([[0.0], [math.sqrt(2.0) * sig]])
+    assert O.kernel_dlogsigma(x, x, sig)[0, 1] == pytest.approx(2.0 / math.e, rel=1e-14)
+
+
 @pytest.mark.parametrize("which", ["dlogsigma", "dloglambda"])
 def test_hypergrad_central_differences(which):
     P = ks.make_config(5, n=80, m=30, s=16)
