@@ -173,6 +173,40 @@ krr_status krr_pcg_solve(krr_handle* h, const float* X, int n, int d, int ldx,
                          const krr_opts* opts, krr_report* rep);
 
 /*
+ * One independent problem of a batch: the arguments of krr_pcg_solve for
+ * one system (K + lambda I) C = Y (Eq. (1)) with its own RFF draw.  Any
+ * pointer may be host or device memory.
+ */
+typedef struct krr_problem {
+  const float* X;   /* n x d (ldx) FP32 */
+  int n, d, ldx;
+  double sigma, lambda;
+  const float* W;   /* d x s FP32 (may be NULL when opts->precond == 0) */
+  const float* b;   /* s FP32 */
+  int s;
+  const double* Y;  /* n x k (ldy) */
+  int k, ldy;
+  double* C;        /* n x k (ldc), output */
+  int ldc;
+} krr_problem;
+
+/*
+ * Algorithm 1 for `nprob` independent problems of any sizes.  The paper
+ * solves one problem at a time; this call runs their PCG loops in lockstep
+ * inside one CUDA graph launch per refinement round: each problem's
+ * iteration sits under its own conditional node, so a converged problem
+ * stops costing launches while the others continue, and the graph runs
+ * the problems' kernels concurrently (largest n first).  Set-up (features,
+ * factors) runs per problem before the loop.  opts applies to every
+ * problem (KRR_FP64, KRR_FP32 or KRR_MIXED; warm_start must be 0).
+ * reps (may be NULL) receives nprob reports; their ms_* fields are the
+ * batch's times.  Returns KRR_OK when every problem converged, otherwise
+ * the status of the first problem (in the caller's order) that did not.
+ */
+krr_status krr_pcg_solve_batched(krr_handle* h, const krr_problem* probs, int nprob,
+                                 const krr_opts* opts, krr_report* reps);
+
+/*
  * Predictor f(x) = sum_i c_i k(x_i, x) (Section 1) at m held-out points:
  *   F = K(Xte, Xtr) C.  Xtr: n x d (ldxtr), Xte: m x d (ldxte) FP32,
  * C: n x k double (ldc), F: m x k double (ldf); host or device pointers

@@ -52,6 +52,13 @@ class krr_report(C.Structure):
                 "ms_setup": self.ms_setup, "ms_solve": self.ms_solve, "ms_total": self.ms_total}
 
 
+class krr_problem(C.Structure):
+    _fields_ = [("X", C.c_void_p), ("n", C.c_int), ("d", C.c_int), ("ldx", C.c_int),
+                ("sigma", C.c_double), ("lam", C.c_double), ("W", C.c_void_p),
+                ("b", C.c_void_p), ("s", C.c_int), ("Y", C.c_void_p), ("k", C.c_int),
+                ("ldy", C.c_int), ("C", C.c_void_p), ("ldc", C.c_int)]
+
+
 _vp, _i, _d = C.c_void_p, C.c_int, C.c_double
 _SIGS = {
     "krr_default_opts": (None, [C.POINTER(krr_opts)]),
@@ -66,6 +73,8 @@ _SIGS = {
     "krr_precond_apply": (_i, [_vp, _vp, _i, _i, _vp, _i]),
     "krr_pcg_solve": (_i, [_vp, _vp, _i, _i, _i, _d, _d, _vp, _vp, _i, _vp, _i, _i, _vp, _i,
                            C.POINTER(krr_opts), C.POINTER(krr_report)]),
+    "krr_pcg_solve_batched": (_i, [_vp, C.POINTER(krr_problem), _i, C.POINTER(krr_opts),
+                                   C.POINTER(krr_report)]),
     "krr_predict": (_i, [_vp, _vp, _i, _i, _vp, _i, _i, _i, _d, _vp, _i, _i, _vp, _i, _i]),
     "krr_kernel_matvec_fp64_noalloc": (_i, [_vp, _i, _i, _vp, _i, _i, _i, _d, _d, _vp, _i, _i,
                                             _vp, _i, _vp]),
@@ -231,6 +240,35 @@ def krr_pcg_solve(h: Handle, X, sigma: float, lam: float, W, b, Y, C_out, opts: 
         h._check(st)
     out = rep.as_dict()
     out["status_code"] = st
+    return out
+
+
+def krr_pcg_solve_batched(h: Handle, problems, opts: krr_opts | None = None,
+                          check: bool = True) -> list[dict]:
+    """Algorithm 1 for independent problems in lockstep (one graph launch per round).
+
+    ``problems``: a sequence of ``(X, sigma, lam, W, b, Y, C_out)`` tuples of
+    host (numpy) or device (torch) buffers, shapes as for ``krr_pcg_solve``.
+    Returns one report dict per problem; with ``check`` a non-OK status raises.
+    """
+    arr = (krr_problem * len(problems))()
+    for i, (X, sigma, lam, W, b, Y, Cout) in enumerate(problems):
+        n, d = X.shape
+        arr[i] = krr_problem(_ptr(X), n, d, _ld(X), float(sigma), float(lam),
+                             _ptr(W) if W is not None else None,
+                             _ptr(b) if b is not None else None,
+                             W.shape[1] if W is not None else 0,
+                             _ptr(Y), Y.shape[1], _ld(Y), _ptr(Cout), _ld(Cout))
+    reps = (krr_report * len(problems))()
+    o = opts if opts is not None else default_opts()
+    st = _lib.krr_pcg_solve_batched(h.ptr, arr, len(problems), C.byref(o), reps)
+    if check:
+        h._check(st)
+    out = []
+    for r in reps:
+        dct = r.as_dict()
+        dct["status_code"] = r.status
+        out.append(dct)
     return out
 
 

@@ -36,6 +36,7 @@ struct krr_handle {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   TcState tc;
   HpState hp;
+  std::vector<krr_handle*> subs;  // per-problem handles of krr_pcg_solve_batched
 };
 
 namespace krr {
@@ -717,6 +718,364 @@ double host_dot(krr_handle* h, const double* A, int lda, const double* B, int ld
   return h->hostd[0];
 }
 
+// ---------------------------------------------------------- batched solve --
+// Captures what `f` enqueues on the handle's capture stream into graph `g`
+// after the nodes `deps`; returns the number of kernel launches captured.
+template <typename F>
+long long capture_into(krr_handle* h, cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                       F&& f) {
+  KRR_CUDA(cudaStreamBeginCaptureToGraph(h->cap, g, deps, nullptr, ndeps,
+                                         cudaStreamCaptureModeRelaxed));
+  capture_begin();
+  try {
+    f(h->cap);
+  } catch (...) {
+    capture_end();
+    cudaGraph_t tmp;
+    cudaStreamEndCapture(h->cap, &tmp);
+    cudaGetLastError();
+    throw;
+  }
+  long long n = capture_end();
+  cudaGraph_t out = nullptr;
+  KRR_CUDA(cudaStreamEndCapture(h->cap, &out));
+  return n;
+}
+
+// One solve of a lockstep batch: its handle (workspace, scalars, factors,
+// product state) and its loop body.
+struct BatchEntry {
+  krr_handle* sub = nullptr;
+  std::function<void(cudaStream_t)> body;
+  long long body_launches = 0;
+};
+
+// Runs the loop bodies of independent PCG solves in lockstep in one graph
+// launch.  Graph: WHILE { gate -> IF_0 { body_0 } ... IF_{m-1} { body_{m-1} }
+// -> tail }.  The gate sets IF_i from solve i's `run` flag, so a finished
+// solve launches nothing; the IF nodes have no edges between them, so the
+// graph executor may run the solves' kernels concurrently; the tail keeps
+// the loop going while any solve runs.  pcg_begin must have run for every
+// entry.
+void pcg_loop_batched(krr_handle* h, std::vector<BatchEntry>& E) {
+  const int ne = (int)E.size();
+  if (ne == 0) return;
+  cudaStream_t st = h->stream;
+  CgScalars** d_scs = wsT<CgScalars*>(h, "bt_scs", ne);
+  unsigned long long* d_cond = wsT<unsigned long long>(h, "bt_cond", ne);
+  std::vector<CgScalars*> scs(ne);
+  std::vector<unsigned long long> conds(ne);
+  for (int i = 0; i < ne; ++i) scs[i] = E[i].sub->sc;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  KRR_CUDA(cudaGraphCreate(&graph, 0));
+  long long fixed = 0;
+  try {
+    cudaGraphConditionalHandle wcond;
+    KRR_CUDA(cudaGraphConditionalHandleCreate(&wcond, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams wp = {cudaGraphNodeTypeConditional};
+    wp.conditional.handle = wcond;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    KRR_CUDA(cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &wp));
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    for (int i = 0; i < ne; ++i) {
+      cudaGraphConditionalHandle c;
+      KRR_CUDA(cudaGraphConditionalHandleCreate(&c, body, 0, 0));
+      conds[i] = (unsigned long long)c;
+    }
+    KRR_CUDA(cudaMemcpyAsync(d_scs, scs.data(), ne * sizeof(CgScalars*), cudaMemcpyHostToDevice,
+                             st));
+    KRR_CUDA(cudaMemcpyAsync(d_cond, conds.data(), ne * sizeof(unsigned long long),
+                             cudaMemcpyHostToDevice, st));
+    fixed += capture_into(h, body, nullptr, 0,
+                          [&](cudaStream_t cs) { launch_batch_gate(cs, d_scs, d_cond, ne); });
+    size_t nn = 1;
+    cudaGraphNode_t gate = nullptr;
+    KRR_CUDA(cudaGraphGetNodes(body, &gate, &nn));
+    KRR_REQUIRE(nn == 1 && gate, "batched loop: unexpected gate graph");
+    std::vector<cudaGraphNode_t> ifn(ne);
+    for (int i = 0; i < ne; ++i) {
+      cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
+      ip.conditional.handle = (cudaGraphConditionalHandle)conds[i];
+      ip.conditional.type = cudaGraphCondTypeIf;
+      ip.conditional.size = 1;
+      KRR_CUDA(cudaGraphAddNode(&ifn[i], body, &gate, nullptr, 1, &ip));
+      E[i].body_launches =
+          capture_into(h, ip.conditional.phGraph_out[0], nullptr, 0, E[i].body);
+    }
+    fixed += capture_into(h, body, ifn.data(), ifn.size(), [&](cudaStream_t cs) {
+      launch_batch_tail(cs, d_scs, ne, (unsigned long long)wcond);
+    });
+    KRR_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    KRR_CUDA(cudaGraphLaunch(exec, st));
+    KRR_CUDA(cudaStreamSynchronize(st));
+  } catch (...) {
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    throw;
+  }
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  int rounds = 0;
+  for (int i = 0; i < ne; ++i) {
+    krr_handle* g = E[i].sub;
+    KRR_CUDA(cudaMemcpyAsync(g->sc_host, g->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+  }
+  KRR_CUDA(cudaStreamSynchronize(st));
+  for (int i = 0; i < ne; ++i) {
+    const int it = E[i].sub->sc_host->iter;
+    rounds = std::max(rounds, it);
+    add_launches(E[i].body_launches * (long long)it);
+  }
+  add_launches(fixed * (long long)rounds);
+}
+
+// A problem of krr_pcg_solve_batched with its device operands and progress.
+struct BItem {
+  int idx = 0;                   // position in the caller's array
+  krr_handle* sub = nullptr;
+  const float* X = nullptr;
+  int n = 0, d = 0, ldx = 0, k = 0, ldy = 0, ldc = 0, s = 0;
+  double sigma = 0.0, lambda = 0.0;
+  const double* Y = nullptr;
+  double* C = nullptr;           // device result (the caller's or a staging copy)
+  double* C_user = nullptr;
+  bool c_host = false;
+  bool done = false;
+  krr_status status = KRR_OK;
+  int matvecs = 0, outer = 0, remaining = 0;
+  int iters[KRR_MAX_RHS] = {0};
+  double rel[KRR_MAX_RHS] = {0};
+  double yy[KRR_MAX_RHS] = {0};
+  ColScale inv;
+};
+
+ColScale ones() {
+  ColScale one;
+  for (int c = 0; c < KRR_MAX_RHS; ++c) one.v[c] = 1.0;
+  return one;
+}
+
+template <typename T>
+PcgSpec<T> item_spec(BItem& it, const double* Ytol, double tol, int prec, bool precond) {
+  krr_handle* g = it.sub;
+  const size_t nk = (size_t)it.n * it.k;
+  PcgSpec<T> S;
+  S.n = it.n;
+  S.k = it.k;
+  S.Ytol = Ytol;
+  S.ldy = it.k;
+  const bool f = sizeof(T) == 4;
+  S.x = wsT<T>(g, f ? "v_xf" : "v_x", nk);
+  S.r = wsT<T>(g, f ? "v_rf" : "v_r", nk);
+  S.p = wsT<T>(g, f ? "v_pf" : "v_p", nk);
+  S.z = wsT<T>(g, f ? "v_zf" : "v_z", nk);
+  S.q = wsT<T>(g, f ? "v_qf" : "v_q", nk);
+  S.tol = tol;
+  S.max_iter = it.remaining;
+  S.prec = prec;
+  const float* X = it.X;
+  const int n = it.n, ldx = it.ldx, d = it.d, k = it.k;
+  const double sigma = it.sigma, lambda = it.lambda;
+  S.matvec = [g, X, n, ldx, d, sigma, lambda, k, prec](cudaStream_t s2, const T* V, T* Q) {
+    matvec_dispatch(g, s2, X, n, ldx, X, n, ldx, d, sigma, lambda, V, k, k, Q, k, prec);
+  };
+  if (precond)
+    S.apply = [g, k](cudaStream_t s2, const T* R, T* Zo) { apply_precond<T>(g, s2, R, k, k, Zo, k); };
+  return S;
+}
+
+// Per-column relative residual ||Rd_c|| / ||y_c|| of an item (host read).
+bool item_converged(BItem& it, const double* Rd, double tol, double* rr) {
+  host_colnorm2<double>(it.sub, Rd, it.n, it.k, it.k, rr);
+  bool ok = true;
+  for (int c = 0; c < it.k; ++c) {
+    double rel = it.yy[c] > 0 ? std::sqrt(rr[c] / it.yy[c]) : 0.0;
+    it.rel[c] = rel;
+    if (!std::isfinite(rel)) it.status = KRR_ENAN;
+    if (!(rel <= tol)) ok = false;
+  }
+  return ok;
+}
+
+// Plain PCG (FP64 or FP32 vectors) for every item in lockstep; FP64 true
+// residual after each round, FP64 items restart from it up to three times.
+template <typename T>
+void batched_plain(krr_handle* h, std::vector<BItem>& B, const krr_opts& o, int prec) {
+  const ColScale one = ones();
+  for (BItem& it : B) {
+    krr_handle* g = it.sub;
+    const size_t nk = (size_t)it.n * it.k;
+    double* Yc = wsT<double>(g, "v_y", nk);
+    launch_convert<double, double>(g->stream, it.Y, it.n, it.k, it.ldy, Yc, it.k, one);
+    host_colnorm2<double>(g, Yc, it.n, it.k, it.k, it.yy);
+    PcgSpec<T> S = item_spec<T>(it, Yc, o.tol, prec, o.precond != 0);
+    KRR_CUDA(cudaMemsetAsync(S.x, 0, nk * sizeof(T), g->stream));
+    launch_convert<double, T>(g->stream, Yc, it.n, it.k, it.k, S.r, it.k, one);
+    it.remaining = o.max_iter;
+  }
+  std::vector<bool> pending(B.size(), true);
+  for (;;) {
+    std::vector<BatchEntry> E;
+    std::vector<int> act;
+    for (size_t i = 0; i < B.size(); ++i) {
+      BItem& it = B[i];
+      if (it.done || !pending[i]) continue;
+      double* Yc = wsT<double>(it.sub, "v_y", (size_t)it.n * it.k);
+      PcgSpec<T> S = item_spec<T>(it, Yc, o.tol, prec, o.precond != 0);
+      pcg_begin<T>(it.sub, S);
+      krr_handle* g = it.sub;
+      E.push_back(BatchEntry{g, [g, S](cudaStream_t cs) { pcg_body<T>(g, S, cs, 0ull); }, 0});
+      act.push_back((int)i);
+    }
+    if (E.empty()) break;
+    if (o.max_iter > 0) pcg_loop_batched(h, E);
+    for (int i : act) {
+      BItem& it = B[i];
+      krr_handle* g = it.sub;
+      pending[i] = false;
+      LoopOut lo;
+      pcg_finish(g, it.k, &lo);
+      for (int c = 0; c < it.k; ++c) it.iters[c] += lo.iters[c];
+      it.remaining -= lo.iter;
+      it.matvecs += lo.iter;
+      if (lo.flags & FLAG_NAN) {
+        it.status = KRR_ENAN;
+        it.done = true;
+        continue;
+      }
+      if (lo.flags & FLAG_BREAKDOWN) {
+        it.status = KRR_EBREAKDOWN;
+        it.done = true;
+        continue;
+      }
+      const size_t nk = (size_t)it.n * it.k;
+      double* Yc = wsT<double>(g, "v_y", nk);
+      double* xd = wsT<double>(g, "v_xd", nk);
+      double* AX = wsT<double>(g, "v_ax", nk);
+      double* Rd = wsT<double>(g, "v_rd", nk);
+      PcgSpec<T> S = item_spec<T>(it, Yc, o.tol, prec, o.precond != 0);
+      launch_convert<T, double>(g->stream, S.x, it.n, it.k, it.k, xd, it.k, one);
+      matvec_dispatch(g, g->stream, it.X, it.n, it.ldx, it.X, it.n, it.ldx, it.d, it.sigma,
+                      it.lambda, xd, it.k, it.k, AX, it.k, prec == KRR_FP64 ? KRR_FP64 : KRR_HP);
+      ++it.matvecs;
+      launch_sub_d(g->stream, Yc, it.k, AX, it.k, it.n, it.k, Rd, it.k);
+      double rr[KRR_MAX_RHS];
+      if (item_converged(it, Rd, o.tol, rr) && it.status == KRR_OK) {
+        it.done = true;
+      } else if (it.status != KRR_OK || (lo.flags & FLAG_CAP) || it.remaining <= 0 ||
+                 prec != KRR_FP64 || it.outer >= 3) {
+        if (it.status == KRR_OK) it.status = KRR_ENOTCONV;
+        it.done = true;
+      } else {
+        ++it.outer;
+        launch_convert<double, T>(g->stream, Rd, it.n, it.k, it.k, S.r, it.k, one);
+        pending[i] = true;
+      }
+    }
+  }
+  for (BItem& it : B) {
+    PcgSpec<T> S = item_spec<T>(it, nullptr, o.tol, prec, false);
+    launch_convert<T, double>(it.sub->stream, S.x, it.n, it.k, it.k, it.C, it.ldc, one);
+  }
+}
+
+// Mixed precision for every item: rounds of lockstep BF16 inner PCG on the
+// scaled residuals, each followed by the HP residual of every item.
+void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
+  const ColScale one = ones();
+  for (BItem& it : B) {
+    krr_handle* g = it.sub;
+    const size_t nk = (size_t)it.n * it.k;
+    double* Yc = wsT<double>(g, "v_y", nk);
+    double* Cd = wsT<double>(g, "v_cd", nk);
+    double* Rd = wsT<double>(g, "v_rd", nk);
+    wsT<double>(g, "v_ax", nk);
+    wsT<double>(g, "v_rs", nk);
+    launch_convert<double, double>(g->stream, it.Y, it.n, it.k, it.ldy, Yc, it.k, one);
+    KRR_CUDA(cudaMemsetAsync(Cd, 0, nk * sizeof(double), g->stream));
+    KRR_CUDA(cudaMemcpyAsync(Rd, Yc, nk * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+    host_colnorm2<double>(g, Yc, it.n, it.k, it.k, it.yy);
+    it.remaining = o.max_iter;
+  }
+  for (;;) {
+    std::vector<BatchEntry> E;
+    std::vector<int> act;
+    for (size_t i = 0; i < B.size(); ++i) {
+      BItem& it = B[i];
+      if (it.done) continue;
+      krr_handle* g = it.sub;
+      const size_t nk = (size_t)it.n * it.k;
+      double* Rd = wsT<double>(g, "v_rd", nk);
+      double* Rs = wsT<double>(g, "v_rs", nk);
+      double rr[KRR_MAX_RHS];
+      const bool ok = item_converged(it, Rd, o.tol, rr);
+      if (it.status != KRR_OK || ok) {
+        it.done = true;
+        continue;
+      }
+      if (it.outer >= o.max_outer || it.remaining <= 0) {
+        it.status = KRR_ENOTCONV;
+        it.done = true;
+        continue;
+      }
+      ++it.outer;
+      ColScale sc;
+      for (int c = 0; c < KRR_MAX_RHS; ++c) sc.v[c] = it.inv.v[c] = 0.0;
+      for (int c = 0; c < it.k; ++c)
+        if (it.rel[c] > o.tol) {
+          sc.v[c] = 1.0 / std::sqrt(rr[c]);
+          it.inv.v[c] = std::sqrt(rr[c]);
+        }
+      PcgSpec<float> S = item_spec<float>(it, Rs, o.inner_tol, KRR_BF16, o.precond != 0);
+      launch_convert<double, double>(g->stream, Rd, it.n, it.k, it.k, Rs, it.k, sc);
+      launch_convert<double, float>(g->stream, Rs, it.n, it.k, it.k, S.r, it.k, one);
+      KRR_CUDA(cudaMemsetAsync(S.x, 0, nk * sizeof(float), g->stream));
+      pcg_begin<float>(g, S);
+      E.push_back(BatchEntry{g, [g, S](cudaStream_t cs) { pcg_body<float>(g, S, cs, 0ull); }, 0});
+      act.push_back((int)i);
+    }
+    if (E.empty()) break;
+    pcg_loop_batched(h, E);
+    for (int i : act) {
+      BItem& it = B[i];
+      krr_handle* g = it.sub;
+      LoopOut lo;
+      pcg_finish(g, it.k, &lo);
+      for (int c = 0; c < it.k; ++c) it.iters[c] += lo.iters[c];
+      it.remaining -= lo.iter;
+      it.matvecs += lo.iter;
+      if (lo.flags & FLAG_NAN) {
+        it.status = KRR_ENAN;
+        it.done = true;
+        continue;
+      }
+      const size_t nk = (size_t)it.n * it.k;
+      double* Yc = wsT<double>(g, "v_y", nk);
+      double* Cd = wsT<double>(g, "v_cd", nk);
+      double* Rd = wsT<double>(g, "v_rd", nk);
+      double* AX = wsT<double>(g, "v_ax", nk);
+      const float* xf = wsT<float>(g, "v_xf", nk);
+      launch_axpy_d<float>(g->stream, xf, it.n, it.k, it.k, Cd, it.k, it.inv);
+      matvec_dispatch(g, g->stream, it.X, it.n, it.ldx, it.X, it.n, it.ldx, it.d, it.sigma,
+                      it.lambda, Cd, it.k, it.k, AX, it.k, KRR_HP);
+      ++it.matvecs;
+      launch_sub_d(g->stream, Yc, it.k, AX, it.k, it.n, it.k, Rd, it.k);
+    }
+  }
+  for (BItem& it : B) {
+    krr_handle* g = it.sub;
+    const size_t nk = (size_t)it.n * it.k;
+    double* Cd = wsT<double>(g, "v_cd", nk);
+    launch_convert<double, double>(g->stream, Cd, it.n, it.k, it.k, it.C, it.ldc, one);
+    if (tc_error(g->tc, g->stream) || hp_error(g->hp, g->stream)) {
+      it.status = KRR_ETIMEOUT;
+    }
+  }
+}
+
 }  // namespace
 
 // ======================================================================= ABI
@@ -789,6 +1148,8 @@ krr_status krr_destroy(krr_handle* h) {
   free_buf(h->pc.Linv);
   free_buf(h->pc.LinvT);
   free_buf(h->pc.U);
+  for (krr_handle* sub : h->subs) krr_destroy(sub);
+  h->subs.clear();
   tc_release(h->tc);
   hp_release(h->hp);
   if (h->sc) cudaFree(h->sc);
@@ -912,6 +1273,116 @@ krr_status krr_pcg_solve(krr_handle* h, const float* X, int n, int d, int ldx, d
     }
     if (status != KRR_OK) h->err = krr_status_string(status);
     return status;
+  });
+}
+
+krr_status krr_pcg_solve_batched(krr_handle* h, const krr_problem* probs, int nprob,
+                                 const krr_opts* opts, krr_report* reps) {
+  return guard(h, [&]() -> krr_status {
+    krr_opts o;
+    if (opts)
+      o = *opts;
+    else
+      krr_default_opts(&o);
+    KRR_REQUIRE(probs && nprob > 0, "pcg_solve_batched: need nprob > 0 problems");
+    KRR_REQUIRE(!o.warm_start, "pcg_solve_batched: warm_start is not supported");
+    for (int i = 0; i < nprob; ++i) {
+      const krr_problem& p = probs[i];
+      KRR_REQUIRE(p.X && p.Y && p.C, "pcg_solve_batched: null pointer in problem " +
+                                         std::to_string(i));
+      check_solve_args(o, p.n, p.d, p.ldx, p.sigma, p.lambda, p.W, p.b, p.s, p.k, p.ldy, p.ldc);
+    }
+    cudaStream_t st = h->stream;
+    while ((int)h->subs.size() < nprob) {
+      krr_handle* sub = nullptr;
+      krr_status cs = krr_create(&sub, (void*)st);
+      if (cs != KRR_OK) throw Error{cs, "pcg_solve_batched: could not create a problem handle"};
+      h->subs.push_back(sub);
+    }
+    KRR_CUDA(cudaEventRecord(h->ev[0], st));
+    // largest problems first: their graph branches are issued first
+    std::vector<int> order(nprob);
+    for (int i = 0; i < nprob; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      const double wa = (double)probs[a].n * probs[a].n * (probs[a].d + probs[a].k);
+      const double wb = (double)probs[b].n * probs[b].n * (probs[b].d + probs[b].k);
+      return wa > wb;
+    });
+    std::vector<BItem> B(nprob);
+    for (int j = 0; j < nprob; ++j) {
+      const int i = order[j];
+      const krr_problem& p = probs[i];
+      BItem& it = B[j];
+      krr_handle* g = h->subs[j];
+      g->stream = st;
+      g->err.clear();
+      it.idx = i;
+      it.sub = g;
+      it.n = p.n;
+      it.d = p.d;
+      it.ldx = p.ldx;
+      it.k = p.k;
+      it.ldy = p.ldy;
+      it.ldc = p.ldc;
+      it.s = p.s;
+      it.sigma = p.sigma;
+      it.lambda = p.lambda;
+      it.X = (const float*)stage_in(g, p.X, (size_t)p.n * p.ldx * sizeof(float), "X");
+      it.Y = (const double*)stage_in(g, p.Y, (size_t)p.n * p.ldy * sizeof(double), "Y");
+      it.C_user = p.C;
+      it.c_host = !on_device(p.C);
+      it.C = it.c_host ? wsT<double>(g, "stage_C", (size_t)p.n * p.ldc) : p.C;
+      const float* Wd = nullptr;
+      const float* bd = nullptr;
+      if (o.precond) {
+        Wd = (const float*)stage_in(g, p.W, (size_t)p.d * p.s * sizeof(float), "W");
+        bd = (const float*)stage_in(g, p.b, (size_t)p.s * sizeof(float), "b");
+      }
+      setup_impl(g, it.X, p.n, p.d, p.ldx, p.sigma, p.lambda, Wd, bd, p.s, o);
+    }
+    KRR_CUDA(cudaEventRecord(h->ev[1], st));
+    if (o.precision == KRR_FP64)
+      batched_plain<double>(h, B, o, KRR_FP64);
+    else if (o.precision == KRR_FP32)
+      batched_plain<float>(h, B, o, KRR_FP32);
+    else
+      batched_mixed(h, B, o);
+    for (BItem& it : B)
+      if (it.c_host)
+        KRR_CUDA(cudaMemcpyAsync(it.C_user, it.C, (size_t)it.n * it.ldc * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+    KRR_CUDA(cudaEventRecord(h->ev[2], st));
+    KRR_CUDA(cudaEventSynchronize(h->ev[2]));
+    krr_status first = KRR_OK;
+    std::vector<krr_status> by_idx(nprob, KRR_OK);
+    for (BItem& it : B) by_idx[it.idx] = it.status;
+    for (int i = 0; i < nprob; ++i)
+      if (by_idx[i] != KRR_OK) {
+        first = by_idx[i];
+        break;
+      }
+    if (reps) {
+      const double ms_setup = ms_between(h->ev[0], h->ev[1]);
+      const double ms_solve = ms_between(h->ev[1], h->ev[2]);
+      const double ms_total = ms_between(h->ev[0], h->ev[2]);
+      for (BItem& it : B) {
+        krr_report& r = reps[it.idx];
+        memset(&r, 0, sizeof(r));
+        r.status = it.status;
+        r.k = it.k;
+        for (int c = 0; c < it.k; ++c) {
+          r.iters[c] = it.iters[c];
+          r.rel_res[c] = it.rel[c];
+        }
+        r.outer_steps = it.outer;
+        r.matvecs = it.matvecs;
+        r.ms_setup = ms_setup;
+        r.ms_solve = ms_solve;
+        r.ms_total = ms_total;
+      }
+    }
+    if (first != KRR_OK) h->err = krr_status_string(first);
+    return first;
   });
 }
 

@@ -60,7 +60,7 @@ def test_status_strings_without_gpu(lib_path):
 
 
 def test_struct_layout_matches_c_compiler(lib_path):
-    """The ctypes mirrors of krr_opts / krr_report have the C layout."""
+    """The ctypes mirrors of krr_opts / krr_report / krr_problem have the C layout."""
     from paper_1611_03220_gb300 import _krr
     src = r'''
 #include <stdio.h>
@@ -70,6 +70,9 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(krr_opts), offsetof(krr_opts, inner_tol),
          offsetof(krr_opts, warm_start), sizeof(krr_report), offsetof(krr_report, rel_res),
          offsetof(krr_report, ms_total));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(krr_problem), offsetof(krr_problem, sigma),
+         offsetof(krr_problem, s), offsetof(krr_problem, Y), offsetof(krr_problem, C),
+         offsetof(krr_problem, ldc));
   return 0;
 }
 '''
@@ -80,6 +83,8 @@ int main(void) {
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True,
                                                check=True).stdout.split()]
-    O, R = _krr.krr_opts, _krr.krr_report
+    O, R, P = _krr.krr_opts, _krr.krr_report, _krr.krr_problem
     assert vals == [ctypes.sizeof(O), O.inner_tol.offset, O.warm_start.offset, ctypes.sizeof(R),
-                    R.rel_res.offset, R.ms_total.offset]
+                    R.rel_res.offset, R.ms_total.offset,
+                    ctypes.sizeof(P), P.sigma.offset, P.s.offset, P.Y.offset, P.C.offset,
+                    P.ldc.offset]
