@@ -208,8 +208,11 @@ void matvec_dispatch(krr_handle* h, cudaStream_t st, const float* Xr, int nr, in
 void matvec_reserve(krr_handle* h, int n, int k, int prec) {
   switch (prec) {
     case KRR_FP64:
+      wsT<double>(h, "mv_part64", mv_fp64_part_elems(n, n, k));
+      return;
     case KRR_HP:
       wsT<double>(h, "mv_part64", mv_fp64_part_elems(n, n, k));
+      if (h->hp.ready) hp_reserve(h->hp, h->stream, k);
       return;
     case KRR_FP32:
       wsT<float>(h, "mv_part32", mv_fp32_part_elems(n, n, k));
@@ -547,11 +550,8 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
   double* Rd = wsT<double>(h, "v_rd", nk);
   double* AX = wsT<double>(h, "v_ax", nk);
   double* Rs = wsT<double>(h, "v_rs", nk);  // scaled residual (inner tolerance reference)
-  float* x = wsT<float>(h, "v_xf", nk);
-  float* r = wsT<float>(h, "v_rf", nk);
-  float* p = wsT<float>(h, "v_pf", nk);
-  float* z = wsT<float>(h, "v_zf", nk);
-  float* q = wsT<float>(h, "v_qf", nk);
+  double* Cp = wsT<double>(h, "v_cprev", nk);
+  double* Rp = wsT<double>(h, "v_rprev", nk);
   ColScale one;
   for (int c = 0; c < KRR_MAX_RHS; ++c) one.v[c] = 1.0;
   launch_convert<double, double>(st, a.Y, n, k, a.ldy, Yc, k, one);
@@ -567,64 +567,119 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
   }
   double yy[KRR_MAX_RHS];
   host_colnorm2<double>(h, Yc, n, k, k, yy);
-  auto mv = [&](cudaStream_t s2, const float* V, float* Q) {
-    matvec_dispatch(h, s2, a.X, n, a.ldx, a.X, n, a.ldx, a.d, a.sigma, a.lambda, V, k, k, Q, k,
-                    KRR_BF16);
-  };
-  std::function<void(cudaStream_t, const float*, float*)> ap;
-  if (a.o.precond)
-    ap = [&](cudaStream_t s2, const float* R, float* Zo) {
-      apply_precond<float>(h, s2, R, k, k, Zo, k);
-    };
   int total_iters[KRR_MAX_RHS] = {0};
   krr_status status = KRR_OK;
   int outer = 0;
   int remaining = a.o.max_iter;
+  // inner solves on the HP product once a BF16 correction contracts the
+  // residual by less than a half (see batched_mixed)
+  bool hp_inner = false;
+  double rel_prev = 0.0;
+  double rel[KRR_MAX_RHS] = {0}, rel_saved[KRR_MAX_RHS] = {0};
   for (;;) {
     double rr[KRR_MAX_RHS];
     host_colnorm2<double>(h, Rd, n, k, k, rr);
-    bool ok = true;
-    ColScale sc, inv;
-    for (int c = 0; c < KRR_MAX_RHS; ++c) sc.v[c] = inv.v[c] = 0.0;
+    bool ok = true, finite = true;
+    double now = 0.0;
     for (int c = 0; c < k; ++c) {
-      double rel = yy[c] > 0 ? std::sqrt(rr[c] / yy[c]) : 0.0;
-      if (rep) rep->rel_res[c] = rel;
-      if (!std::isfinite(rel)) {
-        status = KRR_ENAN;
-      } else if (rel > a.o.tol) {
-        ok = false;
-        sc.v[c] = 1.0 / std::sqrt(rr[c]);
-        inv.v[c] = std::sqrt(rr[c]);
+      rel[c] = yy[c] > 0 ? std::sqrt(rr[c] / yy[c]) : 0.0;
+      if (!std::isfinite(rel[c])) finite = false;
+      if (!(rel[c] <= a.o.tol)) ok = false;
+      now = std::max(now, rel[c]);
+    }
+    if (finite && ok) break;
+    if (outer > 0) {
+      if (!finite || !(now < rel_prev)) {
+        // the last correction did not help: take it back
+        KRR_CUDA(cudaMemcpyAsync(Cd, Cp, nk * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        KRR_CUDA(cudaMemcpyAsync(Rd, Rp, nk * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        host_colnorm2<double>(h, Rd, n, k, k, rr);
+        for (int c = 0; c < k; ++c) rel[c] = rel_saved[c];
+        finite = true;
+        if (hp_inner) {
+          status = KRR_ENOTCONV;
+          break;
+        }
+        hp_inner = true;
+      } else if (now > 0.5 * rel_prev) {
+        hp_inner = true;
       }
     }
-    if (status != KRR_OK || ok) break;
+    if (!finite) {
+      status = KRR_ENAN;
+      break;
+    }
     if (outer >= a.o.max_outer || remaining <= 0) {
       status = KRR_ENOTCONV;
       break;
     }
     ++outer;
+    rel_prev = 0.0;
+    ColScale sc, inv;
+    for (int c = 0; c < KRR_MAX_RHS; ++c) sc.v[c] = inv.v[c] = 0.0;
+    for (int c = 0; c < k; ++c) {
+      rel_saved[c] = rel[c];
+      rel_prev = std::max(rel_prev, rel[c]);
+      if (rel[c] > a.o.tol) {
+        sc.v[c] = 1.0 / std::sqrt(rr[c]);
+        inv.v[c] = std::sqrt(rr[c]);
+      }
+    }
+    KRR_CUDA(cudaMemcpyAsync(Cp, Cd, nk * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    KRR_CUDA(cudaMemcpyAsync(Rp, Rd, nk * sizeof(double), cudaMemcpyDeviceToDevice, st));
     launch_convert<double, double>(st, Rd, n, k, k, Rs, k, sc);
-    launch_convert<double, float>(st, Rs, n, k, k, r, k, one);
-    KRR_CUDA(cudaMemsetAsync(x, 0, nk * sizeof(float), st));
     LoopOut lo;
-    PcgSpec<float> S;
-    S.n = n; S.k = k; S.Ytol = Rs; S.ldy = k;
-    S.x = x; S.r = r; S.p = p; S.z = z; S.q = q;
-    S.tol = a.o.inner_tol; S.max_iter = remaining; S.matvec = mv; S.apply = ap; S.prec = KRR_BF16;
-    pcg_loop<float>(h, S, a.o.use_graph != 0, &lo, matvecs);
+    if (!hp_inner) {
+      PcgSpec<float> S;
+      S.n = n; S.k = k; S.Ytol = Rs; S.ldy = k;
+      S.x = wsT<float>(h, "v_xf", nk); S.r = wsT<float>(h, "v_rf", nk);
+      S.p = wsT<float>(h, "v_pf", nk); S.z = wsT<float>(h, "v_zf", nk);
+      S.q = wsT<float>(h, "v_qf", nk);
+      S.tol = a.o.inner_tol; S.max_iter = remaining; S.prec = KRR_BF16;
+      S.matvec = [&](cudaStream_t s2, const float* V, float* Q) {
+        matvec_dispatch(h, s2, a.X, n, a.ldx, a.X, n, a.ldx, a.d, a.sigma, a.lambda, V, k, k, Q,
+                        k, KRR_BF16);
+      };
+      if (a.o.precond)
+        S.apply = [&](cudaStream_t s2, const float* R, float* Zo) {
+          apply_precond<float>(h, s2, R, k, k, Zo, k);
+        };
+      launch_convert<double, float>(st, Rs, n, k, k, S.r, k, one);
+      KRR_CUDA(cudaMemsetAsync(S.x, 0, nk * sizeof(float), st));
+      pcg_loop<float>(h, S, a.o.use_graph != 0, &lo, matvecs);
+      if (!(lo.flags & FLAG_NAN)) launch_axpy_d<float>(st, S.x, n, k, k, Cd, k, inv);
+    } else {
+      PcgSpec<double> S;
+      S.n = n; S.k = k; S.Ytol = Rs; S.ldy = k;
+      S.x = wsT<double>(h, "v_x", nk); S.r = wsT<double>(h, "v_r", nk);
+      S.p = wsT<double>(h, "v_p", nk); S.z = wsT<double>(h, "v_z", nk);
+      S.q = wsT<double>(h, "v_q", nk);
+      S.tol = std::min(a.o.inner_tol, std::max(1e-11, 0.5 * a.o.tol / rel_prev));
+      S.max_iter = remaining; S.prec = KRR_HP;
+      S.matvec = [&](cudaStream_t s2, const double* V, double* Q) {
+        matvec_dispatch(h, s2, a.X, n, a.ldx, a.X, n, a.ldx, a.d, a.sigma, a.lambda, V, k, k, Q,
+                        k, KRR_HP);
+      };
+      if (a.o.precond)
+        S.apply = [&](cudaStream_t s2, const double* R, double* Zo) {
+          apply_precond<double>(h, s2, R, k, k, Zo, k);
+        };
+      launch_convert<double, double>(st, Rs, n, k, k, S.r, k, one);
+      KRR_CUDA(cudaMemsetAsync(S.x, 0, nk * sizeof(double), st));
+      pcg_loop<double>(h, S, a.o.use_graph != 0, &lo, matvecs);
+      if (!(lo.flags & FLAG_NAN)) launch_axpy_d<double>(st, S.x, n, k, k, Cd, k, inv);
+    }
     for (int c = 0; c < k; ++c) total_iters[c] += lo.iters[c];
     remaining -= lo.iter;
-    if (lo.flags & FLAG_NAN) {
-      status = KRR_ENAN;
-      break;
-    }
-    // breakdown of the inner solve still leaves a usable correction
-    launch_axpy_d<float>(st, x, n, k, k, Cd, k, inv);
+    // a NaN in the inner solve leaves Cd unchanged; the next pass takes the
+    // correction back and switches to the HP inner solve
     matvec_dispatch(h, st, a.X, n, a.ldx, a.X, n, a.ldx, a.d, a.sigma, a.lambda, Cd, k, k, AX, k,
                     KRR_HP);
     ++*matvecs;
     launch_sub_d(st, Yc, k, AX, k, n, k, Rd, k);
   }
+  if (rep)
+    for (int c = 0; c < k; ++c) rep->rel_res[c] = rel[c];
   launch_convert<double, double>(st, Cd, n, k, k, a.C, a.ldc, one);
   if (rep) {
     for (int c = 0; c < k; ++c) rep->iters[c] = total_iters[c];
@@ -850,7 +905,18 @@ struct BItem {
   double rel[KRR_MAX_RHS] = {0};
   double yy[KRR_MAX_RHS] = {0};
   ColScale inv;
+  // mixed precision: inner solves switch from BF16 to the HP product when a
+  // BF16 correction contracts the residual by less than a half
+  bool hp_inner = false;
+  double rel_prev = 0.0;
+  double rel_saved[KRR_MAX_RHS] = {0};
 };
+
+double max_rel(const BItem& it) {
+  double m = 0.0;
+  for (int c = 0; c < it.k; ++c) m = std::max(m, it.rel[c]);
+  return m;
+}
 
 ColScale ones() {
   ColScale one;
@@ -982,8 +1048,13 @@ void batched_plain(krr_handle* h, std::vector<BItem>& B, const krr_opts& o, int 
   }
 }
 
-// Mixed precision for every item: rounds of lockstep BF16 inner PCG on the
-// scaled residuals, each followed by the HP residual of every item.
+// Mixed precision for every item: rounds of lockstep inner PCG on the scaled
+// residuals, each followed by the HP residual of every item.  The inner
+// product is the BF16 tensor-core product; an item whose BF16 correction
+// contracts its residual by less than a half (the BF16 kernel of the
+// rounded points is too far from K for its lambda) discards a correction
+// that made things worse and continues with inner solves on the HP product
+// in FP64 vectors, run to the accuracy the outer test needs.
 void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
   const ColScale one = ones();
   for (BItem& it : B) {
@@ -994,6 +1065,8 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
     double* Rd = wsT<double>(g, "v_rd", nk);
     wsT<double>(g, "v_ax", nk);
     wsT<double>(g, "v_rs", nk);
+    wsT<double>(g, "v_cprev", nk);
+    wsT<double>(g, "v_rprev", nk);
     launch_convert<double, double>(g->stream, it.Y, it.n, it.k, it.ldy, Yc, it.k, one);
     KRR_CUDA(cudaMemsetAsync(Cd, 0, nk * sizeof(double), g->stream));
     KRR_CUDA(cudaMemcpyAsync(Rd, Yc, nk * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
@@ -1008,11 +1081,40 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
       if (it.done) continue;
       krr_handle* g = it.sub;
       const size_t nk = (size_t)it.n * it.k;
+      double* Cd = wsT<double>(g, "v_cd", nk);
       double* Rd = wsT<double>(g, "v_rd", nk);
       double* Rs = wsT<double>(g, "v_rs", nk);
+      double* Cp = wsT<double>(g, "v_cprev", nk);
+      double* Rp = wsT<double>(g, "v_rprev", nk);
       double rr[KRR_MAX_RHS];
       const bool ok = item_converged(it, Rd, o.tol, rr);
-      if (it.status != KRR_OK || ok) {
+      if (it.status == KRR_OK && ok) {
+        it.done = true;
+        continue;
+      }
+      if (it.outer > 0) {
+        const double now = max_rel(it);
+        if (!(now < it.rel_prev)) {
+          // the last correction did not help: take it back
+          KRR_CUDA(cudaMemcpyAsync(Cd, Cp, nk * sizeof(double), cudaMemcpyDeviceToDevice,
+                                   g->stream));
+          KRR_CUDA(cudaMemcpyAsync(Rd, Rp, nk * sizeof(double), cudaMemcpyDeviceToDevice,
+                                   g->stream));
+          for (int c = 0; c < it.k; ++c) it.rel[c] = it.rel_saved[c];
+          host_colnorm2<double>(g, Rd, it.n, it.k, it.k, rr);
+          it.status = KRR_OK;
+          if (it.hp_inner) {
+            // HP inner solves no longer help: the HP residual's accuracy floor
+            it.status = KRR_ENOTCONV;
+            it.done = true;
+            continue;
+          }
+          it.hp_inner = true;
+        } else if (now > 0.5 * it.rel_prev) {
+          it.hp_inner = true;
+        }
+      }
+      if (it.status != KRR_OK) {
         it.done = true;
         continue;
       }
@@ -1022,6 +1124,10 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
         continue;
       }
       ++it.outer;
+      it.rel_prev = max_rel(it);
+      for (int c = 0; c < it.k; ++c) it.rel_saved[c] = it.rel[c];
+      KRR_CUDA(cudaMemcpyAsync(Cp, Cd, nk * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+      KRR_CUDA(cudaMemcpyAsync(Rp, Rd, nk * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
       ColScale sc;
       for (int c = 0; c < KRR_MAX_RHS; ++c) sc.v[c] = it.inv.v[c] = 0.0;
       for (int c = 0; c < it.k; ++c)
@@ -1029,12 +1135,23 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
           sc.v[c] = 1.0 / std::sqrt(rr[c]);
           it.inv.v[c] = std::sqrt(rr[c]);
         }
-      PcgSpec<float> S = item_spec<float>(it, Rs, o.inner_tol, KRR_BF16, o.precond != 0);
       launch_convert<double, double>(g->stream, Rd, it.n, it.k, it.k, Rs, it.k, sc);
-      launch_convert<double, float>(g->stream, Rs, it.n, it.k, it.k, S.r, it.k, one);
-      KRR_CUDA(cudaMemsetAsync(S.x, 0, nk * sizeof(float), g->stream));
-      pcg_begin<float>(g, S);
-      E.push_back(BatchEntry{g, [g, S](cudaStream_t cs) { pcg_body<float>(g, S, cs, 0ull); }, 0});
+      if (!it.hp_inner) {
+        PcgSpec<float> S = item_spec<float>(it, Rs, o.inner_tol, KRR_BF16, o.precond != 0);
+        launch_convert<double, float>(g->stream, Rs, it.n, it.k, it.k, S.r, it.k, one);
+        KRR_CUDA(cudaMemsetAsync(S.x, 0, nk * sizeof(float), g->stream));
+        pcg_begin<float>(g, S);
+        E.push_back(BatchEntry{g, [g, S](cudaStream_t cs) { pcg_body<float>(g, S, cs, 0ull); }, 0});
+      } else {
+        // one inner solve to the accuracy the outer test needs
+        const double tin = std::min(o.inner_tol, std::max(1e-11, 0.5 * o.tol / it.rel_prev));
+        PcgSpec<double> S = item_spec<double>(it, Rs, tin, KRR_HP, o.precond != 0);
+        launch_convert<double, double>(g->stream, Rs, it.n, it.k, it.k, S.r, it.k, one);
+        KRR_CUDA(cudaMemsetAsync(S.x, 0, nk * sizeof(double), g->stream));
+        pcg_begin<double>(g, S);
+        E.push_back(
+            BatchEntry{g, [g, S](cudaStream_t cs) { pcg_body<double>(g, S, cs, 0ull); }, 0});
+      }
       act.push_back((int)i);
     }
     if (E.empty()) break;
@@ -1047,18 +1164,21 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
       for (int c = 0; c < it.k; ++c) it.iters[c] += lo.iters[c];
       it.remaining -= lo.iter;
       it.matvecs += lo.iter;
-      if (lo.flags & FLAG_NAN) {
-        it.status = KRR_ENAN;
-        it.done = true;
-        continue;
-      }
       const size_t nk = (size_t)it.n * it.k;
       double* Yc = wsT<double>(g, "v_y", nk);
       double* Cd = wsT<double>(g, "v_cd", nk);
       double* Rd = wsT<double>(g, "v_rd", nk);
       double* AX = wsT<double>(g, "v_ax", nk);
-      const float* xf = wsT<float>(g, "v_xf", nk);
-      launch_axpy_d<float>(g->stream, xf, it.n, it.k, it.k, Cd, it.k, it.inv);
+      // a NaN in the inner solve leaves Cd unchanged; the next round takes
+      // the correction back and switches to the HP inner solve
+      if (lo.flags & FLAG_NAN) {
+      } else if (it.hp_inner) {
+        launch_axpy_d<double>(g->stream, wsT<double>(g, "v_x", nk), it.n, it.k, it.k, Cd, it.k,
+                              it.inv);
+      } else {
+        launch_axpy_d<float>(g->stream, wsT<float>(g, "v_xf", nk), it.n, it.k, it.k, Cd, it.k,
+                             it.inv);
+      }
       matvec_dispatch(g, g->stream, it.X, it.n, it.ldx, it.X, it.n, it.ldx, it.d, it.sigma,
                       it.lambda, Cd, it.k, it.k, AX, it.k, KRR_HP);
       ++it.matvecs;

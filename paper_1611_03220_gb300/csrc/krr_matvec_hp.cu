@@ -8,29 +8,33 @@
 // float-float arithmetic on the FP32 pipes.
 //
 // 1. Fixed-point slices.  With u_i = sqrt(log2 e)/sigma (x_i - mu) (FP64) and
-//    E_i the exponent of max_t |u_it|, every coordinate is cut into four
+//    E_i the exponent of max_t |u_it|, every coordinate is cut into five
 //    signed base-512 digits relative to 2^E_i:
-//      u_it ~= 2^(E_i - 8) (q0 + q1 2^-9 + q2 2^-18 + q3 2^-27),  |q| <= 256,
-//    each digit exact in BF16 (every integer in [-256, 256] is).  The kernel
-//    computes the kernel of these truncated points (error below 2^(E_i - 36)
-//    per coordinate).
-// 2. Exact dot products.  For a pair of row/column tiles the tensor core
-//    accumulates, per level m = a + b <= 3, L_m = sum_{a+b=m} sum_t q_ia q_jb
-//    in FP32 in TMEM.  Every term and partial sum is an integer of magnitude
-//    at most (m + 1) 64 2^16 <= 2^24 (d <= 64), so the sums are exact.
-//    10 slice-pair GEMMs per tile.
+//      u_it ~= 2^(E_i - 8) (q0 + q1 2^-9 + q2 2^-18 + q3 2^-27 + q4 2^-36),
+//    |q| <= 256, each digit exact in BF16 (every integer in [-256, 256] is).
+//    The kernel computes the kernel of these truncated points (error below
+//    2^(E_i - 45) per coordinate).
+// 2. Dot products from exact integer sums.  For a pair of row/column tiles
+//    the tensor core accumulates, per level m = a + b, the sums
+//    L_m = sum_{a+b=m} sum_t q_ia q_jb in FP32 in TMEM.  For m <= 3 every
+//    term and partial sum is an integer of magnitude at most
+//    (m + 1) 64 2^16 <= 2^24 (d <= 64), so L_0..L_3 are exact.  Level 4
+//    shares the level-3 accumulator: its five pair products are summed
+//    first, and the first level-3 product scales that input by 2^-9 (the
+//    MMA's input-D scale), leaving L_3 + 2^-9 L_4 with a rounding error of
+//    2^-24 of a term already weighted 2^-27.  15 slice-pair GEMMs per tile.
 // 3. Float-float epilogue.  u_i.u_j = 2^(E_i+E_j-16) sum_m 2^-9m L_m, then
 //    arg = u_i.u_j - n_i/2 - n_j/2 (n_i = ||u_i||^2 split into two floats),
-//    2^arg by a table-driven reduction (64-entry table of 2^(j/64), after
+//    2^arg by a table-driven reduction (256-entry table of 2^(j/256), after
 //    P. T. P. Tang's table method, 1989) and a degree-4 Taylor polynomial on
-//    |r ln 2| <= ln 2 / 128, and the row sums K_ij v_j accumulated as
-//    float-float pairs.
+//    |r ln 2| <= ln 2 / 512, and the row sums K_ij v_j accumulated as
+//    float-float pairs.  Each K_ij carries about 1e-13 relative error.
 //
 // Pipeline (one persistent CTA per SM, 320 threads): warp 0 loads by TMA the
-// row tile's four slices once per work item and streams the column tiles'
+// row tile's five slices once per work item and streams the column tiles'
 // slices through a ring of stages; warp 1 issues the MMAs into one of two
-// TMEM buffers (4 levels x 64 columns each, 512 columns in all); warps 2-9
-// run the epilogue.  Every mbarrier wait is bounded.
+// TMEM buffers (4 accumulators x 64 columns each, 512 columns in all); warps
+// 2-9 run the epilogue.  Every mbarrier wait is bounded.
 #include <cuda.h>
 
 #include <cmath>
@@ -49,9 +53,9 @@ using namespace ptx;
 constexpr int BM = 128;
 constexpr int BN = 64;
 constexpr int KP = 64;                 // padded coordinates (d <= 64)
-constexpr int NSL = 4;                 // slices
-constexpr int NLEV = 4;                // levels kept (a + b <= 3)
-constexpr int NS = 3;                  // column-tile stages
+constexpr int NSL = 5;                 // slices
+constexpr int NLEV = 4;                // accumulators: L0, L1, L2, L3 + 2^-9 L4
+constexpr int NTAB = 256;              // exp2 table entries
 constexpr int NUM_EPI = 8;
 constexpr int THREADS = 32 * (2 + NUM_EPI);
 constexpr int TMEM_COLS = 512;         // 2 buffers x 4 levels x 64 columns
@@ -67,8 +71,14 @@ struct HpParams {
   const float* cold;    // n_pad x CW: (b_hi, b_lo, 2^(E-8), 0, vh[KV], vl[KV])
   float* part;          // nchunk x n_pad x 2KV float-float partial row sums
   int* err;
-  float tab[128];       // 2^(j/64) as (hi, lo) pairs
+  float tab[2 * NTAB];  // 2^(j/256) as (hi, lo) pairs
 };
+
+// Column-tile stages: three, or two when the column records are long.
+template <int KV>
+constexpr int ns_of() {
+  return KV >= 16 ? 2 : 3;
+}
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
@@ -80,14 +90,15 @@ template <int KV, int CW>
 __global__ void __launch_bounds__(THREADS, 1)
 hp_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  HpParams p) {
+  constexpr int NS = ns_of<KV>();
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;                                   // A_BYTES
   uint8_t* sB = sA + A_BYTES;                           // NS x B_BYTES
   float* cbuf = (float*)(sB + NS * B_BYTES);            // 2 x BN x CW
   float* comb = cbuf + 2 * BN * CW;                     // BM x 2KV
-  float* tab = comb + BM * 2 * KV;                      // 128
-  uint64_t* bars = (uint64_t*)(tab + 128);
+  float* tab = comb + BM * 2 * KV;                      // 2 NTAB
+  uint64_t* bars = (uint64_t*)(tab + 2 * NTAB);
   uint64_t* full = bars;
   uint64_t* empty = full + NS;
   uint64_t* tfull = empty + NS;
@@ -103,7 +114,7 @@ hp_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int items = p.n_rt * p.nchunk;
 
-  for (int e = threadIdx.x; e < 128; e += THREADS) tab[e] = p.tab[e];
+  for (int e = threadIdx.x; e < 2 * NTAB; e += THREADS) tab[e] = p.tab[e];
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
@@ -197,7 +208,7 @@ hp_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
           fence_after();
           const uint32_t sb = smem_u32(sB + st * B_BYTES);
 #pragma unroll
-          for (int m = 0; m < NLEV; ++m) {
+          for (int m = 0; m < 3; ++m) {
             const uint32_t d = tmem + (acc * NLEV + m) * BN;
 #pragma unroll
             for (int a = 0; a <= m; ++a) {
@@ -206,6 +217,31 @@ hp_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
               for (int kk = 0; kk < KP / 16; ++kk) {
                 mma_bf16(d, sdesc(sa + a * A_SLICE + kk * 32), sdesc(sb + b * B_SLICE + kk * 32),
                          IDESC, (a > 0 || kk > 0) ? 1u : 0u);
+              }
+            }
+          }
+          {
+            // level 4 first, then level 3 on top of 2^-9 times it
+            const uint32_t d = tmem + (acc * NLEV + 3) * BN;
+#pragma unroll
+            for (int a = 0; a <= 4; ++a) {
+#pragma unroll
+              for (int kk = 0; kk < KP / 16; ++kk) {
+                mma_bf16(d, sdesc(sa + a * A_SLICE + kk * 32),
+                         sdesc(sb + (4 - a) * B_SLICE + kk * 32), IDESC,
+                         (a > 0 || kk > 0) ? 1u : 0u);
+              }
+            }
+#pragma unroll
+            for (int a = 0; a <= 3; ++a) {
+#pragma unroll
+              for (int kk = 0; kk < KP / 16; ++kk) {
+                const uint64_t da = sdesc(sa + a * A_SLICE + kk * 32);
+                const uint64_t db = sdesc(sb + (3 - a) * B_SLICE + kk * 32);
+                if (a == 0 && kk == 0)
+                  mma_bf16_scale9(d, da, db, IDESC);
+                else
+                  mma_bf16(d, da, db, IDESC, 1u);
               }
             }
           }
@@ -268,9 +304,11 @@ hp_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             // scaled dot product from the exact level sums
             const float l0 = __uint_as_float(L[0][j]);
             const float t1 = __uint_as_float(L[1][j]) * 0x1p-9f;
-            float sh, sl;
+            const float t2 = __uint_as_float(L[2][j]) * 0x1p-18f;
+            float sh, sl, e2;
             two_sum(l0, t1, sh, sl);
-            sl = fmaf(__uint_as_float(L[2][j]), 0x1p-18f, sl);
+            two_sum(sh, t2, sh, e2);
+            sl += e2;
             sl = fmaf(__uint_as_float(L[3][j]), 0x1p-27f, sl);
             const float sc = sci * cd.z;
             const float dh = sh * sc, dl = sl * sc;
@@ -285,25 +323,29 @@ hp_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
               xh = -125.f;
               xl = 0.f;
             }
-            // 2^x = 2^(k/64) * e^(r ln 2), k = rint(64 x)
-            const float kf = rintf(xh * 64.f);
-            const float rh = fmaf(kf, -0.015625f, xh);
+            // 2^x = 2^(k/256) * e^(r ln 2), k = rint(256 x), r = (xh - k/256) + xl
+            // kept as an exact float pair so that y = r ln 2 has a tiny low part
+            const float kf = rintf(xh * 256.f);
+            float rh, rl;
+            two_sum(fmaf(kf, -0.00390625f, xh), xl, rh, rl);
             const float yh = rh * 0.693147182464599609375f;
             float yl = fmaf(rh, 0.693147182464599609375f, -yh);
             yl = fmaf(rh, -1.904654299957768e-09f, yl);  // ln 2 - float(ln 2)
-            yl = fmaf(xl, 0.693147182464599609375f, yl);
+            yl = fmaf(rl, 0.693147182464599609375f, yl);
+            // e^yh = 1 + yh + pp (degree-4 Taylor), then times (1 + yl)
             float pp = fmaf(yh, 0.041666666666666667f, 0.16666666666666667f);
             pp = fmaf(yh, pp, 0.5f);
             pp = pp * yh * yh;
             const float eh = 1.f + yh;
-            const float el = ((1.f - eh) + yh) + (yl + pp);
+            const float e0 = ((1.f - eh) + yh) + pp;
+            const float el = fmaf(yl, eh + e0, e0);
             const int k = (int)kf;
-            const float2 tv = *reinterpret_cast<const float2*>(tab + 2 * (k & 63));
+            const float2 tv = *reinterpret_cast<const float2*>(tab + 2 * (k & (NTAB - 1)));
             const float kh0 = eh * tv.x;
             float kl0 = fmaf(eh, tv.x, -kh0);
             kl0 = fmaf(eh, tv.y, kl0);
             kl0 = fmaf(el, tv.x, kl0);
-            const float s2 = __int_as_float((127 + (k >> 6)) << 23);
+            const float s2 = __int_as_float((127 + (k >> 8)) << 23);
             const float kh = kh0 * s2, kl = kl0 * s2;
             // q += K_ij v_j in float-float
 #pragma unroll
@@ -356,7 +398,7 @@ hp_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 }
 
 // ------------------------------------------------------------ helpers ----
-// Per row: u = scale (x - mu) in FP64, E = exponent of max |u|, four base-512
+// Per row: u = scale (x - mu) in FP64, E = exponent of max |u|, five base-512
 // digits per coordinate (exact in BF16), a = -||u~||^2 / 2 as two floats.
 __global__ void hp_prep_kernel(const float* __restrict__ X, int n, int ld, int d,
                                const double* __restrict__ mu, double scale, int n_pad,
@@ -385,7 +427,8 @@ __global__ void hp_prep_kernel(const float* __restrict__ X, int n, int ld, int d
       q[a] = rint(w);                // |q| <= 256
       w = (w - q[a]) * 512.0;        // |w| <= 256
     }
-    const double ut = ldexp(q[0] + q[1] * 0x1p-9 + q[2] * 0x1p-18 + q[3] * 0x1p-27, E - 8);
+    const double ut =
+        ldexp(q[0] + q[1] * 0x1p-9 + q[2] * 0x1p-18 + q[3] * 0x1p-27 + q[4] * 0x1p-36, E - 8);
     nrm += ut * ut;
 #pragma unroll
     for (int a = 0; a < NSL; ++a)
@@ -511,8 +554,8 @@ constexpr int cw_of() {
 
 template <int KV>
 size_t smem_bytes() {
-  return 1024 + (size_t)A_BYTES + (size_t)NS * B_BYTES + (size_t)2 * BN * cw_of<KV>() * 4 +
-         (size_t)BM * 2 * KV * 4 + 128 * 4 + 256;
+  return 1024 + (size_t)A_BYTES + (size_t)ns_of<KV>() * B_BYTES +
+         (size_t)2 * BN * cw_of<KV>() * 4 + (size_t)BM * 2 * KV * 4 + 2 * NTAB * 4 + 256;
 }
 
 template <int KV>
@@ -614,8 +657,8 @@ void hp_matvec(HpState& t, cudaStream_t st, const float* X, int n, int ldx, int 
   p.cold = (const float*)t.cold.p;
   p.part = (float*)t.part.p;
   p.err = (int*)t.err.p;
-  for (int j = 0; j < 64; ++j) {
-    const double v = std::exp2((double)j / 64.0);
+  for (int j = 0; j < NTAB; ++j) {
+    const double v = std::exp2((double)j / NTAB);
     const float hi = (float)v;
     p.tab[2 * j] = hi;
     p.tab[2 * j + 1] = (float)(v - (double)hi);

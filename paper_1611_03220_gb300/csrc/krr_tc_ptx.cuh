@@ -105,6 +105,17 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b,
       : "memory");
 }
 
+// D = A B + 2^-9 D (the input-D scale of tcgen05.mma, kind::f16).
+__device__ __forceinline__ void mma_bf16_scale9(uint32_t dtmem, uint64_t a, uint64_t b,
+                                                uint32_t idesc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, 1, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p, 9;\n\t}\n" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(idesc)
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
