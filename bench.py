@@ -41,6 +41,9 @@ WORKLOAD = ("gaussian-mixture n=65536 d=64 (10 centres N(0,4I), unit spread), si
             "lambda=1e-4, s=2048 RFF, tol 1e-6, predict m=8192")
 M_TEST = 8192
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) of one tc_matvec_kernel<1> launch at n = 65536, d = 64, from the
+# ncu capture summarised in profiles/tc_matvec_kernel_n65536_d64.md
+TC_DRAM_BYTES_N65536 = 8678656
 
 
 def parse():
@@ -305,8 +308,12 @@ def run_ours(args, rank, world, local):
         lanes = 2 ** round(math.log2(ex2_rate / (sms * clk_mhz * 1e6)))
     peak = (lanes or 16) * sms * 2070e6
     achieved = pairs / t_mv
+    # algorithmic bytes of one product: the BF16 points once, w, and the row sums
+    alg_bytes = n_pad * d_pad * 2 + n * 4 + n * 4
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
-                "unit": "Gexp/s", "frac": achieved / peak, "traffic": None,
+                "unit": "Gexp/s", "frac": achieved / peak,
+                "traffic": TC_DRAM_BYTES_N65536 if n == 65536 and P.d == 64 else None,
+                "traffic_unit": "DRAM bytes per launch (ncu)", "alg_bytes": alg_bytes,
                 "kernel": "tc_matvec_kernel (+ w/reduce helpers)",
                 "peak_basis": (f"{lanes or 16} MUFU ex2 lanes/SM/clk x {sms} SMs x 2070 MHz "
                                f"(lanes from the ex2 probe: {ex2_rate and ex2_rate / 1e9:.0f} "
