@@ -293,38 +293,38 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         if (!(ok = mbar_wait(smem_u32(&wfull[ws]), wph, abort_flag, p.err))) break;
         fence_after();
         const float* wb = wbuf + ws * BN * KV;
-        // The accumulator slice is read in rounds of up to two 32-column chunks;
-        // the TMEM buffer goes back to the MMA warp right after the last round
-        // is loaded (with one round, before any math).
+        // The accumulator slice is read in 32-column chunks, the next chunk's
+        // TMEM load in flight while the current chunk's exponentials run; the
+        // TMEM buffer goes back to the MMA warp as soon as the last chunk has
+        // landed in registers.
         constexpr int NCH = COLS / 32;
-        constexpr int RB = NCH < 2 ? NCH : 2;
         constexpr int PER = EMU > 0 ? 32 / EMU : 33;
-#pragma unroll 1
-        for (int r0 = 0; r0 < NCH; r0 += RB) {
-        uint32_t raw[RB][32];
-#pragma unroll
-        for (int b = 0; b < RB; ++b) {
-          const uint32_t ta =
-              tmem + ((uint32_t)(quad * 32) << 16) + acc * BN + grp * COLS + (r0 + b) * 32;
-          tmem_ld16_nowait(ta, *reinterpret_cast<uint32_t(*)[16]>(&raw[b][0]));
-          tmem_ld16_nowait(ta + 16, *reinterpret_cast<uint32_t(*)[16]>(&raw[b][16]));
-        }
+        const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + acc * BN + grp * COLS;
+        uint32_t raw[2][32];
+        tmem_ld16_nowait(tbase, *reinterpret_cast<uint32_t(*)[16]>(&raw[0][0]));
+        tmem_ld16_nowait(tbase + 16, *reinterpret_cast<uint32_t(*)[16]>(&raw[0][16]));
         tmem_wait_ld();
-        if (r0 + RB >= NCH) {
+        if (NCH == 1) {
           fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(smem_u32(&tempty[acc]));
         }
 #pragma unroll
-        for (int b = 0; b < RB; ++b) {
+        for (int cc = 0; cc < NCH; ++cc) {
+          const int cur = cc & 1;
+          if (cc + 1 < NCH) {
+            tmem_ld16_nowait(tbase + (cc + 1) * 32,
+                             *reinterpret_cast<uint32_t(*)[16]>(&raw[cur ^ 1][0]));
+            tmem_ld16_nowait(tbase + (cc + 1) * 32 + 16,
+                             *reinterpret_cast<uint32_t(*)[16]>(&raw[cur ^ 1][16]));
+          }
           // all exponentials of the chunk first (independent), then the contraction
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const float s = __uint_as_float(raw[b][j]);
-            raw[b][j] = __float_as_uint((j % PER == PER - 1) ? ex2_fma(s) : ex2_mufu(s));
+            const float s = __uint_as_float(raw[cur][j]);
+            raw[cur][j] = __float_as_uint((j % PER == PER - 1) ? ex2_fma(s) : ex2_mufu(s));
           }
-          const float4* w4 =
-              reinterpret_cast<const float4*>(wb + (grp * COLS + (r0 + b) * 32) * KV);
+          const float4* w4 = reinterpret_cast<const float4*>(wb + (grp * COLS + cc * 32) * KV);
 #pragma unroll
           for (int j4 = 0; j4 < 32 * KV / 4; ++j4) {
             const float4 wv = w4[j4];
@@ -333,10 +333,17 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             for (int u = 0; u < 4; ++u) {
               const int idx = j4 * 4 + u;  // = j * KV + c
               const int j = idx / KV, c = idx % KV;
-              q[j % CH][c] = fmaf(__uint_as_float(raw[b][j]), wq[u], q[j % CH][c]);
+              q[j % CH][c] = fmaf(__uint_as_float(raw[cur][j]), wq[u], q[j % CH][c]);
             }
           }
-        }
+          if (cc + 1 < NCH) {
+            tmem_wait_ld();
+            if (cc + 2 == NCH) {
+              fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(smem_u32(&tempty[acc]));
+            }
+          }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&wempty[ws]));
