@@ -26,6 +26,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -60,6 +61,8 @@ def parse():
                          "--profile-iters PCG iterations with the host-driven loop (every "
                          "launch listed); otherwise 3 launches of that kernel product / apply")
     ap.add_argument("--profile-iters", type=int, default=12)
+    ap.add_argument("--profile-k", type=int, default=1,
+                    help="right-hand sides of the --profile bf16/hp/fp32 products")
     return ap.parse_args()
 
 
@@ -77,7 +80,9 @@ class ClockSampler:
     def __init__(self, gpu: int):
         self.gpu = gpu
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu}.csv")
+        # the raw samples go to KRR_CLOCKS_DIR (default: the system temp directory)
+        out = os.environ.get("KRR_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"clocks_gpu{gpu}.csv")
 
     def start(self):
         try:
@@ -203,7 +208,7 @@ def run_profile(args):
             K.krr_precond_apply(h, R, Zo)
     else:
         dt = torch.float64 if args.profile == "hp" else torch.float32
-        V = torch.randn((n, 1), dtype=dt, device="cuda")
+        V = torch.randn((n, args.profile_k), dtype=dt, device="cuda")
         Q = torch.empty_like(V)
         for _ in range(3):
             K.krr_kernel_matvec(h, X, X, P.sigma, P.lam, V, Q, args.profile)

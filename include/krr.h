@@ -54,7 +54,9 @@ typedef enum {
   KRR_FP32 = 1,        /* FP32 SIMT: the plain single-precision path        */
   KRR_BF16 = 2,        /* tcgen05 BF16 tensor cores, FP32 accumulation      */
   KRR_HP = 3,          /* extended precision for refinement residuals       */
-  KRR_MIXED = 4        /* solver only: BF16 inner PCG + HP refinement       */
+  KRR_MIXED = 4,       /* solver only: BF16 inner PCG + HP refinement       */
+  KRR_BF16X3 = 5       /* tcgen05 BF16 on split points (hi + lo, d <= 64):  */
+                       /* hi.hi + lo.hi + hi.lo, about 2^-16 relative dots  */
 } krr_precision;
 
 /* How the preconditioner is applied (Section 3.1). */
@@ -122,8 +124,8 @@ krr_status krr_rff_features(krr_handle* h, const float* X, int n, int d, int ldx
  * (Section 3.1, "multiplying the kernel matrix by a vector"):
  *   Q[i, :] = sum_j k(xr_i, xc_j) V[j, :] + shift * V[i, :]
  * Xr: nr x d (ldxr), Xc: nc x d (ldxc), FP32.  V: nc x k (ldv), Q: nr x k
- * (ldq).  V and Q are double for KRR_FP64 and KRR_HP and float for KRR_FP32
- * and KRR_BF16.  `shift` (lambda of Eq. (1)) needs nr == nc and is added
+ * (ldq).  V and Q are double for KRR_FP64 and KRR_HP and float for KRR_FP32,
+ * KRR_BF16 and KRR_BF16X3.  `shift` (lambda of Eq. (1)) needs nr == nc and is added
  * only when it is nonzero; pass Xr == Xc for the training system.
  * 1 <= k <= KRR_MAX_RHS.
  */
@@ -134,7 +136,7 @@ krr_status krr_kernel_matvec(krr_handle* h, const float* Xr, int nr, int ldxr,
                              int precision);
 
 /*
- * Preconditioner set-up, Algorithm 1 lines 6-7 and Section 3.1:
+ * Preconditioner set-up of Algorithm 1 and Section 3.1:
  *   G = Z^T Z + lambda_p I_s (FP64 accumulation), L L^T = G (FP64
  *   Cholesky, lower L), then either U = L^-1 Z^T (KRR_APPLY_U, stored FP32
  *   s x n) or L^-1 kept for triangular solves (KRR_APPLY_ZL).
@@ -148,7 +150,7 @@ krr_status krr_precond_setup(krr_handle* h, const float* Z, int n, int s, int ld
 
 /*
  * Apply the preconditioner inverse of the last krr_precond_setup
- * (Algorithm 1 line 9):  Zout = (Z Z^T + lambda_p I)^-1 R.
+ * (the PCG step of Algorithm 1):  Zout = (Z Z^T + lambda_p I)^-1 R.
  * R, Zout: n x k double (ldr, ldo).  1 <= k <= KRR_MAX_RHS.
  */
 krr_status krr_precond_apply(krr_handle* h, const double* R, int k, int ldr,
@@ -162,7 +164,9 @@ krr_status krr_precond_apply(krr_handle* h, const double* R, int k, int ldr,
  * Y, C: n x k double (ldy, ldc).  X, W, b, Y and C may be host or device
  * pointers.  With opts->precision == KRR_MIXED the inner PCG runs the BF16
  * tensor-core product and an outer refinement loop recomputes the residual
- * in KRR_HP arithmetic and FP64 vectors.  `rep` (may be NULL) receives the
+ * in KRR_HP arithmetic and FP64 vectors; when a correction contracts the
+ * residual by less than a half, later inner solves use KRR_BF16X3 (d <= 64)
+ * and then KRR_HP products.  `rep` (may be NULL) receives the
  * per-column report.  Returns KRR_ENOTCONV if max_iter is reached (C holds
  * the last iterate), KRR_EBREAKDOWN / KRR_ENAN on breakdown.
  */

@@ -16,10 +16,10 @@ Sketching and Preconditioning"):
 * ``rff_features``            -- random Fourier features, Section 2.2, with the
                                  sqrt(2/s) scale (reading: the printed s^-1/2
                                  misses the factor 2 of E[cos cos] = k / 2).
-* ``precond_setup/apply``     -- Algorithm 1 lines 4-7 and the Woodbury form of
+* ``precond_setup/apply``     -- the set-up of Algorithm 1 and the Woodbury form of
                                  Section 3.1: L L^T = Z^T Z + lambda_p I,
                                  U = L^-1 Z^T, M^-1 v = (v - U^T U v)/lambda_p.
-* ``pcg``                     -- PCG from x0 = 0 (Algorithm 1 line 9; the
+* ``pcg``                     -- PCG from x0 = 0 (Algorithm 1; the
                                  Hestenes-Stiefel recurrences), stopping on the
                                  true relative residual (Section 5).
 * ``krr_pcg_solve``           -- Algorithm 1 end to end.
@@ -146,7 +146,7 @@ def rff_features(X: np.ndarray, W: np.ndarray, b: np.ndarray) -> np.ndarray:
 # ------------------------------------------------------ preconditioner ----
 
 def gram(Z: np.ndarray, lam_p: float) -> np.ndarray:
-    """G = Z^T Z + lambda_p I_s (Algorithm 1 line 6)."""
+    """G = Z^T Z + lambda_p I_s (the Gram step of Algorithm 1)."""
     Z = np.asarray(Z, np.float64)
     G = Z.T @ Z
     G[np.diag_indices_from(G)] += lam_p
@@ -154,7 +154,7 @@ def gram(Z: np.ndarray, lam_p: float) -> np.ndarray:
 
 
 def precond_setup(Z: np.ndarray, lam_p: float) -> dict:
-    """Cholesky L L^T = G and U = L^-1 Z^T (Section 3.1; Algorithm 1 lines 6-7).
+    """Cholesky L L^T = G and U = L^-1 Z^T (Section 3.1; the set-up of Algorithm 1).
 
     Reading: the printed text pairs L L^T with U = L^-T Z^T and the algorithm
     pairs L^T L with L^T U = Z^T; both give U^T U = Z G^-1 Z^T only as
@@ -167,7 +167,7 @@ def precond_setup(Z: np.ndarray, lam_p: float) -> dict:
 
 
 def precond_apply(P: dict, R: np.ndarray) -> np.ndarray:
-    """M^-1 R = lambda_p^-1 (R - U^T (U R)) (Algorithm 1 line 9, Section 3.1 Woodbury form)."""
+    """M^-1 R = lambda_p^-1 (R - U^T (U R)) (Algorithm 1, Section 3.1 Woodbury form)."""
     U = P["U"]
     R = np.asarray(R, np.float64)
     return (R - U.T @ (U @ R)) / P["lam_p"]
@@ -261,7 +261,7 @@ def krr_pcg_solve(X, Y, sigma: float, lam: float, W, b, lam_p: float | None = No
                   explicit_max: int = 8192) -> dict:
     """Algorithm 1: RFF features, Woodbury preconditioner, PCG on (K + lambda I) c = y.
 
-    K is formed explicitly (Algorithm 1 line 3) for n <= ``explicit_max``;
+    K is formed explicitly (as Algorithm 1 does) for n <= ``explicit_max``;
     above that its row blocks are recomputed at every product.
     ``precond=False`` runs plain CG (M = I), the comparator of Table 4.
     """

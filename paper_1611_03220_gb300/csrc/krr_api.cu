@@ -3,7 +3,7 @@
 // Algorithm 1 of the paper, end to end on one GPU:
 //   features Z (Section 2.2) -> G = Z^T Z + lambda_p I -> L L^T = G ->
 //   factors for the Woodbury apply (Section 3.1) -> PCG on (K + lambda I) c = y
-//   with K applied on the fly (Algorithm 1 line 9), stopping on the relative
+//   with K applied on the fly (the PCG step of Algorithm 1), stopping on the relative
 //   residual of every column (Section 5).
 // The PCG iteration is captured once per solve into a CUDA graph whose body
 // sits under a conditional WHILE node; the loop's last kernel decides on the
@@ -193,9 +193,10 @@ void matvec_dispatch(krr_handle* h, cudaStream_t st, const float* Xr, int nr, in
                      (float*)Q, ldq, nr_, nc_, part);
       return;
     }
-    case KRR_BF16: {
+    case KRR_BF16:
+    case KRR_BF16X3: {
       tc_matvec(h->tc, st, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, shift, (const float*)V, k, ldv,
-                (float*)Q, ldq);
+                (float*)Q, ldq, prec == KRR_BF16X3 ? 1 : 0);
       return;
     }
     default:
@@ -220,6 +221,7 @@ void matvec_reserve(krr_handle* h, int n, int k, int prec) {
       wsT<float>(h, "mv_nrm_c", (size_t)n);
       return;
     case KRR_BF16:
+    case KRR_BF16X3:
       tc_reserve(h->tc, h->stream, k);
       return;
     default:
@@ -264,7 +266,7 @@ void pcg_begin(krr_handle* h, const PcgSpec<T>& S) {
   launch_cg_rz_first<T>(st, h->sc, S.r, S.z, S.p, S.n, S.k, part);
 }
 
-// One iteration (Algorithm 1 line 9): q = A p, alpha, x and r updates,
+// One PCG iteration of Algorithm 1: q = A p, alpha, x and r updates,
 // z = M^-1 r, beta and p; the tail kernel decides whether to continue.
 // Enqueues only (no allocation), so it can be captured into a graph.
 template <typename T>
@@ -539,6 +541,71 @@ krr_status solve_plain(krr_handle* h, const SolveArgs& a, int prec, krr_report* 
   return status;
 }
 
+// Inner-solve arithmetic of the mixed solve, in the order it is tried: the
+// BF16 product, the split-point BF16 product (d <= 64), the HP product.
+enum InnerLevel { INNER_BF16 = 0, INNER_SPLIT = 1, INNER_HP = 2 };
+
+int next_level(int level, int d) {
+  if (level == INNER_BF16 && d <= 64) return INNER_SPLIT;
+  return INNER_HP;
+}
+
+// Relative tolerance of an inner solve: the BF16 solve stops at inner_tol;
+// the more accurate ones go as far as the outer test needs (0.5 tol / rel)
+// within what their arithmetic can reach.
+double inner_tol_for(int level, const krr_opts& o, double rel) {
+  if (level == INNER_BF16) return o.inner_tol;
+  const double want = 0.5 * o.tol / rel;
+  return std::min(o.inner_tol, std::max(level == INNER_SPLIT ? 1e-5 : 1e-11, want));
+}
+
+const char* level_name(int level) {
+  return level == INNER_BF16 ? "BF16" : (level == INNER_SPLIT ? "BF16x3" : "HP");
+}
+
+// Operators of an FP64-vector inner solve at the split or HP level: the
+// product in KRR_BF16X3 (through FP32 copies of the vectors) or KRR_HP; the
+// preconditioner in FP32 arithmetic through FP32 copies (any fixed SPD
+// approximation serves as a preconditioner).  Scratch is looked up by name,
+// so the first (uncaptured) call allocates it.
+void double_inner_ops(krr_handle* h, const float* X, int n, int ldx, int d, double sigma,
+                      double lambda, int k, int level, bool precond,
+                      std::function<void(cudaStream_t, const double*, double*)>& matvec,
+                      std::function<void(cudaStream_t, const double*, double*)>& apply) {
+  const size_t nk = (size_t)n * k;
+  ColScale one;
+  for (int c = 0; c < KRR_MAX_RHS; ++c) one.v[c] = 1.0;
+  // allocated here: the loop body may be captured into a graph
+  wsT<float>(h, "v_cvin", nk);
+  wsT<float>(h, "v_cvout", nk);
+  wsT<float>(h, "v_cvr", nk);
+  wsT<float>(h, "v_cvz", nk);
+  if (level == INNER_SPLIT) {
+    matvec = [h, X, n, ldx, d, sigma, lambda, k, nk, one](cudaStream_t s2, const double* V,
+                                                          double* Q) {
+      float* vf = wsT<float>(h, "v_cvin", nk);
+      float* qf = wsT<float>(h, "v_cvout", nk);
+      launch_convert<double, float>(s2, V, n, k, k, vf, k, one);
+      matvec_dispatch(h, s2, X, n, ldx, X, n, ldx, d, sigma, lambda, vf, k, k, qf, k,
+                      KRR_BF16X3);
+      launch_convert<float, double>(s2, qf, n, k, k, Q, k, one);
+    };
+  } else {
+    matvec = [h, X, n, ldx, d, sigma, lambda, k](cudaStream_t s2, const double* V, double* Q) {
+      matvec_dispatch(h, s2, X, n, ldx, X, n, ldx, d, sigma, lambda, V, k, k, Q, k, KRR_HP);
+    };
+  }
+  apply = nullptr;
+  if (precond)
+    apply = [h, n, k, nk, one](cudaStream_t s2, const double* R, double* Zo) {
+      float* rf = wsT<float>(h, "v_cvr", nk);
+      float* zf = wsT<float>(h, "v_cvz", nk);
+      launch_convert<double, float>(s2, R, n, k, k, rf, k, one);
+      apply_precond<float>(h, s2, rf, k, k, zf, k);
+      launch_convert<float, double>(s2, zf, n, k, k, Zo, k, one);
+    };
+}
+
 // Mixed precision: BF16 tensor-core inner PCG with FP32 vectors; outer
 // iterative refinement with the residual in HP arithmetic and FP64 vectors.
 krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* matvecs) {
@@ -571,9 +638,9 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
   krr_status status = KRR_OK;
   int outer = 0;
   int remaining = a.o.max_iter;
-  // inner solves on the HP product once a BF16 correction contracts the
-  // residual by less than a half (see batched_mixed)
-  bool hp_inner = false;
+  // the inner arithmetic moves up a level (BF16 -> BF16x3 -> HP) once a
+  // correction contracts the residual by less than a half (see batched_mixed)
+  int level = INNER_BF16;
   double rel_prev = 0.0;
   double rel[KRR_MAX_RHS] = {0}, rel_saved[KRR_MAX_RHS] = {0};
   for (;;) {
@@ -587,6 +654,8 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
       if (!(rel[c] <= a.o.tol)) ok = false;
       now = std::max(now, rel[c]);
     }
+    KRR_TRACE("mixed: outer %d rel %.3e (previous %.3e) inner %s", outer, now, rel_prev,
+              level_name(level));
     if (finite && ok) break;
     if (outer > 0) {
       if (!finite || !(now < rel_prev)) {
@@ -596,13 +665,13 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
         host_colnorm2<double>(h, Rd, n, k, k, rr);
         for (int c = 0; c < k; ++c) rel[c] = rel_saved[c];
         finite = true;
-        if (hp_inner) {
+        if (level == INNER_HP) {
           status = KRR_ENOTCONV;
           break;
         }
-        hp_inner = true;
-      } else if (now > 0.5 * rel_prev) {
-        hp_inner = true;
+        level = next_level(level, a.d);
+      } else if (now > 0.5 * rel_prev && level != INNER_HP) {
+        level = next_level(level, a.d);
       }
     }
     if (!finite) {
@@ -629,16 +698,17 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
     KRR_CUDA(cudaMemcpyAsync(Rp, Rd, nk * sizeof(double), cudaMemcpyDeviceToDevice, st));
     launch_convert<double, double>(st, Rd, n, k, k, Rs, k, sc);
     LoopOut lo;
-    if (!hp_inner) {
+    if (level == INNER_BF16) {
+      const int prec = KRR_BF16;
       PcgSpec<float> S;
       S.n = n; S.k = k; S.Ytol = Rs; S.ldy = k;
       S.x = wsT<float>(h, "v_xf", nk); S.r = wsT<float>(h, "v_rf", nk);
       S.p = wsT<float>(h, "v_pf", nk); S.z = wsT<float>(h, "v_zf", nk);
       S.q = wsT<float>(h, "v_qf", nk);
-      S.tol = a.o.inner_tol; S.max_iter = remaining; S.prec = KRR_BF16;
-      S.matvec = [&](cudaStream_t s2, const float* V, float* Q) {
+      S.tol = inner_tol_for(level, a.o, rel_prev); S.max_iter = remaining; S.prec = prec;
+      S.matvec = [&, prec](cudaStream_t s2, const float* V, float* Q) {
         matvec_dispatch(h, s2, a.X, n, a.ldx, a.X, n, a.ldx, a.d, a.sigma, a.lambda, V, k, k, Q,
-                        k, KRR_BF16);
+                        k, prec);
       };
       if (a.o.precond)
         S.apply = [&](cudaStream_t s2, const float* R, float* Zo) {
@@ -654,16 +724,12 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
       S.x = wsT<double>(h, "v_x", nk); S.r = wsT<double>(h, "v_r", nk);
       S.p = wsT<double>(h, "v_p", nk); S.z = wsT<double>(h, "v_z", nk);
       S.q = wsT<double>(h, "v_q", nk);
-      S.tol = std::min(a.o.inner_tol, std::max(1e-11, 0.5 * a.o.tol / rel_prev));
-      S.max_iter = remaining; S.prec = KRR_HP;
-      S.matvec = [&](cudaStream_t s2, const double* V, double* Q) {
-        matvec_dispatch(h, s2, a.X, n, a.ldx, a.X, n, a.ldx, a.d, a.sigma, a.lambda, V, k, k, Q,
-                        k, KRR_HP);
-      };
-      if (a.o.precond)
-        S.apply = [&](cudaStream_t s2, const double* R, double* Zo) {
-          apply_precond<double>(h, s2, R, k, k, Zo, k);
-        };
+      S.tol = inner_tol_for(level, a.o, rel_prev);
+      S.max_iter = remaining;
+      S.prec = level == INNER_SPLIT ? KRR_BF16X3 : KRR_HP;
+      if (level == INNER_SPLIT) tc_prepare_split(h->tc, st, a.X, n, a.ldx, a.d, a.sigma);
+      double_inner_ops(h, a.X, n, a.ldx, a.d, a.sigma, a.lambda, k, level, a.o.precond != 0,
+                       S.matvec, S.apply);
       launch_convert<double, double>(st, Rs, n, k, k, S.r, k, one);
       KRR_CUDA(cudaMemsetAsync(S.x, 0, nk * sizeof(double), st));
       pcg_loop<double>(h, S, a.o.use_graph != 0, &lo, matvecs);
@@ -671,6 +737,7 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
     }
     for (int c = 0; c < k; ++c) total_iters[c] += lo.iters[c];
     remaining -= lo.iter;
+    KRR_TRACE("mixed: inner solve %d iterations, flags %d", lo.iter, lo.flags);
     // a NaN in the inner solve leaves Cd unchanged; the next pass takes the
     // correction back and switches to the HP inner solve
     matvec_dispatch(h, st, a.X, n, a.ldx, a.X, n, a.ldx, a.d, a.sigma, a.lambda, Cd, k, k, AX, k,
@@ -705,7 +772,7 @@ void check_solve_args(const krr_opts& o, int n, int d, int ldx, double sigma, do
   }
 }
 
-// Algorithm 1 lines 4-7 on device-resident operands: RFF features and the
+// The set-up of Algorithm 1 on device-resident operands: RFF features and the
 // preconditioner factors; for the mixed solve also the BF16 and HP operands.
 void setup_impl(krr_handle* h, const float* Xd, int n, int d, int ldx, double sigma,
                 double lambda, const float* Wd, const float* bd, int s, const krr_opts& o) {
@@ -905,9 +972,9 @@ struct BItem {
   double rel[KRR_MAX_RHS] = {0};
   double yy[KRR_MAX_RHS] = {0};
   ColScale inv;
-  // mixed precision: inner solves switch from BF16 to the HP product when a
-  // BF16 correction contracts the residual by less than a half
-  bool hp_inner = false;
+  // mixed precision: the inner arithmetic moves up a level (BF16 -> BF16x3
+  // -> HP) when a correction contracts the residual by less than a half
+  int level = INNER_BF16;
   double rel_prev = 0.0;
   double rel_saved[KRR_MAX_RHS] = {0};
 };
@@ -1103,15 +1170,15 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
           for (int c = 0; c < it.k; ++c) it.rel[c] = it.rel_saved[c];
           host_colnorm2<double>(g, Rd, it.n, it.k, it.k, rr);
           it.status = KRR_OK;
-          if (it.hp_inner) {
+          if (it.level == INNER_HP) {
             // HP inner solves no longer help: the HP residual's accuracy floor
             it.status = KRR_ENOTCONV;
             it.done = true;
             continue;
           }
-          it.hp_inner = true;
-        } else if (now > 0.5 * it.rel_prev) {
-          it.hp_inner = true;
+          it.level = next_level(it.level, it.d);
+        } else if (now > 0.5 * it.rel_prev && it.level != INNER_HP) {
+          it.level = next_level(it.level, it.d);
         }
       }
       if (it.status != KRR_OK) {
@@ -1136,16 +1203,21 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
           it.inv.v[c] = std::sqrt(rr[c]);
         }
       launch_convert<double, double>(g->stream, Rd, it.n, it.k, it.k, Rs, it.k, sc);
-      if (!it.hp_inner) {
+      if (it.level == INNER_BF16) {
         PcgSpec<float> S = item_spec<float>(it, Rs, o.inner_tol, KRR_BF16, o.precond != 0);
         launch_convert<double, float>(g->stream, Rs, it.n, it.k, it.k, S.r, it.k, one);
         KRR_CUDA(cudaMemsetAsync(S.x, 0, nk * sizeof(float), g->stream));
         pcg_begin<float>(g, S);
         E.push_back(BatchEntry{g, [g, S](cudaStream_t cs) { pcg_body<float>(g, S, cs, 0ull); }, 0});
       } else {
-        // one inner solve to the accuracy the outer test needs
-        const double tin = std::min(o.inner_tol, std::max(1e-11, 0.5 * o.tol / it.rel_prev));
-        PcgSpec<double> S = item_spec<double>(it, Rs, tin, KRR_HP, o.precond != 0);
+        // FP64 vectors; the split or HP product
+        if (it.level == INNER_SPLIT)
+          tc_prepare_split(g->tc, g->stream, it.X, it.n, it.ldx, it.d, it.sigma);
+        PcgSpec<double> S = item_spec<double>(it, Rs, inner_tol_for(it.level, o, it.rel_prev),
+                                              it.level == INNER_SPLIT ? KRR_BF16X3 : KRR_HP,
+                                              false);
+        double_inner_ops(g, it.X, it.n, it.ldx, it.d, it.sigma, it.lambda, it.k, it.level,
+                         o.precond != 0, S.matvec, S.apply);
         launch_convert<double, double>(g->stream, Rs, it.n, it.k, it.k, S.r, it.k, one);
         KRR_CUDA(cudaMemsetAsync(S.x, 0, nk * sizeof(double), g->stream));
         pcg_begin<double>(g, S);
@@ -1170,14 +1242,14 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
       double* Rd = wsT<double>(g, "v_rd", nk);
       double* AX = wsT<double>(g, "v_ax", nk);
       // a NaN in the inner solve leaves Cd unchanged; the next round takes
-      // the correction back and switches to the HP inner solve
-      if (lo.flags & FLAG_NAN) {
-      } else if (it.hp_inner) {
-        launch_axpy_d<double>(g->stream, wsT<double>(g, "v_x", nk), it.n, it.k, it.k, Cd, it.k,
-                              it.inv);
-      } else {
-        launch_axpy_d<float>(g->stream, wsT<float>(g, "v_xf", nk), it.n, it.k, it.k, Cd, it.k,
-                             it.inv);
+      // the correction back and moves the inner arithmetic up a level
+      if (!(lo.flags & FLAG_NAN)) {
+        if (it.level != INNER_BF16)
+          launch_axpy_d<double>(g->stream, wsT<double>(g, "v_x", nk), it.n, it.k, it.k, Cd, it.k,
+                                it.inv);
+        else
+          launch_axpy_d<float>(g->stream, wsT<float>(g, "v_xf", nk), it.n, it.k, it.k, Cd, it.k,
+                               it.inv);
       }
       matvec_dispatch(g, g->stream, it.X, it.n, it.ldx, it.X, it.n, it.ldx, it.d, it.sigma,
                       it.lambda, Cd, it.k, it.k, AX, it.k, KRR_HP);
@@ -1314,10 +1386,12 @@ krr_status krr_kernel_matvec(krr_handle* h, const float* Xr, int nr, int ldxr, c
                 "kernel_matvec: leading dimension too small");
     KRR_REQUIRE(sigma > 0.0 && std::isfinite(sigma), "kernel_matvec: sigma must be > 0");
     KRR_REQUIRE(shift == 0.0 || nr == nc, "kernel_matvec: shift needs a square product");
-    KRR_REQUIRE(precision >= KRR_FP64 && precision <= KRR_HP, "kernel_matvec: bad precision");
+    KRR_REQUIRE(precision == KRR_FP64 || precision == KRR_FP32 || precision == KRR_BF16 ||
+                    precision == KRR_HP || precision == KRR_BF16X3,
+                "kernel_matvec: bad precision");
     matvec_dispatch(h, h->stream, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, shift, V, k, ldv, Q, ldq,
                     precision);
-    if ((precision == KRR_BF16 && tc_error(h->tc, h->stream)) ||
+    if (((precision == KRR_BF16 || precision == KRR_BF16X3) && tc_error(h->tc, h->stream)) ||
         (precision == KRR_HP && hp_error(h->hp, h->stream)))
       throw Error{KRR_ETIMEOUT, "tensor-core product: a pipeline wait hit its limit"};
     return KRR_OK;

@@ -1,4 +1,4 @@
-// Conjugate-gradient vector kernels (Algorithm 1 line 9: PCG on
+// Conjugate-gradient vector kernels (the PCG step of Algorithm 1: PCG on
 // (K + lambda I) c = y with the random-feature preconditioner).
 //
 // Each column of the n x k block iterates independently (Section 5 asks the

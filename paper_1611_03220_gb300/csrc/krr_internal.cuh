@@ -78,7 +78,7 @@ struct CgScalars {
 
 enum : int { FLAG_BREAKDOWN = 1, FLAG_NAN = 2, FLAG_CAP = 4 };
 
-// Per-handle preconditioner state (Algorithm 1 lines 6-7).
+// Per-handle preconditioner state (the set-up step of Algorithm 1).
 struct Precond {
   bool ready = false;
   int n = 0, s = 0, form = KRR_APPLY_ZL, z_bf16 = 0;

@@ -1,7 +1,7 @@
 // High-precision kernel-matrix product on the BF16 tensor cores, for the
 // residual of the iterative refinement:
 //   Q = K(X, X) V + shift V,   K_ij = exp(-||x_i - x_j||^2 / (2 sigma^2)),
-// with V and Q in FP64 and K_ij accurate to about 1e-9 relative (the paper's
+// with V and Q in FP64 and K_ij accurate to about 1e-13 relative (the paper's
 // Gaussian kernel, Section 5; the product is the per-iteration cost named in
 // Section 3.1).  GB300's FP64 pipe runs at about 1/64 of FP32, so the FP64
 // arithmetic is replaced by exact integer products on the tensor cores and

@@ -33,7 +33,9 @@
 //              thread keeps CH independent accumulator chains per RHS.
 // Work items are (row tile, column chunk) pairs dealt round-robin; each item
 // writes one partial row sum per chunk, and a second kernel adds the chunks
-// in FP64, applies ra_i and the shift.  Every mbarrier wait is bounded: on
+// in FP64, applies ra_i and the shift.  This kernel serves k <= 2 right-hand
+// sides; from k = 3 on, tc_matvec2_kernel (below) contracts on the tensor
+// cores instead of the FMA pipe.  Every mbarrier wait is bounded: on
 // expiry the kernel raises an error flag, drains its own copies and MMAs,
 // frees TMEM and returns.
 #include <cuda.h>
@@ -82,6 +84,7 @@ struct TcParams {
   int n_rt, n_ct, nchunk, cpc, nkb;
   int n_rpad;
   int a_res;        // 1: one K-block, the row tile stays in shared memory per item
+  int x3;           // split points xh = hi + lo: S = hi.hi + lo.hi + hi.lo (a_res only)
   int ns;           // stages in the ring (<= NS_MAX)
   const float* w;   // n_ct*BN x KV
   float* part;      // nchunk x n_rpad x KV
@@ -112,6 +115,7 @@ __device__ __forceinline__ float ex2_fma(float x) {
 template <int KV>
 __global__ void __launch_bounds__(Cfg<KV>::THREADS, 1)
 tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
                  TcParams p) {
   constexpr int NEPI = Cfg<KV>::NEPI, NW = Cfg<KV>::NW, CH = Cfg<KV>::CH;
   constexpr int EMU = Cfg<KV>::EMU, COLS = Cfg<KV>::COLS, NG = NEPI / 4;
@@ -119,8 +123,9 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int NS = p.ns;
   const int sbytes = p.a_res ? B_BYTES : STAGE_BYTES;   // bytes per stage
-  uint8_t* abuf = smem;                                  // A_BYTES when a_res
-  uint8_t* stages = smem + (p.a_res ? A_BYTES : 0);
+  const int abytes = p.a_res ? (p.x3 ? 2 * A_BYTES : A_BYTES) : 0;
+  uint8_t* abuf = smem;                                  // row tile (hi, lo) when a_res
+  uint8_t* stages = smem + abytes;
   float* wbuf = (float*)(stages + NS * sbytes);          // NW x BN x KV
   float* comb = wbuf + NW * BN * KV;                     // (NG-1) x BM x KV
   uint64_t* bars = (uint64_t*)(comb + (NG - 1) * BM * KV);
@@ -175,8 +180,9 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         const int ct0 = ch * p.cpc, ct1 = min(p.n_ct, ct0 + p.cpc);
         if (p.a_res) {
           if (!(ok = mbar_wait(smem_u32(aempty), aph ^ 1, abort_flag, p.err))) break;
-          mbar_expect_tx(smem_u32(afull), A_BYTES);
+          mbar_expect_tx(smem_u32(afull), abytes);
           tma_load_2d(smem_u32(abuf), &tmA, 0, rt * BM, smem_u32(afull));
+          if (p.x3) tma_load_2d(smem_u32(abuf + A_BYTES), &tmA2, 0, rt * BM, smem_u32(afull));
           a_pending = true;
           aph ^= 1;
         }
@@ -193,8 +199,9 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             if (!(ok = mbar_wait(smem_u32(&empty[st]), ph ^ 1, abort_flag, p.err))) break;
             const uint32_t sa = smem_u32(stages + st * sbytes);
             if (p.a_res) {
+              // x3: stage 0 holds the column tile's hi slice, stage 1 its lo slice
               mbar_expect_tx(smem_u32(&full[st]), B_BYTES);
-              tma_load_2d(sa, &tmB, 0, ct * BN, smem_u32(&full[st]));
+              tma_load_2d(sa, kb == 1 ? &tmB2 : &tmB, 0, ct * BN, smem_u32(&full[st]));
             } else {
               mbar_expect_tx(smem_u32(&full[st]), STAGE_BYTES);
               tma_load_2d(sa, &tmA, kb * BK, rt * BM, smem_u32(&full[st]));
@@ -251,6 +258,12 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             for (int kk = 0; kk < BK / UK; ++kk)
               mma_bf16(d, sdesc(sa + kk * UK * 2), sdesc(sb + kk * UK * 2), IDESC,
                        (kb > 0 || kk > 0) ? 1u : 0u);
+            if (p.x3 && kb == 0) {
+              // lo rows against the hi columns
+#pragma unroll
+              for (int kk = 0; kk < BK / UK; ++kk)
+                mma_bf16(d, sdesc(sa + A_BYTES + kk * UK * 2), sdesc(sb + kk * UK * 2), IDESC, 1u);
+            }
             any = true;
             mma_commit(smem_u32(&empty[st]));
             if (++st == (uint32_t)NS) {
@@ -387,22 +400,374 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
   if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
 }
 
+// ------------------------------------------------------ two-GEMM variant --
+// For k >= 4 right-hand sides the per-entry FMAs against w dominate the
+// epilogue above.  This variant contracts on the tensor cores instead:
+//   S = xh_rows . xh_cols^T   GEMM 1 (M=128, N=128), double-buffered in TMEM
+//   P = bf16(exp2(S))          epilogue (MUFU), stored to shared memory in the
+//                              128-byte-swizzled K-major operand layout
+//   D += P . Vt^T              GEMM 2 (M=128, N=16, K=128), Vt = bf16(ra_j v_jc)
+// D (128 x 16 FP32 in TMEM) accumulates over the item's column tiles and the
+// epilogue writes it as the item's partial row sums.  P carries one more
+// BF16 rounding of each kernel entry and Vt one of each weight (2^-9
+// relative each), the same order as the point rounding that the outer
+// refinement removes.
+//   warp 0  TMA: row tile (resident when d <= 64), column-tile K-blocks, the
+//           tile's Vt block (two 64-column boxes).
+//   warp 1  MMA: GEMM 1 of tile t, then GEMM 2 of tile t-1 (P of tile t-1 is
+//           being written while GEMM 1 of tile t runs).
+//   warps 2-17  epilogue: warp w owns TMEM lanes 32*(w%4)..+31 and one of
+//           four 32-column quarters of the tile (half of one K-atom of P).
+constexpr int BN2 = 128;
+constexpr int N2 = 16;
+constexpr int NEPI2 = 16;
+constexpr int THREADS2 = 32 * (2 + NEPI2);
+constexpr int B2_BYTES = BN2 * BK * 2;             // 16 KiB
+constexpr int STAGE2_BYTES = A_BYTES + B2_BYTES;   // 32 KiB
+constexpr int P_ATOM = BM * 128;                   // 16 KiB: 128 rows x 64 BF16
+constexpr int P_BYTES = 2 * P_ATOM;                // 32 KiB
+constexpr int V_ATOM = N2 * 128;                   // 2 KiB: 16 rows x 64 BF16
+constexpr int V_BYTES = 2 * V_ATOM;                // 4 KiB
+constexpr int NV2 = 4;                             // Vt ring slots
+constexpr int TMEM_D2 = 2 * BN2;                   // D at TMEM columns 256..271
+constexpr uint32_t IDESC1 = idesc_bf16(BM, BN2);
+constexpr uint32_t IDESC2 = idesc_bf16(BM, N2);
+
+struct Tc2Params {
+  int n_rt, n_ct, nchunk, cpc, nkb, n_rpad, kv;
+  int a_res, ns;
+  int x3;       // split points as in tc_matvec_kernel (a_res only)
+  float* part;  // nchunk x n_rpad x kv
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t a, uint32_t x, uint32_t y, uint32_t z,
+                                             uint32_t w) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z),
+               "r"(w)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(THREADS2, 1)
+tc_matvec2_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmX2,
+                  const __grid_constant__ CUtensorMap tmV, Tc2Params p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int NS = p.ns;
+  const int sbytes = p.a_res ? B2_BYTES : STAGE2_BYTES;
+  const int abytes = p.a_res ? (p.x3 ? 2 * A_BYTES : A_BYTES) : 0;
+  uint8_t* abuf = smem;
+  uint8_t* stages = smem + abytes;
+  uint8_t* pbuf = stages + NS * sbytes;             // 2 x P_BYTES
+  uint8_t* vbuf = pbuf + 2 * P_BYTES;               // NV2 x V_BYTES
+  uint64_t* bars = (uint64_t*)(vbuf + NV2 * V_BYTES);
+  uint64_t* full = bars;
+  uint64_t* empty = full + NS_MAX;
+  uint64_t* tfull = empty + NS_MAX;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* pfull = tempty + 2;
+  uint64_t* pempty = pfull + 2;
+  uint64_t* vfull = pempty + 2;
+  uint64_t* vempty = vfull + NV2;
+  uint64_t* afull = vempty + NV2;
+  uint64_t* aempty = afull + 1;
+  uint64_t* dfull = aempty + 1;
+  uint64_t* dempty = dfull + 1;
+  uint64_t* drain = dempty + 1;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int items = p.n_rt * p.nchunk;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS_MAX; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(smem_u32(&tfull[s]), 1);
+      mbar_init(smem_u32(&tempty[s]), NEPI2);
+      mbar_init(smem_u32(&pfull[s]), NEPI2);
+      mbar_init(smem_u32(&pempty[s]), 1);
+    }
+    for (int s = 0; s < NV2; ++s) {
+      mbar_init(smem_u32(&vfull[s]), 1);
+      mbar_init(smem_u32(&vempty[s]), 1);
+    }
+    mbar_init(smem_u32(afull), 1);
+    mbar_init(smem_u32(aempty), 1);
+    mbar_init(smem_u32(dfull), 1);
+    mbar_init(smem_u32(dempty), 4);
+    mbar_init(smem_u32(drain), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t st = 0, ph = 0, vs = 0, vph = 0, aph = 0, issued = 0, vissued = 0;
+      bool ok = true, a_pending = false;
+      for (int item = blockIdx.x; ok && item < items; item += gridDim.x) {
+        const int rt = item / p.nchunk, ch = item % p.nchunk;
+        const int ct0 = ch * p.cpc, ct1 = min(p.n_ct, ct0 + p.cpc);
+        if (p.a_res) {
+          if (!(ok = mbar_wait(smem_u32(aempty), aph ^ 1, abort_flag, p.err))) break;
+          mbar_expect_tx(smem_u32(afull), abytes);
+          tma_load_2d(smem_u32(abuf), &tmX, 0, rt * BM, smem_u32(afull));
+          if (p.x3) tma_load_2d(smem_u32(abuf + A_BYTES), &tmX2, 0, rt * BM, smem_u32(afull));
+          a_pending = true;
+          aph ^= 1;
+        }
+        for (int ct = ct0; ok && ct < ct1; ++ct) {
+          if (!(ok = mbar_wait(smem_u32(&vempty[vs]), vph ^ 1, abort_flag, p.err))) break;
+          const uint32_t sv = smem_u32(vbuf + vs * V_BYTES);
+          mbar_expect_tx(smem_u32(&vfull[vs]), V_BYTES);
+          tma_load_2d(sv, &tmV, ct * BN2, 0, smem_u32(&vfull[vs]));
+          tma_load_2d(sv + V_ATOM, &tmV, ct * BN2 + 64, 0, smem_u32(&vfull[vs]));
+          ++vissued;
+          if (++vs == NV2) {
+            vs = 0;
+            vph ^= 1;
+          }
+          for (int kb = 0; kb < p.nkb; ++kb) {
+            if (!(ok = mbar_wait(smem_u32(&empty[st]), ph ^ 1, abort_flag, p.err))) break;
+            const uint32_t sa = smem_u32(stages + st * sbytes);
+            if (p.a_res) {
+              mbar_expect_tx(smem_u32(&full[st]), B2_BYTES);
+              tma_load_2d(sa, kb == 1 ? &tmX2 : &tmX, 0, ct * BN2, smem_u32(&full[st]));
+            } else {
+              mbar_expect_tx(smem_u32(&full[st]), STAGE2_BYTES);
+              tma_load_2d(sa, &tmX, kb * BK, rt * BM, smem_u32(&full[st]));
+              tma_load_2d(sa + A_BYTES, &tmX, kb * BK, ct * BN2, smem_u32(&full[st]));
+            }
+            ++issued;
+            if (++st == (uint32_t)NS) {
+              st = 0;
+              ph ^= 1;
+            }
+          }
+        }
+      }
+      if (!ok) {
+        // let the copies still in flight land before the CTA can exit
+        uint32_t s2 = st, p2 = ph;
+        const uint32_t nout = issued < (uint32_t)NS ? issued : (uint32_t)NS;
+        for (uint32_t q = 0; q < nout; ++q) {
+          if (s2 == 0) {
+            s2 = NS - 1;
+            p2 ^= 1;
+          } else {
+            --s2;
+          }
+          mbar_drain(smem_u32(&full[s2]), p2);
+        }
+        uint32_t v2 = vs, q2 = vph;
+        const uint32_t vout = vissued < (uint32_t)NV2 ? vissued : (uint32_t)NV2;
+        for (uint32_t q = 0; q < vout; ++q) {
+          if (v2 == 0) {
+            v2 = NV2 - 1;
+            q2 ^= 1;
+          } else {
+            --v2;
+          }
+          mbar_drain(smem_u32(&vfull[v2]), q2);
+        }
+        if (a_pending) mbar_drain(smem_u32(afull), aph ^ 1);
+      }
+    }
+  } else if (warp == 1) {
+    // ----------------------------------------------------------------- MMA
+    if (lane == 0) {
+      uint32_t st = 0, ph = 0, acc = 0, aph = 0, afp = 0, pb = 0, pph = 0, vs = 0, vph = 0;
+      uint32_t dph = 0;
+      bool ok = true, any = false;
+      const uint32_t pbase = smem_u32(pbuf), vbase = smem_u32(vbuf);
+      // GEMM 2 of the tile whose P sits in buffer pb and whose Vt sits in slot vs
+      auto gemm2 = [&](bool first) -> bool {
+        if (first) {
+          if (!mbar_wait(smem_u32(dempty), dph ^ 1, abort_flag, p.err)) return false;
+          dph ^= 1;
+        }
+        if (!mbar_wait(smem_u32(&pfull[pb]), pph, abort_flag, p.err)) return false;
+        if (!mbar_wait(smem_u32(&vfull[vs]), vph, abort_flag, p.err)) return false;
+        fence_after();
+        const uint32_t pa = pbase + pb * P_BYTES, va = vbase + vs * V_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < BN2 / UK; ++kk) {
+          const uint32_t g = kk >> 2, o = (kk & 3) * UK * 2;
+          mma_bf16(tmem + TMEM_D2, sdesc(pa + g * P_ATOM + o), sdesc(va + g * V_ATOM + o), IDESC2,
+                   (!first || kk > 0) ? 1u : 0u);
+        }
+        any = true;
+        mma_commit(smem_u32(&pempty[pb]));
+        mma_commit(smem_u32(&vempty[vs]));
+        pb ^= 1;
+        if (pb == 0) pph ^= 1;
+        if (++vs == NV2) {
+          vs = 0;
+          vph ^= 1;
+        }
+        return true;
+      };
+      for (int item = blockIdx.x; ok && item < items; item += gridDim.x) {
+        const int ch = item % p.nchunk;
+        const int ct0 = ch * p.cpc, ct1 = min(p.n_ct, ct0 + p.cpc);
+        if (p.a_res) {
+          if (!(ok = mbar_wait(smem_u32(afull), afp, abort_flag, p.err))) break;
+          afp ^= 1;
+          fence_after();
+        }
+        for (int ct = ct0; ok && ct < ct1; ++ct) {
+          if (!(ok = mbar_wait(smem_u32(&tempty[acc]), aph ^ 1, abort_flag, p.err))) break;
+          fence_after();
+          const uint32_t d = tmem + acc * BN2;
+          for (int kb = 0; kb < p.nkb; ++kb) {
+            if (!(ok = mbar_wait(smem_u32(&full[st]), ph, abort_flag, p.err))) break;
+            fence_after();
+            const uint32_t ss = smem_u32(stages + st * sbytes);
+            const uint32_t sa = p.a_res ? smem_u32(abuf) : ss;
+            const uint32_t sb = p.a_res ? ss : ss + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / UK; ++kk)
+              mma_bf16(d, sdesc(sa + kk * UK * 2), sdesc(sb + kk * UK * 2), IDESC1,
+                       (kb > 0 || kk > 0) ? 1u : 0u);
+            if (p.x3 && kb == 0) {
+#pragma unroll
+              for (int kk = 0; kk < BK / UK; ++kk)
+                mma_bf16(d, sdesc(sa + A_BYTES + kk * UK * 2), sdesc(sb + kk * UK * 2), IDESC1,
+                         1u);
+            }
+            any = true;
+            mma_commit(smem_u32(&empty[st]));
+            if (++st == (uint32_t)NS) {
+              st = 0;
+              ph ^= 1;
+            }
+          }
+          if (!ok) break;
+          mma_commit(smem_u32(&tfull[acc]));
+          acc ^= 1;
+          if (acc == 0) aph ^= 1;
+          if (ct > ct0 && !(ok = gemm2(ct - 1 == ct0))) break;
+        }
+        if (!ok) break;
+        if (!(ok = gemm2(ct1 - 1 == ct0))) break;
+        mma_commit(smem_u32(dfull));
+        if (p.a_res) mma_commit(smem_u32(aempty));
+      }
+      if (any) {
+        mma_commit(smem_u32(drain));
+        mbar_drain(smem_u32(drain), 0);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int e = warp - 2;
+    const int quad = warp & 3;
+    const int grp = e >> 2;  // 32-column quarter
+    const int row = quad * 32 + lane;
+    const uint32_t prow = (uint32_t)(grp >> 1) * P_ATOM + (uint32_t)(row >> 3) * 1024u +
+                          (uint32_t)(row & 7) * 128u;
+    const uint32_t psw = (uint32_t)(row & 7);
+    const uint32_t q0 = (uint32_t)(grp & 1) * 4;
+    const uint32_t pbase = smem_u32(pbuf);
+    uint32_t acc = 0, aph = 0, pb = 0, pph = 0, dph = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+      const int rt = item / p.nchunk, ch = item % p.nchunk;
+      const int ct0 = ch * p.cpc, ct1 = min(p.n_ct, ct0 + p.cpc);
+      for (int ct = ct0; ok && ct < ct1; ++ct) {
+        if (!(ok = mbar_wait(smem_u32(&tfull[acc]), aph, abort_flag, p.err))) break;
+        fence_after();
+        const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + acc * BN2 + grp * 32;
+        uint32_t raw[32];
+        tmem_ld16_nowait(tbase, *reinterpret_cast<uint32_t(*)[16]>(&raw[0]));
+        tmem_ld16_nowait(tbase + 16, *reinterpret_cast<uint32_t(*)[16]>(&raw[16]));
+        tmem_wait_ld();
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&tempty[acc]));
+        uint32_t pk[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          pk[j] = pack_bf16(ex2_mufu(__uint_as_float(raw[2 * j])),
+                            ex2_mufu(__uint_as_float(raw[2 * j + 1])));
+        // P buffer pb is free once GEMM 2 of two tiles back has read it
+        if (!(ok = mbar_wait(smem_u32(&pempty[pb]), pph ^ 1, abort_flag, p.err))) break;
+        const uint32_t pa = pbase + pb * P_BYTES + prow;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          st_shared_v4(pa + (((q0 + u) ^ psw) << 4), pk[4 * u], pk[4 * u + 1], pk[4 * u + 2],
+                       pk[4 * u + 3]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&pfull[pb]));
+        acc ^= 1;
+        if (acc == 0) aph ^= 1;
+        pb ^= 1;
+        if (pb == 0) pph ^= 1;
+      }
+      if (ok) ok = mbar_wait(smem_u32(dfull), dph, abort_flag, p.err);
+      dph ^= 1;
+      if (ok && grp == 0) {
+        fence_after();
+        uint32_t dv[16];
+        tmem_ld16_nowait(tmem + ((uint32_t)(quad * 32) << 16) + TMEM_D2, dv);
+        tmem_wait_ld();
+        float* out = p.part + ((size_t)ch * p.n_rpad + (size_t)rt * BM + row) * p.kv;
+#pragma unroll
+        for (int c = 0; c < N2; ++c)
+          if (c < p.kv) out[c] = __uint_as_float(dv[c]);
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(dempty));
+      }
+      if (bar_or<NEPI2 * 32>(!ok || *abort_flag)) break;
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+}
+
 // ------------------------------------------------------------ helpers ----
 // xh = bf16(scale (x - mu)) padded to n_pad x kp, nh = ||xh||^2, ra = exp2(-nh/2).
+// With Xlo the points are split, xh = hi + lo with lo = bf16(u - hi), and nh
+// is taken of hi + lo.
 __global__ void prep_rows_kernel(const float* __restrict__ X, int n, int ld, int d,
                                  const double* __restrict__ mu, double scale, int n_pad, int kp,
-                                 __nv_bfloat16* __restrict__ Xa, float* __restrict__ ra,
-                                 float* __restrict__ nh_out) {
+                                 __nv_bfloat16* __restrict__ Xa, __nv_bfloat16* __restrict__ Xlo,
+                                 float* __restrict__ ra, float* __restrict__ nh_out) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= n_pad) return;
   const int i = warp;
   double nh = 0.0;
   for (int t = lane; t < kp; t += 32) {
-    float v = 0.f;
-    if (i < n && t < d) v = (float)(scale * ((double)X[(size_t)i * ld + t] - mu[t]));
-    __nv_bfloat16 b = __float2bfloat16_rn(v);
+    double u = 0.0;
+    if (i < n && t < d) u = scale * ((double)X[(size_t)i * ld + t] - mu[t]);
+    const __nv_bfloat16 b = __float2bfloat16_rn((float)u);
     Xa[(size_t)i * kp + t] = b;
     double bv = (double)__bfloat162float(b);
+    if (Xlo) {
+      const __nv_bfloat16 l = __float2bfloat16_rn((float)(u - bv));
+      Xlo[(size_t)i * kp + t] = l;
+      bv += (double)__bfloat162float(l);
+    }
     nh += bv * bv;
   }
   for (int off = 16; off; off >>= 1) nh += __shfl_xor_sync(0xffffffffu, nh, off);
@@ -436,6 +801,18 @@ __global__ void make_w_kernel(const float* __restrict__ V, int n, int k, int ldv
        e += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(e / kv), c = (int)(e % kv);
     w[e] = (j < n && c < k) ? ra[j] * V[(size_t)j * ldv + c] : 0.f;
+  }
+}
+
+// Vt[c, j] = bf16(ra_j v[j, c]) for c < k, 0 for padding; N2 x n_pad, j fastest.
+__global__ void make_vt_kernel(const float* __restrict__ V, int n, int k, int ldv,
+                               const float* __restrict__ ra, int n_pad,
+                               __nv_bfloat16* __restrict__ vt) {
+  const size_t total = (size_t)N2 * n_pad;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / n_pad), j = (int)(e % n_pad);
+    vt[e] = __float2bfloat16_rn((j < n && c < k) ? ra[j] * V[(size_t)j * ldv + c] : 0.f);
   }
 }
 
@@ -530,50 +907,83 @@ int choose_nchunk(int n_rt, int n_ct, int grid) {
 }
 
 template <int KV>
-size_t smem_bytes(int a_res, int ns) {
+size_t smem_bytes(int a_res, int ns, int x3) {
   constexpr int NW = Cfg<KV>::NW, NG = Cfg<KV>::NEPI / 4;
-  return 1024 + (a_res ? (size_t)A_BYTES + (size_t)ns * B_BYTES : (size_t)ns * STAGE_BYTES) +
+  return 1024 +
+         (a_res ? (size_t)(x3 ? 2 : 1) * A_BYTES + (size_t)ns * B_BYTES
+                : (size_t)ns * STAGE_BYTES) +
          (size_t)NW * BN * KV * 4 + (size_t)(NG - 1) * BM * KV * 4 + 256;
 }
 
 template <int KV>
-void launch_kernel(cudaStream_t st, const CUtensorMap& a, const CUtensorMap& b, const TcParams& p,
-                   int grid) {
+void launch_kernel(cudaStream_t st, const CUtensorMap& a, const CUtensorMap& b,
+                   const CUtensorMap& a2, const CUtensorMap& b2, const TcParams& p, int grid) {
   static size_t attr = 0;
-  const size_t sm = smem_bytes<KV>(p.a_res, p.ns);
+  const size_t sm = smem_bytes<KV>(p.a_res, p.ns, p.x3);
   if (attr < sm) {
     KRR_CUDA(cudaFuncSetAttribute(tc_matvec_kernel<KV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sm));
     attr = sm;
   }
-  tc_matvec_kernel<KV><<<grid, Cfg<KV>::THREADS, sm, st>>>(a, b, p);
+  tc_matvec_kernel<KV><<<grid, Cfg<KV>::THREADS, sm, st>>>(a, b, a2, b2, p);
   KRR_CHECK_LAUNCH();
 }
 
-void dispatch(int kv, cudaStream_t st, const CUtensorMap& a, const CUtensorMap& b,
-              const TcParams& p, int grid) {
-  switch (kv) {
-    case 1: launch_kernel<1>(st, a, b, p, grid); break;
-    case 2: launch_kernel<2>(st, a, b, p, grid); break;
-    case 4: launch_kernel<4>(st, a, b, p, grid); break;
-    case 8: launch_kernel<8>(st, a, b, p, grid); break;
-    case 12: launch_kernel<12>(st, a, b, p, grid); break;
-    default: launch_kernel<16>(st, a, b, p, grid); break;
-  }
+void dispatch(int kv, cudaStream_t st, const TcOperand& op, const TcParams& p, int grid) {
+  if (kv == 1)
+    launch_kernel<1>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid);
+  else
+    launch_kernel<2>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid);
 }
 
-// Prepare one operand set into `op`.
+size_t smem2_bytes(int a_res, int ns, int x3) {
+  return 1024 +
+         (a_res ? (size_t)(x3 ? 2 : 1) * A_BYTES + (size_t)ns * B2_BYTES
+                : (size_t)ns * STAGE2_BYTES) +
+         (size_t)2 * P_BYTES + (size_t)NV2 * V_BYTES + 256;
+}
+
+void launch_kernel2(cudaStream_t st, const CUtensorMap& x, const CUtensorMap& x2,
+                    const CUtensorMap& v, const Tc2Params& p, int grid) {
+  static size_t attr = 0;
+  const size_t sm = smem2_bytes(p.a_res, p.ns, p.x3);
+  if (attr < sm) {
+    KRR_CUDA(cudaFuncSetAttribute(tc_matvec2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm));
+    attr = sm;
+  }
+  tc_matvec2_kernel<<<grid, THREADS2, sm, st>>>(x, x2, v, p);
+  KRR_CHECK_LAUNCH();
+}
+
+// Vt tensor map: N2 rows of n_pad BF16, boxes of 64 columns x N2 rows.
+void make_vt_map(CUtensorMap* m, const void* base, int n_pad) {
+  cuuint64_t gdim[2] = {(cuuint64_t)n_pad, (cuuint64_t)N2};
+  cuuint64_t gstride[1] = {(cuuint64_t)n_pad * 2};
+  cuuint32_t box[2] = {64, (cuuint32_t)N2};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim,
+                           gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    throw Error{KRR_ECUDA, "cuTensorMapEncodeTiled (Vt) failed: " + std::to_string((int)r)};
+}
+
+// Prepare one operand set into `op` (split into hi + lo when `split`).
 void prep_operand(TcOperand& op, cudaStream_t st, const float* X, int n, int ld, int d,
-                  const double* mu, double scale) {
+                  const double* mu, double scale, bool split) {
   const int kp = (d + BK - 1) / BK * BK;
   const int n_pad = (n + PAD - 1) / PAD * PAD;
   ensure(op.Xa, (size_t)n_pad * kp * 2);
+  if (split) ensure(op.Xlo, (size_t)n_pad * kp * 2);
   ensure(op.ra, (size_t)n_pad * 4);
   ensure(op.nh, (size_t)n_pad * 4 + 16);
   prep_rows_kernel<<<(n_pad * 32 + 255) / 256, 256, 0, st>>>(
-      X, n, ld, d, mu, scale, n_pad, kp, (__nv_bfloat16*)op.Xa.p, (float*)op.ra.p,
-      (float*)op.nh.p);
+      X, n, ld, d, mu, scale, n_pad, kp, (__nv_bfloat16*)op.Xa.p,
+      split ? (__nv_bfloat16*)op.Xlo.p : nullptr, (float*)op.ra.p, (float*)op.nh.p);
   KRR_CHECK_LAUNCH();
+  op.split = split;
   op.src = X;
   op.n = n;
   op.ld = ld;
@@ -582,17 +992,22 @@ void prep_operand(TcOperand& op, cudaStream_t st, const float* X, int n, int ld,
   op.n_pad = n_pad;
   make_map(&op.map_a, op.Xa.p, n_pad, kp, BM);
   make_map(&op.map_b, op.Xa.p, n_pad, kp, BN);
+  make_map(&op.map_a2, split ? op.Xlo.p : op.Xa.p, n_pad, kp, BM);
+  make_map(&op.map_b2, split ? op.Xlo.p : op.Xa.p, n_pad, kp, BN);
 }
 
 struct Plan {
   int kv, n_rt, n_ct, cpc, nchunk;
 };
 
+// Right-hand-side counts from which the two-GEMM variant is used.
+constexpr int KV_GEMM2 = 4;
+
 Plan plan_for(const TcOperand& op, int k) {
   Plan pl;
   pl.kv = kv_bucket(k);
   pl.n_rt = op.n_pad / BM;
-  pl.n_ct = op.n_pad / BN;
+  pl.n_ct = op.n_pad / (pl.kv >= KV_GEMM2 ? BN2 : BN);
   const int req = choose_nchunk(pl.n_rt, pl.n_ct, sm_count());
   pl.cpc = (pl.n_ct + req - 1) / req;
   pl.nchunk = (pl.n_ct + pl.cpc - 1) / pl.cpc;
@@ -610,7 +1025,7 @@ void tc_prepare(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int
   ensure(t.mu, (size_t)d * sizeof(double));
   ensure(t.w, (size_t)((n + 127) / 128) * d * sizeof(double));  // w doubles as the slab scratch
   launch_colmean(st, X, n, ldx, d, (double*)t.mu.p, (double*)t.w.p);
-  prep_operand(t.cols, st, X, n, ldx, d, (const double*)t.mu.p, scale);
+  prep_operand(t.cols, st, X, n, ldx, d, (const double*)t.mu.p, scale, false);
   ensure(t.scal, 16);
   KRR_CUDA(cudaMemsetAsync(t.scal.p, 0, 16, st));
   max_kernel<<<std::min(8 * sm_count(), (t.cols.n_pad + 255) / 256), 256, 0, st>>>(
@@ -628,11 +1043,29 @@ void tc_prepare(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int
   t.ready = true;
 }
 
+void tc_prepare_split(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int d,
+                      double sigma) {
+  tc_prepare(t, st, X, n, ldx, d, sigma);
+  if (t.split_ready && t.split.src == X && t.split.n == n && t.split.ld == ldx && t.split.d == d &&
+      t.split_sigma == sigma)
+    return;
+  if (t.cols.kp != BK)
+    throw Error{KRR_EUNSUPPORTED, "split BF16 product needs d <= 64"};
+  const double c = 1.4426950408889634 / (2.0 * sigma * sigma);
+  prep_operand(t.split, st, X, n, ldx, d, (const double*)t.mu.p, std::sqrt(2.0 * c), true);
+  t.split_sigma = sigma;
+  t.split_ready = true;
+}
+
 void tc_reserve(TcState& t, cudaStream_t st, int k) {
   if (!t.ready) throw Error{KRR_EINVAL, "tensor-core product used before tc_prepare"};
   const Plan pl = plan_for(t.cols, k);
   ensure(t.w, (size_t)t.cols.n_pad * pl.kv * 4);
   ensure(t.part, (size_t)pl.nchunk * t.cols.n_pad * pl.kv * 4);
+  if (pl.kv >= KV_GEMM2 && t.vt.bytes < (size_t)N2 * t.cols.n_pad * 2) {
+    ensure(t.vt, (size_t)N2 * t.cols.n_pad * 2);
+    make_vt_map(&t.map_v, t.vt.p, t.cols.n_pad);
+  }
   if (!t.err.p) {
     ensure(t.err, 16);
     KRR_CUDA(cudaMemsetAsync(t.err.p, 0, 16, st));
@@ -645,13 +1078,47 @@ void tc_clear_error(TcState& t, cudaStream_t st) {
 
 void tc_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
                int nc, int ldxc, int d, double sigma, double shift, const float* V, int k,
-               int ldv, float* Q, int ldq) {
+               int ldv, float* Q, int ldq, int split) {
   const bool same = (Xr == Xc && nr == nc && ldxr == ldxc);
   if (!same) throw Error{KRR_EUNSUPPORTED, "BF16 product supports the training system (Xr == Xc)"};
-  tc_prepare(t, st, Xc, nc, ldxc, d, sigma);
+  if (split)
+    tc_prepare_split(t, st, Xc, nc, ldxc, d, sigma);
+  else
+    tc_prepare(t, st, Xc, nc, ldxc, d, sigma);
   tc_reserve(t, st, k);
-  TcOperand& op = t.cols;
+  TcOperand& op = split ? t.split : t.cols;
   const Plan pl = plan_for(op, k);
+  // split points: the row tile's hi and lo stay resident, each column tile
+  // streams its hi and lo slices as two stages
+  const int nkb = split ? 2 : op.kp / BK;
+  const int a_res = (split || nkb == 1) ? 1 : 0;
+  if (pl.kv >= KV_GEMM2) {
+    make_vt_kernel<<<std::min(8 * sm_count(), (int)(((size_t)N2 * op.n_pad + 255) / 256)), 256,
+                     0, st>>>(V, nc, k, ldv, (const float*)op.ra.p, op.n_pad,
+                              (__nv_bfloat16*)t.vt.p);
+    KRR_CHECK_LAUNCH();
+    Tc2Params p2;
+    p2.n_rt = pl.n_rt;
+    p2.n_ct = pl.n_ct;
+    p2.nchunk = pl.nchunk;
+    p2.cpc = pl.cpc;
+    p2.nkb = nkb;
+    p2.n_rpad = op.n_pad;
+    p2.kv = pl.kv;
+    p2.a_res = a_res;
+    p2.ns = a_res ? 4 : 3;
+    p2.x3 = split;
+    p2.part = (float*)t.part.p;
+    p2.err = (int*)t.err.p;
+    const int grid2 = std::min(pl.n_rt * pl.nchunk, sm_count());
+    launch_kernel2(st, op.map_a, op.map_a2, t.map_v, p2, grid2);
+    const size_t total2 = (size_t)nr * k;
+    tc_reduce_kernel<<<std::min(8 * sm_count(), (int)((total2 + 255) / 256)), 256, 0, st>>>(
+        (const float*)t.part.p, pl.nchunk, op.n_pad, pl.kv, (const float*)op.ra.p, nr, k, V, ldv,
+        shift, Q, ldq);
+    KRR_CHECK_LAUNCH();
+    return;
+  }
   make_w_kernel<<<std::min(8 * sm_count(), (int)(((size_t)op.n_pad * pl.kv + 255) / 256)), 256,
                   0, st>>>(V, nc, k, ldv, (const float*)op.ra.p, op.n_pad, pl.kv, (float*)t.w.p);
   KRR_CHECK_LAUNCH();
@@ -660,16 +1127,17 @@ void tc_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr, c
   p.n_ct = pl.n_ct;
   p.nchunk = pl.nchunk;
   p.cpc = pl.cpc;
-  p.nkb = op.kp / BK;
-  p.a_res = p.nkb == 1 ? 1 : 0;
-  p.ns = p.a_res ? 4 : 3;
+  p.nkb = nkb;
+  p.a_res = a_res;
+  p.ns = a_res ? 4 : 3;
+  p.x3 = split;
   p.n_rpad = op.n_pad;
   p.w = (const float*)t.w.p;
   p.part = (float*)t.part.p;
   p.err = (int*)t.err.p;
   const int items = pl.n_rt * pl.nchunk;
   const int grid = std::min(items, sm_count());
-  dispatch(pl.kv, st, op.map_a, op.map_b, p, grid);
+  dispatch(pl.kv, st, op, p, grid);
   const size_t total = (size_t)nr * k;
   tc_reduce_kernel<<<std::min(8 * sm_count(), (int)((total + 255) / 256)), 256, 0, st>>>(
       (const float*)t.part.p, pl.nchunk, op.n_pad, pl.kv, (const float*)op.ra.p, nr, k, V, ldv,
@@ -686,7 +1154,9 @@ int tc_error(TcState& t, cudaStream_t st) {
 }
 
 void tc_release(TcState& t) {
-  DevBuf* bufs[] = {&t.cols.Xa, &t.cols.ra, &t.cols.nh, &t.mu, &t.scal, &t.w, &t.part, &t.err};
+  DevBuf* bufs[] = {&t.cols.Xa, &t.cols.ra, &t.cols.nh, &t.mu,        &t.scal,
+                    &t.w,       &t.part,    &t.err,     &t.vt,        &t.split.Xa,
+                    &t.split.Xlo, &t.split.ra, &t.split.nh};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   t = TcState();

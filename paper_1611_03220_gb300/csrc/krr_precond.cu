@@ -1,5 +1,5 @@
 // Random-feature preconditioner M = Z Z^T + lambda_p I (Section 3.1,
-// Algorithm 1 lines 6-9):
+// Algorithm 1):
 //   G = Z^T Z + lambda_p I_s              gram_kernel / gram_finalize_kernel
 //   L L^T = G (lower, FP64)               potrf / trsm / syrk kernels
 //   L^-1 (for the ZL apply form)          diag_inv / offdiag_inv kernels

@@ -1,7 +1,7 @@
 // Random Fourier features, Section 2.2 of the paper:
 //   Z[i, j] = sqrt(2/s) cos(x_i . w_j + b_j)
 // with w_j ~ N(0, sigma^-2 I) and b_j ~ U[0, 2 pi) supplied by the caller
-// (Algorithm 1 lines 4-5).  The sqrt(2/s) scale makes E[Z Z^T] = K; the
+// (the feature step of Algorithm 1).  The sqrt(2/s) scale makes E[Z Z^T] = K; the
 // printed s^-1/2 omits the factor 2 of E[cos(a + b) cos(c + b)].
 //
 // One FP32 register-tiled GEMM X W (128 x 128 tile per CTA, 8 x 8 per

@@ -10,11 +10,14 @@ namespace krr {
 // (K-major, 128-byte rows per 64-element K-block), nh = ||xh||^2 and
 // ra = exp2(-nh / 2), with TMA descriptors for 128-row and 256-row boxes.
 struct TcOperand {
-  DevBuf Xa, ra, nh;
+  DevBuf Xa, Xlo, ra, nh;   // Xlo: low BF16 parts of split points (else unused)
   const float* src = nullptr;
   int n = 0, ld = 0, d = 0, kp = 0, n_pad = 0;
+  bool split = false;
   CUtensorMap map_a;
   CUtensorMap map_b;
+  CUtensorMap map_a2;       // the low parts (split), else the same as map_a / map_b
+  CUtensorMap map_b2;
 };
 
 struct TcState {
@@ -24,14 +27,19 @@ struct TcState {
   DevBuf w;             // n_pad x kv column weights ra_j v_j
   DevBuf part;          // nchunk x n_pad x kv partial row sums
   DevBuf err;           // device error flag (bounded-wait expiry)
+  DevBuf vt;            // 16 x n_pad BF16 ra_j v_jc (two-GEMM variant, k >= 3)
+  CUtensorMap map_v;
+  TcOperand split;      // split points xh = hi + lo (KRR_BF16X3, d <= 64)
+  double split_sigma = 0.0;
+  bool split_ready = false;
   double sigma = 0.0;
   bool rows_same = false;
   bool ready = false;
   bool err_zeroed = false;
 };
 
-// High-precision product state (krr_matvec_hp.cu): four base-512 fixed-point
-// digit slices of the centred, scaled points (BF16, (4 n_pad) x 64), per-row
+// High-precision product state (krr_matvec_hp.cu): five base-512 fixed-point
+// digit slices of the centred, scaled points (BF16, (5 n_pad) x 64), per-row
 // (a_hi, a_lo, 2^(E-8)), per-call column records and partial sums.
 struct HpState {
   DevBuf mu, slab, slices, rowd, cold, part, err;
@@ -46,7 +54,7 @@ struct HpState {
 bool hp_supported(int d);
 void hp_prepare(HpState& t, cudaStream_t st, const float* X, int n, int ldx, int d, double sigma);
 void hp_reserve(HpState& t, cudaStream_t st, int k);
-// Q = K(X, X) V + shift V with V, Q in FP64 and K_ij to ~1e-9 relative (d <= 64).
+// Q = K(X, X) V + shift V with V, Q in FP64 and K_ij to ~1e-13 relative (d <= 64).
 void hp_matvec(HpState& t, cudaStream_t st, const float* X, int n, int ldx, int d, double sigma,
                double shift, const double* V, int k, int ldv, double* Q, int ldq);
 void hp_clear_error(HpState& t, cudaStream_t st);
@@ -55,10 +63,14 @@ void hp_release(HpState& t);
 
 // Prepare the operands for the training set X (n x d, ldx) at bandwidth sigma.
 void tc_prepare(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int d, double sigma);
-// Q = K(X, X) V + shift V through the tensor cores (Xr must equal Xc).
+// Also the split operands xh = bf16(u) + bf16(u - bf16(u)) (d <= 64).
+void tc_prepare_split(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int d,
+                      double sigma);
+// Q = K(X, X) V + shift V through the tensor cores (Xr must equal Xc); with
+// `split` the dot products use split points (hi.hi + lo.hi + hi.lo).
 void tc_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
                int nc, int ldxc, int d, double sigma, double shift, const float* V, int k,
-               int ldv, float* Q, int ldq);
+               int ldv, float* Q, int ldq, int split = 0);
 // Allocate the product's workspace for k right-hand sides (call before a
 // graph capture; tc_prepare must have run).
 void tc_reserve(TcState& t, cudaStream_t st, int k);

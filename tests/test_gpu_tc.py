@@ -40,6 +40,12 @@ def h(K):
     hh.close()
 
 
+def bf16_round(a):
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32))
+    return t.to(torch.bfloat16).to(torch.float64).numpy()
+
+
 def rounded_points(X, sigma):
     """xh = bf16(sqrt(log2 e)/sigma * (x - mean)) in FP64 (mean in FP64)."""
     X64 = X.astype(np.float64)
@@ -49,7 +55,8 @@ def rounded_points(X, sigma):
     return torch.from_numpy(xf).to(torch.bfloat16).to(torch.float64).numpy()
 
 
-@pytest.mark.parametrize("n,d,k", [(1000, 37, 1), (777, 64, 3), (1300, 100, 10), (300, 8, 16)])
+@pytest.mark.parametrize("n,d,k", [(1000, 37, 1), (777, 64, 3), (1300, 100, 10), (300, 8, 16),
+                                   (2000, 784, 10), (520, 64, 2)])
 def test_matvec_bf16_matches_rounded_oracle(K, h, n, d, k):
     rng = np.random.default_rng(n + d + k)
     X = rng.standard_normal((n, d)).astype(np.float32)
@@ -64,11 +71,62 @@ def test_matvec_bf16_matches_rounded_oracle(K, h, n, d, k):
     ref = Kh @ V.astype(np.float64)
     scale = Kh @ np.abs(V.astype(np.float64))
     got = Q.cpu().numpy().astype(np.float64)
-    assert np.all(np.abs(got - ref) <= 1e-5 * scale), np.max(np.abs(got - ref) / scale)
+    if k < 3:
+        # FP32 exponentials contracted in FP32
+        assert np.all(np.abs(got - ref) <= 1e-5 * scale), np.max(np.abs(got - ref) / scale)
+    else:
+        # two-GEMM variant: P = bf16(exp2(xh_i.xh_j)) and Vt = bf16(ra_j v_j) on the
+        # tensor cores; emulate both roundings in FP64 (round to nearest even)
+        S = Xh @ Xh.T
+        P = bf16_round(np.exp2(S))
+        ra = np.exp2(-0.5 * np.sum(Xh * Xh, axis=1)).astype(np.float32).astype(np.float64)
+        Vt = bf16_round((ra[:, None] * V.astype(np.float64)).astype(np.float32))
+        emul = ra[:, None] * (P @ Vt)
+        assert np.all(np.abs(got - emul) <= 1e-3 * scale), np.max(np.abs(got - emul) / scale)
+        # each term carries two BF16 roundings of at most 2^-9 relative
+        assert np.all(np.abs(got - ref) <= 2 ** -8 * scale), np.max(np.abs(got - ref) / scale)
     # and against the exact kernel of the unrounded points: the BF16 rounding of x
     # moves -||x_i - x_j||^2/(2 sigma^2) by about 2^-8 of its size
     exact = O.gaussian_kernel(X, X, sigma) @ V.astype(np.float64)
     assert np.all(np.abs(got - exact) <= 3e-2 * scale)
+
+
+def split_points(X, sigma):
+    """hi = bf16(u), lo = bf16(u - hi) for u = sqrt(log2 e)/sigma (x - mean), in FP64."""
+    X64 = X.astype(np.float64)
+    u = (math.sqrt(LOG2E) / sigma) * (X64 - X64.mean(axis=0))
+    hi = bf16_round(u.astype(np.float32))
+    lo = bf16_round((u - hi).astype(np.float32))
+    return hi, lo
+
+
+@pytest.mark.parametrize("n,d,k", [(1000, 37, 1), (600, 64, 2), (777, 54, 4), (300, 8, 16)])
+def test_matvec_bf16x3_matches_split_oracle(K, h, n, d, k):
+    """Split points xh = hi + lo: S = hi.hi + lo.hi + hi.lo on the tensor cores
+    (lo.lo dropped), norms of hi + lo.  Emulated in FP64; k >= 3 adds the BF16
+    rounding of exp2(S) and of the weights (two-GEMM variant)."""
+    rng = np.random.default_rng(n + d + k + 7)
+    X = (rng.standard_normal((n, d)) * np.linspace(0.5, 2.0, d)).astype(np.float32)
+    V = rng.standard_normal((n, k)).astype(np.float32)
+    sigma = 0.7 * math.sqrt(d)
+    Q = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    Xd = torch.from_numpy(X).cuda()
+    K.krr_kernel_matvec(h, Xd, Xd, sigma, 0.0, torch.from_numpy(V).cuda(), Q, "bf16x3")
+    got = Q.cpu().numpy().astype(np.float64)
+    hi, lo = split_points(X, sigma)
+    xs = hi + lo
+    S = hi @ hi.T + lo @ hi.T + hi @ lo.T
+    nh = np.sum(xs * xs, axis=1)
+    Kt = np.exp2(S - 0.5 * nh[:, None] - 0.5 * nh[None, :])
+    V64 = V.astype(np.float64)
+    scale = Kt @ np.abs(V64)
+    exact = O.gaussian_kernel(X, X, sigma) @ V64
+    if k < 3:
+        assert np.all(np.abs(got - Kt @ V64) <= 1e-5 * scale), np.max(np.abs(got - Kt @ V64) / scale)
+        # 16-bit points: the kernel moves by about 2^-16 of -log2 K
+        assert np.all(np.abs(got - exact) <= 2e-4 * scale), np.max(np.abs(got - exact) / scale)
+    else:
+        assert np.all(np.abs(got - exact) <= 2 ** -8 * scale), np.max(np.abs(got - exact) / scale)
 
 
 @pytest.mark.parametrize("n,d,k,shift", [(1000, 37, 1, 0.0), (777, 64, 3, 1e-4), (300, 8, 16, 0.0),
@@ -104,7 +162,7 @@ def test_matvec_bf16_shift(K, h):
     np.testing.assert_allclose((Q1 - Q0).cpu().numpy(), 0.25 * V, rtol=1e-5, atol=1e-5)
 
 
-@pytest.mark.parametrize("cfg,n,s,tol", [(2, 4096, 128, 1e-6), (5, 3000, 256, 1e-6),
+@pytest.mark.parametrize("cfg,n,s,tol", [(2, 4096, 128, 1e-6), (5, 3000, 256, 1e-6), (5, 8192, 512, 1e-6),
                                          (1, 2000, 200, 1e-8)])
 def test_pcg_mixed_reaches_tolerance(K, h, cfg, n, s, tol):
     """BF16 inner PCG + refinement with an FP64 residual reaches the FP64 target.
