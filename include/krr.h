@@ -55,8 +55,12 @@ typedef enum {
   KRR_BF16 = 2,        /* tcgen05 BF16 tensor cores, FP32 accumulation      */
   KRR_HP = 3,          /* extended precision for refinement residuals       */
   KRR_MIXED = 4,       /* solver only: BF16 inner PCG + HP refinement       */
-  KRR_BF16X3 = 5       /* tcgen05 BF16 on split points (hi + lo, d <= 64):  */
+  KRR_BF16X3 = 5,      /* tcgen05 BF16 on split points (hi + lo, d <= 64):  */
                        /* hi.hi + lo.hi + hi.lo, about 2^-16 relative dots  */
+  KRR_BF16P = 6        /* KRR_BF16 with the contraction with V on the tensor */
+                       /* cores (exp2 values rounded to BF16, 2^-9 each);    */
+                       /* products only: the entrywise rounding can make    */
+                       /* K + lambda I indefinite, so solvers never use it   */
 } krr_precision;
 
 /* How the preconditioner is applied (Section 3.1). */
@@ -125,7 +129,7 @@ krr_status krr_rff_features(krr_handle* h, const float* X, int n, int d, int ldx
  *   Q[i, :] = sum_j k(xr_i, xc_j) V[j, :] + shift * V[i, :]
  * Xr: nr x d (ldxr), Xc: nc x d (ldxc), FP32.  V: nc x k (ldv), Q: nr x k
  * (ldq).  V and Q are double for KRR_FP64 and KRR_HP and float for KRR_FP32,
- * KRR_BF16 and KRR_BF16X3.  `shift` (lambda of Eq. (1)) needs nr == nc and is added
+ * KRR_BF16, KRR_BF16X3 and KRR_BF16P.  `shift` (lambda of Eq. (1)) needs nr == nc and is added
  * only when it is nonzero; pass Xr == Xc for the training system.
  * 1 <= k <= KRR_MAX_RHS.
  */

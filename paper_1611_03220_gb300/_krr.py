@@ -27,7 +27,8 @@ STATUS = {0: "KRR_OK", 1: "KRR_EINVAL", 2: "KRR_ENOMEM", 3: "KRR_ECUDA", 4: "KRR
           9: "KRR_EUNSUPPORTED"}
 KRR_OK, KRR_EINVAL, KRR_ENOMEM, KRR_ECUDA, KRR_ECHOL = 0, 1, 2, 3, 4
 KRR_ENOTCONV, KRR_EBREAKDOWN, KRR_ENAN, KRR_ETIMEOUT, KRR_EUNSUPPORTED = 5, 6, 7, 8, 9
-PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2, "hp": 3, "mixed": 4, "bf16x3": 5}
+PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2, "hp": 3, "mixed": 4, "bf16x3": 5,
+             "bf16p": 6}
 APPLY_FORM = {"zl": 0, "u": 1}
 
 

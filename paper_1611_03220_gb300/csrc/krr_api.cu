@@ -178,11 +178,19 @@ void matvec_dispatch(krr_handle* h, cudaStream_t st, const float* Xr, int nr, in
     return;
   }
   switch (prec) {
-    case KRR_FP64:
-    case KRR_HP: {
+    case KRR_FP64: {
       double* part = wsT<double>(h, "mv_part64", mv_fp64_part_elems(nr, nc, k));
       launch_mv_fp64(st, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, shift, (const double*)V, k, ldv,
                      (double*)Q, ldq, part);
+      return;
+    }
+    case KRR_HP: {
+      // distinct row and column sets, or d > 64: the SIMT float-float product
+      double* part = wsT<double>(h, "hpw_part", mv_hpw_part_elems(nr, nc, k));
+      float* nrm_r = wsT<float>(h, "hpw_nr", 2 * (size_t)nr);
+      float* nrm_c = wsT<float>(h, "hpw_nc", 2 * (size_t)nc);
+      launch_mv_hpw(st, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, shift, (const double*)V, k, ldv,
+                    (double*)Q, ldq, part, nrm_r, nrm_c, 0);
       return;
     }
     case KRR_FP32: {
@@ -194,9 +202,10 @@ void matvec_dispatch(krr_handle* h, cudaStream_t st, const float* Xr, int nr, in
       return;
     }
     case KRR_BF16:
-    case KRR_BF16X3: {
+    case KRR_BF16X3:
+    case KRR_BF16P: {
       tc_matvec(h->tc, st, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, shift, (const float*)V, k, ldv,
-                (float*)Q, ldq, prec == KRR_BF16X3 ? 1 : 0);
+                (float*)Q, ldq, prec == KRR_BF16X3 ? 1 : 0, prec == KRR_BF16P ? 1 : 0);
       return;
     }
     default:
@@ -212,8 +221,13 @@ void matvec_reserve(krr_handle* h, int n, int k, int prec) {
       wsT<double>(h, "mv_part64", mv_fp64_part_elems(n, n, k));
       return;
     case KRR_HP:
-      wsT<double>(h, "mv_part64", mv_fp64_part_elems(n, n, k));
-      if (h->hp.ready) hp_reserve(h->hp, h->stream, k);
+      if (h->hp.ready) {
+        hp_reserve(h->hp, h->stream, k);
+      } else {
+        wsT<double>(h, "hpw_part", mv_hpw_part_elems(n, n, k));
+        wsT<float>(h, "hpw_nr", 2 * (size_t)n);
+        wsT<float>(h, "hpw_nc", 2 * (size_t)n);
+      }
       return;
     case KRR_FP32:
       wsT<float>(h, "mv_part32", mv_fp32_part_elems(n, n, k));
@@ -222,7 +236,8 @@ void matvec_reserve(krr_handle* h, int n, int k, int prec) {
       return;
     case KRR_BF16:
     case KRR_BF16X3:
-      tc_reserve(h->tc, h->stream, k);
+    case KRR_BF16P:
+      tc_reserve(h->tc, h->stream, k, prec == KRR_BF16P ? 1 : 0);
       return;
     default:
       return;
@@ -820,12 +835,20 @@ krr_status solve_impl(krr_handle* h, const float* Xd, int n, int d, int ldx, dou
   return status;
 }
 
-// (D o K)(Xr, Xc) V in FP64 (direct differences).
+// (D o K)(Xr, Xc) V: FP64 (direct differences) or HP (float-float SIMT).
 void dsigma_dispatch(krr_handle* h, cudaStream_t st, const float* Xr, int nr, int ldxr,
                      const float* Xc, int nc, int ldxc, int d, double sigma, const double* V,
-                     int k, int ldv, double* Q, int ldq) {
-  double* part = wsT<double>(h, "mv_part64", mv_fp64_part_elems(nr, nc, k));
-  launch_mv_fp64(st, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, 0.0, V, k, ldv, Q, ldq, part, 1);
+                     int k, int ldv, double* Q, int ldq, int prec) {
+  if (prec == KRR_FP64) {
+    double* part = wsT<double>(h, "mv_part64", mv_fp64_part_elems(nr, nc, k));
+    launch_mv_fp64(st, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, 0.0, V, k, ldv, Q, ldq, part, 1);
+    return;
+  }
+  double* part = wsT<double>(h, "hpw_part", mv_hpw_part_elems(nr, nc, k));
+  float* nrm_r = wsT<float>(h, "hpw_nr", 2 * (size_t)nr);
+  float* nrm_c = wsT<float>(h, "hpw_nc", 2 * (size_t)nc);
+  launch_mv_hpw(st, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, 0.0, V, k, ldv, Q, ldq, part, nrm_r,
+                nrm_c, 1);
 }
 
 // sum_{i, c} A[i, c] B[i, c] read back to the host.
@@ -1387,11 +1410,12 @@ krr_status krr_kernel_matvec(krr_handle* h, const float* Xr, int nr, int ldxr, c
     KRR_REQUIRE(sigma > 0.0 && std::isfinite(sigma), "kernel_matvec: sigma must be > 0");
     KRR_REQUIRE(shift == 0.0 || nr == nc, "kernel_matvec: shift needs a square product");
     KRR_REQUIRE(precision == KRR_FP64 || precision == KRR_FP32 || precision == KRR_BF16 ||
-                    precision == KRR_HP || precision == KRR_BF16X3,
+                    precision == KRR_HP || precision == KRR_BF16X3 || precision == KRR_BF16P,
                 "kernel_matvec: bad precision");
     matvec_dispatch(h, h->stream, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, shift, V, k, ldv, Q, ldq,
                     precision);
-    if (((precision == KRR_BF16 || precision == KRR_BF16X3) && tc_error(h->tc, h->stream)) ||
+    if (((precision == KRR_BF16 || precision == KRR_BF16X3 || precision == KRR_BF16P) &&
+         tc_error(h->tc, h->stream)) ||
         (precision == KRR_HP && hp_error(h->hp, h->stream)))
       throw Error{KRR_ETIMEOUT, "tensor-core product: a pipeline wait hit its limit"};
     return KRR_OK;
@@ -1628,8 +1652,10 @@ krr_status krr_kernel_dsigma_matvec(krr_handle* h, const float* Xr, int nr, int 
     KRR_REQUIRE(ldxr >= d && ldxc >= d && ldv >= k && ldq >= k,
                 "kernel_dsigma_matvec: leading dimension too small");
     KRR_REQUIRE(sigma > 0.0 && std::isfinite(sigma), "kernel_dsigma_matvec: sigma must be > 0");
-    KRR_REQUIRE(precision == KRR_FP64, "kernel_dsigma_matvec: precision must be KRR_FP64");
-    dsigma_dispatch(h, h->stream, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, V, k, ldv, Q, ldq);
+    KRR_REQUIRE(precision == KRR_FP64 || precision == KRR_HP,
+                "kernel_dsigma_matvec: precision must be KRR_FP64 or KRR_HP");
+    dsigma_dispatch(h, h->stream, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, V, k, ldv, Q, ldq,
+                    precision);
     return KRR_OK;
   });
 }
@@ -1673,14 +1699,14 @@ krr_status krr_hypergrad(krr_handle* h, const float* X, int n, int d, int ldx, c
     double* t_te = wsT<double>(h, "hg_tte", mk);
     // gbar = K(X, Xte) g_f: the held-out gradient pulled back to the training points
     matvec_dispatch(h, st, Xd, n, ldx, Xted, m, ldxte, d, sigma, 0.0, Gd, k, ldg, gbar, k,
-                    KRR_FP64);
+                    KRR_HP);
     // adjoint system (K + lambda I) w = gbar, the same operator as Eq. (1)
     int matvecs = 1;
     krr_status status = solve_impl(h, Xd, n, d, ldx, sigma, lambda, Wd, bd, s, gbar, k, k, wadj,
                                    k, o, rep, &matvecs, h->ev[1]);
     // (D_te o K_te) c and (D o K) c, then the three contractions
-    dsigma_dispatch(h, st, Xted, m, ldxte, Xd, n, ldx, d, sigma, Cd, k, ldc, t_te, k);
-    dsigma_dispatch(h, st, Xd, n, ldx, Xd, n, ldx, d, sigma, Cd, k, ldc, t_tr, k);
+    dsigma_dispatch(h, st, Xted, m, ldxte, Xd, n, ldx, d, sigma, Cd, k, ldc, t_te, k, KRR_HP);
+    dsigma_dispatch(h, st, Xd, n, ldx, Xd, n, ldx, d, sigma, Cd, k, ldc, t_tr, k, KRR_HP);
     matvecs += 2;
     const double w_c = host_dot(h, wadj, k, Cd, ldc, n, k);
     const double g_t = host_dot(h, Gd, ldg, t_te, k, m, k);

@@ -110,6 +110,13 @@ void launch_mv_fp64(cudaStream_t st, const float* Xr, int nr, int ldxr, const fl
 void launch_mv_fp64_capped(cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
                            int nc, int ldxc, int d, double sigma, double shift, const double* V,
                            int k, int ldv, double* Q, int ldq, double* part, size_t cap);
+// High-precision SIMT product for any d (krr_matvec_hpw.cu): float-float
+// norm-expansion distances and exp2; part: mv_hpw_part_elems doubles,
+// nrm_r / nrm_c: 2 nr / 2 nc floats.  dsigma = 1 gives (D o K) V (no shift).
+size_t mv_hpw_part_elems(int nr, int nc, int k);
+void launch_mv_hpw(cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc, int nc,
+                   int ldxc, int d, double sigma, double shift, const double* V, int k, int ldv,
+                   double* Q, int ldq, double* part, float* nrm_r, float* nrm_c, int dsigma);
 size_t mv_fp32_part_elems(int nr, int nc, int k);
 void launch_mv_fp32(cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
                     int nc, int ldxc, int d, double sigma, double shift, const float* V,

@@ -40,6 +40,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "krr_ff.cuh"
 #include "krr_internal.cuh"
 #include "krr_tc.cuh"
 #include "krr_tc_ptx.cuh"
@@ -49,13 +50,15 @@ namespace krr {
 namespace {
 
 using namespace ptx;
+using ff::exp2_ff;
+using ff::NTAB;
+using ff::two_sum;
 
 constexpr int BM = 128;
 constexpr int BN = 64;
 constexpr int KP = 64;                 // padded coordinates (d <= 64)
 constexpr int NSL = 5;                 // slices
 constexpr int NLEV = 4;                // accumulators: L0, L1, L2, L3 + 2^-9 L4
-constexpr int NTAB = 256;              // exp2 table entries
 constexpr int NUM_EPI = 8;
 constexpr int THREADS = 32 * (2 + NUM_EPI);
 constexpr int TMEM_COLS = 512;         // 2 buffers x 4 levels x 64 columns
@@ -80,11 +83,6 @@ constexpr int ns_of() {
   return KV >= 16 ? 2 : 3;
 }
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
 
 template <int KV, int CW>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -319,34 +317,8 @@ hp_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             const float lo = te + ue + dl + al + cd.y;
             float xh = u + lo;
             float xl = lo - (xh - u);
-            if (xh < -125.f) {
-              xh = -125.f;
-              xl = 0.f;
-            }
-            // 2^x = 2^(k/256) * e^(r ln 2), k = rint(256 x), r = (xh - k/256) + xl
-            // kept as an exact float pair so that y = r ln 2 has a tiny low part
-            const float kf = rintf(xh * 256.f);
-            float rh, rl;
-            two_sum(fmaf(kf, -0.00390625f, xh), xl, rh, rl);
-            const float yh = rh * 0.693147182464599609375f;
-            float yl = fmaf(rh, 0.693147182464599609375f, -yh);
-            yl = fmaf(rh, -1.904654299957768e-09f, yl);  // ln 2 - float(ln 2)
-            yl = fmaf(rl, 0.693147182464599609375f, yl);
-            // e^yh = 1 + yh + pp (degree-4 Taylor), then times (1 + yl)
-            float pp = fmaf(yh, 0.041666666666666667f, 0.16666666666666667f);
-            pp = fmaf(yh, pp, 0.5f);
-            pp = pp * yh * yh;
-            const float eh = 1.f + yh;
-            const float e0 = ((1.f - eh) + yh) + pp;
-            const float el = fmaf(yl, eh + e0, e0);
-            const int k = (int)kf;
-            const float2 tv = *reinterpret_cast<const float2*>(tab + 2 * (k & (NTAB - 1)));
-            const float kh0 = eh * tv.x;
-            float kl0 = fmaf(eh, tv.x, -kh0);
-            kl0 = fmaf(eh, tv.y, kl0);
-            kl0 = fmaf(el, tv.x, kl0);
-            const float s2 = __int_as_float((127 + (k >> 8)) << 23);
-            const float kh = kh0 * s2, kl = kl0 * s2;
+            float kh, kl;
+            exp2_ff(xh, xl, tab, kh, kl);
             // q += K_ij v_j in float-float
 #pragma unroll
             for (int c = 0; c < KV; ++c) {

@@ -33,9 +33,9 @@
 //              thread keeps CH independent accumulator chains per RHS.
 // Work items are (row tile, column chunk) pairs dealt round-robin; each item
 // writes one partial row sum per chunk, and a second kernel adds the chunks
-// in FP64, applies ra_i and the shift.  This kernel serves k <= 2 right-hand
-// sides; from k = 3 on, tc_matvec2_kernel (below) contracts on the tensor
-// cores instead of the FMA pipe.  Every mbarrier wait is bounded: on
+// in FP64, applies ra_i and the shift.  This kernel is the solvers' BF16
+// product for every k; tc_matvec2_kernel (below) contracts on the tensor
+// cores instead, for explicit products only (KRR_BF16P).  Every mbarrier wait is bounded: on
 // expiry the kernel raises an error flag, drains its own copies and MMAs,
 // frees TMEM and returns.
 #include <cuda.h>
@@ -401,7 +401,7 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 }
 
 // ------------------------------------------------------ two-GEMM variant --
-// For k >= 4 right-hand sides the per-entry FMAs against w dominate the
+// For many right-hand sides the per-entry FMAs against w dominate the
 // epilogue above.  This variant contracts on the tensor cores instead:
 //   S = xh_rows . xh_cols^T   GEMM 1 (M=128, N=128), double-buffered in TMEM
 //   P = bf16(exp2(S))          epilogue (MUFU), stored to shared memory in the
@@ -410,8 +410,12 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 // D (128 x 16 FP32 in TMEM) accumulates over the item's column tiles and the
 // epilogue writes it as the item's partial row sums.  P carries one more
 // BF16 rounding of each kernel entry and Vt one of each weight (2^-9
-// relative each), the same order as the point rounding that the outer
-// refinement removes.
+// relative each).  Unlike the rounding of the points, which leaves a
+// Gaussian kernel of nearby points (positive semi-definite), rounding each
+// entry perturbs K by about 2^-9 of its entries with independent signs, a
+// matrix whose norm grows like sqrt(n) times the typical entry: when K has
+// large entries throughout and lambda is small this makes K + lambda I
+// indefinite, so the solvers do not use this variant.
 //   warp 0  TMA: row tile (resident when d <= 64), column-tile K-blocks, the
 //           tile's Vt block (two 64-column boxes).
 //   warp 1  MMA: GEMM 1 of tile t, then GEMM 2 of tile t-1 (P of tile t-1 is
@@ -930,10 +934,14 @@ void launch_kernel(cudaStream_t st, const CUtensorMap& a, const CUtensorMap& b,
 }
 
 void dispatch(int kv, cudaStream_t st, const TcOperand& op, const TcParams& p, int grid) {
-  if (kv == 1)
-    launch_kernel<1>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid);
-  else
-    launch_kernel<2>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid);
+  switch (kv) {
+    case 1: launch_kernel<1>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid); break;
+    case 2: launch_kernel<2>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid); break;
+    case 4: launch_kernel<4>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid); break;
+    case 8: launch_kernel<8>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid); break;
+    case 12: launch_kernel<12>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid); break;
+    default: launch_kernel<16>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid); break;
+  }
 }
 
 size_t smem2_bytes(int a_res, int ns, int x3) {
@@ -1000,14 +1008,11 @@ struct Plan {
   int kv, n_rt, n_ct, cpc, nchunk;
 };
 
-// Right-hand-side counts from which the two-GEMM variant is used.
-constexpr int KV_GEMM2 = 4;
-
-Plan plan_for(const TcOperand& op, int k) {
+Plan plan_for(const TcOperand& op, int k, int gemm2) {
   Plan pl;
   pl.kv = kv_bucket(k);
   pl.n_rt = op.n_pad / BM;
-  pl.n_ct = op.n_pad / (pl.kv >= KV_GEMM2 ? BN2 : BN);
+  pl.n_ct = op.n_pad / (gemm2 ? BN2 : BN);
   const int req = choose_nchunk(pl.n_rt, pl.n_ct, sm_count());
   pl.cpc = (pl.n_ct + req - 1) / req;
   pl.nchunk = (pl.n_ct + pl.cpc - 1) / pl.cpc;
@@ -1057,12 +1062,12 @@ void tc_prepare_split(TcState& t, cudaStream_t st, const float* X, int n, int ld
   t.split_ready = true;
 }
 
-void tc_reserve(TcState& t, cudaStream_t st, int k) {
+void tc_reserve(TcState& t, cudaStream_t st, int k, int gemm2) {
   if (!t.ready) throw Error{KRR_EINVAL, "tensor-core product used before tc_prepare"};
-  const Plan pl = plan_for(t.cols, k);
+  const Plan pl = plan_for(t.cols, k, gemm2);
   ensure(t.w, (size_t)t.cols.n_pad * pl.kv * 4);
   ensure(t.part, (size_t)pl.nchunk * t.cols.n_pad * pl.kv * 4);
-  if (pl.kv >= KV_GEMM2 && t.vt.bytes < (size_t)N2 * t.cols.n_pad * 2) {
+  if (gemm2 && t.vt.bytes < (size_t)N2 * t.cols.n_pad * 2) {
     ensure(t.vt, (size_t)N2 * t.cols.n_pad * 2);
     make_vt_map(&t.map_v, t.vt.p, t.cols.n_pad);
   }
@@ -1078,21 +1083,21 @@ void tc_clear_error(TcState& t, cudaStream_t st) {
 
 void tc_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
                int nc, int ldxc, int d, double sigma, double shift, const float* V, int k,
-               int ldv, float* Q, int ldq, int split) {
+               int ldv, float* Q, int ldq, int split, int gemm2) {
   const bool same = (Xr == Xc && nr == nc && ldxr == ldxc);
   if (!same) throw Error{KRR_EUNSUPPORTED, "BF16 product supports the training system (Xr == Xc)"};
   if (split)
     tc_prepare_split(t, st, Xc, nc, ldxc, d, sigma);
   else
     tc_prepare(t, st, Xc, nc, ldxc, d, sigma);
-  tc_reserve(t, st, k);
+  tc_reserve(t, st, k, gemm2);
   TcOperand& op = split ? t.split : t.cols;
-  const Plan pl = plan_for(op, k);
+  const Plan pl = plan_for(op, k, gemm2);
   // split points: the row tile's hi and lo stay resident, each column tile
   // streams its hi and lo slices as two stages
   const int nkb = split ? 2 : op.kp / BK;
   const int a_res = (split || nkb == 1) ? 1 : 0;
-  if (pl.kv >= KV_GEMM2) {
+  if (gemm2) {
     make_vt_kernel<<<std::min(8 * sm_count(), (int)(((size_t)N2 * op.n_pad + 255) / 256)), 256,
                      0, st>>>(V, nc, k, ldv, (const float*)op.ra.p, op.n_pad,
                               (__nv_bfloat16*)t.vt.p);

@@ -67,13 +67,15 @@ void tc_prepare(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int
 void tc_prepare_split(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int d,
                       double sigma);
 // Q = K(X, X) V + shift V through the tensor cores (Xr must equal Xc); with
-// `split` the dot products use split points (hi.hi + lo.hi + hi.lo).
+// `split` the dot products use split points (hi.hi + lo.hi + hi.lo); with
+// `gemm2` the contraction with V runs on the tensor cores on BF16-rounded
+// kernel entries.
 void tc_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
                int nc, int ldxc, int d, double sigma, double shift, const float* V, int k,
-               int ldv, float* Q, int ldq, int split = 0);
+               int ldv, float* Q, int ldq, int split = 0, int gemm2 = 0);
 // Allocate the product's workspace for k right-hand sides (call before a
 // graph capture; tc_prepare must have run).
-void tc_reserve(TcState& t, cudaStream_t st, int k);
+void tc_reserve(TcState& t, cudaStream_t st, int k, int gemm2 = 0);
 // Reset the error flag (enqueued on st).
 void tc_clear_error(TcState& t, cudaStream_t st);
 // Nonzero if any launch hit a bounded-wait limit since the state was created.

@@ -56,7 +56,7 @@ def rounded_points(X, sigma):
 
 
 @pytest.mark.parametrize("n,d,k", [(1000, 37, 1), (777, 64, 3), (1300, 100, 10), (300, 8, 16),
-                                   (2000, 784, 10), (520, 64, 2)])
+                                   (520, 64, 2)])
 def test_matvec_bf16_matches_rounded_oracle(K, h, n, d, k):
     rng = np.random.default_rng(n + d + k)
     X = rng.standard_normal((n, d)).astype(np.float32)
@@ -71,24 +71,38 @@ def test_matvec_bf16_matches_rounded_oracle(K, h, n, d, k):
     ref = Kh @ V.astype(np.float64)
     scale = Kh @ np.abs(V.astype(np.float64))
     got = Q.cpu().numpy().astype(np.float64)
-    if k < 3:
-        # FP32 exponentials contracted in FP32
-        assert np.all(np.abs(got - ref) <= 1e-5 * scale), np.max(np.abs(got - ref) / scale)
-    else:
-        # two-GEMM variant: P = bf16(exp2(xh_i.xh_j)) and Vt = bf16(ra_j v_j) on the
-        # tensor cores; emulate both roundings in FP64 (round to nearest even)
-        S = Xh @ Xh.T
-        P = bf16_round(np.exp2(S))
-        ra = np.exp2(-0.5 * np.sum(Xh * Xh, axis=1)).astype(np.float32).astype(np.float64)
-        Vt = bf16_round((ra[:, None] * V.astype(np.float64)).astype(np.float32))
-        emul = ra[:, None] * (P @ Vt)
-        assert np.all(np.abs(got - emul) <= 1e-3 * scale), np.max(np.abs(got - emul) / scale)
-        # each term carries two BF16 roundings of at most 2^-9 relative
-        assert np.all(np.abs(got - ref) <= 2 ** -8 * scale), np.max(np.abs(got - ref) / scale)
+    # FP32 exponentials contracted in FP32
+    assert np.all(np.abs(got - ref) <= 1e-5 * scale), np.max(np.abs(got - ref) / scale)
     # and against the exact kernel of the unrounded points: the BF16 rounding of x
     # moves -||x_i - x_j||^2/(2 sigma^2) by about 2^-8 of its size
     exact = O.gaussian_kernel(X, X, sigma) @ V.astype(np.float64)
     assert np.all(np.abs(got - exact) <= 3e-2 * scale)
+
+
+@pytest.mark.parametrize("n,d,k", [(777, 64, 3), (300, 8, 16), (2000, 784, 10), (400, 64, 1)])
+def test_matvec_bf16p_matches_emulated_roundings(K, h, n, d, k):
+    """Two-GEMM variant: P = bf16(exp2(xh_i.xh_j)) and Vt = bf16(ra_j v_j) on the
+    tensor cores; both roundings emulated in FP64 (round to nearest even)."""
+    rng = np.random.default_rng(n + d + k + 3)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    V = rng.standard_normal((n, k)).astype(np.float32)
+    sigma = math.sqrt(d)
+    Q = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    Xd = torch.from_numpy(X).cuda()
+    K.krr_kernel_matvec(h, Xd, Xd, sigma, 0.0, torch.from_numpy(V).cuda(), Q, "bf16p")
+    got = Q.cpu().numpy().astype(np.float64)
+    Xh = rounded_points(X, sigma)
+    S = Xh @ Xh.T
+    P = bf16_round(np.exp2(S))
+    ra = np.exp2(-0.5 * np.sum(Xh * Xh, axis=1)).astype(np.float32).astype(np.float64)
+    Vt = bf16_round((ra[:, None] * V.astype(np.float64)).astype(np.float32))
+    emul = ra[:, None] * (P @ Vt)
+    Kh = O.gaussian_kernel(Xh, Xh, 1.0 / math.sqrt(math.log(2.0)))
+    scale = Kh @ np.abs(V.astype(np.float64))
+    assert np.all(np.abs(got - emul) <= 1e-3 * scale), np.max(np.abs(got - emul) / scale)
+    # each term carries two BF16 roundings of at most 2^-9 relative
+    ref = Kh @ V.astype(np.float64)
+    assert np.all(np.abs(got - ref) <= 2 ** -8 * scale), np.max(np.abs(got - ref) / scale)
 
 
 def split_points(X, sigma):
@@ -103,8 +117,7 @@ def split_points(X, sigma):
 @pytest.mark.parametrize("n,d,k", [(1000, 37, 1), (600, 64, 2), (777, 54, 4), (300, 8, 16)])
 def test_matvec_bf16x3_matches_split_oracle(K, h, n, d, k):
     """Split points xh = hi + lo: S = hi.hi + lo.hi + hi.lo on the tensor cores
-    (lo.lo dropped), norms of hi + lo.  Emulated in FP64; k >= 3 adds the BF16
-    rounding of exp2(S) and of the weights (two-GEMM variant)."""
+    (lo.lo dropped), norms of hi + lo.  Emulated in FP64."""
     rng = np.random.default_rng(n + d + k + 7)
     X = (rng.standard_normal((n, d)) * np.linspace(0.5, 2.0, d)).astype(np.float32)
     V = rng.standard_normal((n, k)).astype(np.float32)
@@ -121,12 +134,9 @@ def test_matvec_bf16x3_matches_split_oracle(K, h, n, d, k):
     V64 = V.astype(np.float64)
     scale = Kt @ np.abs(V64)
     exact = O.gaussian_kernel(X, X, sigma) @ V64
-    if k < 3:
-        assert np.all(np.abs(got - Kt @ V64) <= 1e-5 * scale), np.max(np.abs(got - Kt @ V64) / scale)
-        # 16-bit points: the kernel moves by about 2^-16 of -log2 K
-        assert np.all(np.abs(got - exact) <= 2e-4 * scale), np.max(np.abs(got - exact) / scale)
-    else:
-        assert np.all(np.abs(got - exact) <= 2 ** -8 * scale), np.max(np.abs(got - exact) / scale)
+    assert np.all(np.abs(got - Kt @ V64) <= 1e-5 * scale), np.max(np.abs(got - Kt @ V64) / scale)
+    # 16-bit points: the kernel moves by about 2^-16 of -log2 K
+    assert np.all(np.abs(got - exact) <= 2e-4 * scale), np.max(np.abs(got - exact) / scale)
 
 
 @pytest.mark.parametrize("n,d,k,shift", [(1000, 37, 1, 0.0), (777, 64, 3, 1e-4), (300, 8, 16, 0.0),
@@ -147,6 +157,41 @@ def test_matvec_hp_matches_oracle(K, h, n, d, k, shift):
     scale = O.kernel_matvec_blocked(X, X, np.abs(V), sigma) + shift * np.abs(V)
     err = np.abs(Q.cpu().numpy() - ref)
     assert np.all(err <= 2e-12 * scale), float(np.max(err / scale))
+
+
+@pytest.mark.parametrize("nr,nc,d,k,shift", [(700, 700, 100, 1, 1e-3), (257, 1030, 54, 3, 0.0),
+                                               (500, 500, 784, 10, 0.0), (130, 65, 7, 16, 0.0)])
+def test_matvec_hp_simt_matches_oracle(K, h, nr, nc, d, k, shift):
+    """HP product for any d and for distinct row and column sets: float-float
+    norm-expansion distances of the FP32 inputs, float-float exp2 and sums."""
+    rng = np.random.default_rng(nr + nc + d + k)
+    Xc = (rng.random((nc, d)) * (rng.random((nc, d)) < 0.3)).astype(np.float32) if d == 784 \
+        else (rng.standard_normal((nc, d)) * 1.5 + 0.5).astype(np.float32)
+    Xr = Xc[:nr].copy() if nr == nc else (rng.standard_normal((nr, d)) + 0.5).astype(np.float32)
+    V = rng.standard_normal((nc, k))
+    sigma = 0.9 * math.sqrt(d) if d != 784 else 8.0
+    Xcd = torch.from_numpy(Xc).cuda()
+    Xrd = Xcd if nr == nc else torch.from_numpy(Xr).cuda()
+    Q = torch.empty((nr, k), dtype=torch.float64, device="cuda")
+    K.krr_kernel_matvec(h, Xrd, Xcd, sigma, shift, torch.from_numpy(V).cuda(), Q, "hp")
+    Kx = O.gaussian_kernel(Xr, Xc, sigma)
+    ref = Kx @ V + (shift * V if shift else 0.0)
+    scale = Kx @ np.abs(V) + (shift * np.abs(V) if shift else 0.0)
+    err = np.abs(Q.cpu().numpy() - ref)
+    assert np.all(err <= 2e-12 * scale), float(np.max(err / scale))
+
+
+def test_dsigma_hp_matches_oracle(K, h):
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((400, 54)).astype(np.float32)
+    V = rng.standard_normal((400, 2))
+    sigma = 4.0
+    Xd = torch.from_numpy(X).cuda()
+    Q = torch.empty((400, 2), dtype=torch.float64, device="cuda")
+    K.krr_kernel_dsigma_matvec(h, Xd, Xd, sigma, torch.from_numpy(V).cuda(), Q, precision="hp")
+    G = O.kernel_dlogsigma(X, X, sigma)
+    err = np.abs(Q.cpu().numpy() - G @ V)
+    assert np.all(err <= 2e-12 * (G @ np.abs(V))), float(np.max(err / (G @ np.abs(V))))
 
 
 def test_matvec_bf16_shift(K, h):
