@@ -60,6 +60,9 @@ def parse():
                     help="short run for ncu: 'step' = one mixed and one FP32 solve of "
                          "--profile-iters PCG iterations with the host-driven loop (every "
                          "launch listed); otherwise 3 launches of that kernel product / apply")
+    ap.add_argument("--workload", type=int, default=None, choices=[3, 4, 5],
+                    help="solve one other workload at full size (mixed, tol 1e-6) and print "
+                         "one JSON line of its results instead of the bench line")
     ap.add_argument("--profile-iters", type=int, default=12)
     ap.add_argument("--profile-k", type=int, default=1,
                     help="right-hand sides of the --profile bf16/hp/fp32 products")
@@ -214,6 +217,66 @@ def run_profile(args):
             K.krr_kernel_matvec(h, X, X, P.sigma, P.lam, V, Q, args.profile)
     torch.cuda.synchronize()
     h.close()
+
+
+# ---------------------------------------------------------- workloads ---
+def run_workload(args):
+    """Full-size solves of the multi-RHS (3), uneven-batch (4) and gradient (5)
+    workloads: wall time, iterations and the solver's residual certificate."""
+    import torch
+    from paper_1611_03220_gb300 import build
+    build()
+    from paper_1611_03220_gb300 import _krr as K
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    h = K.Handle()
+    opts = K.default_opts(tol=1e-6, precision="mixed", max_iter=60000, max_outer=60)
+    out = {"workload": args.workload, "precision": "mixed", "tol": 1e-6}
+    if args.workload == 4:
+        probs = ks.make_uneven()
+        items, cs = [], []
+        for P in probs:
+            Cc = torch.zeros((P.n, 1), dtype=torch.float64, device="cuda")
+            cs.append(Cc)
+            items.append((dev(P.X), P.sigma, P.lam, dev(P.W), dev(P.b), dev(P.Y), Cc))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = K.krr_pcg_solve_batched(h, items, opts, check=False)
+        torch.cuda.synchronize()
+        out.update({"s": time.perf_counter() - t0, "ms_setup": reps[0]["ms_setup"],
+                    "problems": len(probs),
+                    "converged": sum(r["status_code"] == K.KRR_OK for r in reps),
+                    "max_iters": max(r["iters"][0] for r in reps),
+                    "max_rel_res": max(r["rel_res"][0] for r in reps),
+                    "sum_n2": float(sum(P.n ** 2 for P in probs))})
+    else:
+        P = ks.make_config(args.workload)
+        Cc = torch.zeros((P.n, P.k), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = K.krr_pcg_solve(h, dev(P.X), P.sigma, P.lam, dev(P.W), dev(P.b), dev(P.Y), Cc, opts,
+                            check=False)
+        torch.cuda.synchronize()
+        out.update({"n": P.n, "d": P.d, "k": P.k, "s": P.s, "solve_s": time.perf_counter() - t0,
+                    "status": r["status"], "iters": r["iters"], "outer_steps": r["outer_steps"],
+                    "ms_setup": r["ms_setup"], "rel_res": max(r["rel_res"])})
+        if args.workload == 5:
+            # the held-out loss gradient: adjoint solve and (D o K) products
+            m = P.Xte.shape[0]
+            F = torch.empty((m, 1), dtype=torch.float64, device="cuda")
+            K.krr_predict(h, dev(P.X), dev(P.Xte), P.sigma, Cc, F, "hp")
+            GF = (2.0 / m) * (F - dev(P.Yte))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            (gs, gl), rg = K.krr_hypergrad(h, dev(P.X), dev(P.Xte), P.sigma, P.lam, dev(P.W),
+                                           dev(P.b), Cc, GF, opts, check=False)
+            torch.cuda.synchronize()
+            out.update({"grad_s": time.perf_counter() - t0, "dlogsigma": gs, "dloglambda": gl,
+                        "adjoint_status": rg["status"], "adjoint_iters": rg["iters"]})
+    h.close()
+    print(json.dumps(out))
 
 
 # ----------------------------------------------------------------- ours ---
@@ -408,6 +471,9 @@ def main():
         return
     if args.profile:
         run_profile(args)
+        return
+    if args.workload:
+        run_workload(args)
         return
     run_ours(args, rank, world, local)
 

@@ -565,6 +565,11 @@ int next_level(int level, int d) {
   return INNER_HP;
 }
 
+// Largest contraction per outer step that keeps the inner arithmetic at its
+// level: a split-level solve costs several BF16 steps, and when it contracts
+// poorly the system is so ill-conditioned that only HP inner solves converge.
+double keep_below(int level) { return level == INNER_BF16 ? 0.5 : 0.2; }
+
 // Relative tolerance of an inner solve: the BF16 solve stops at inner_tol;
 // the more accurate ones go as far as the outer test needs (0.5 tol / rel)
 // within what their arithmetic can reach.
@@ -685,7 +690,7 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
           break;
         }
         level = next_level(level, a.d);
-      } else if (now > 0.5 * rel_prev && level != INNER_HP) {
+      } else if (now > keep_below(level) * rel_prev && level != INNER_HP) {
         level = next_level(level, a.d);
       }
     }
@@ -1200,7 +1205,7 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
             continue;
           }
           it.level = next_level(it.level, it.d);
-        } else if (now > 0.5 * it.rel_prev && it.level != INNER_HP) {
+        } else if (now > keep_below(it.level) * it.rel_prev && it.level != INNER_HP) {
           it.level = next_level(it.level, it.d);
         }
       }

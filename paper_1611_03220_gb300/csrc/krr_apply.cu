@@ -86,28 +86,15 @@ zt_kernel(const void* __restrict__ Zs, int n, int s, const T* __restrict__ R, in
     __syncthreads();
     if (n_ok > 0) {
       const int nrow = min(ZT_ROWS, r1 - base);
-      // G rows' loads are issued before any of them is consumed (fewer when
-      // many right-hand sides already keep the registers busy)
-      constexpr int G = KV <= 2 ? 8 : (KV <= 4 ? 4 : 2);
-      for (int rr0 = 0; rr0 < nrow; rr0 += G) {
-        float z[G][8];
+#pragma unroll 4
+      for (int rr = 0; rr < nrow; ++rr) {
+        float z[8];
+        load8<BF16>(Zs, (size_t)(base + rr) * s + col0, n_ok, vec != 0, z);
 #pragma unroll
-        for (int u = 0; u < G; ++u) {
-          if (rr0 + u < nrow) {
-            load8<BF16>(Zs, (size_t)(base + rr0 + u) * s + col0, n_ok, vec != 0, z[u]);
-          } else {
+        for (int c = 0; c < KV; ++c) {
+          const ACC rv = rs[rr][c];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) z[u][q] = 0.f;
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < G; ++u) {
-#pragma unroll
-          for (int c = 0; c < KV; ++c) {
-            const ACC rv = rs[rr0 + u][c];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) acc[q][c] = fma((ACC)z[u][q], rv, acc[q][c]);
-          }
+          for (int q = 0; q < 8; ++q) acc[q][c] = fma((ACC)z[q], rv, acc[q][c]);
         }
       }
     }
@@ -160,19 +147,8 @@ trmv_kernel(const double* __restrict__ A, int s, const double* __restrict__ x, i
 #pragma unroll
   for (int c = 0; c < KV; ++c) acc[c] = 0.0;
   const double* row = A + (size_t)a * s;
-  // eight independent loads per lane per step
-  int b = lo + lane;
-  for (; b + 7 * 32 < hi; b += 8 * 32) {
-    double av[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) av[u] = __ldg(row + b + u * 32);
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-#pragma unroll
-      for (int c = 0; c < KV; ++c)
-        if (c < k) acc[c] = fma(av[u], __ldg(x + (size_t)(b + u * 32) * k + c), acc[c]);
-  }
-  for (; b < hi; b += 32) {
+#pragma unroll 4
+  for (int b = lo + lane; b < hi; b += 32) {
     const double av = __ldg(row + b);
 #pragma unroll
     for (int c = 0; c < KV; ++c)
@@ -216,42 +192,20 @@ zw_kernel(const void* __restrict__ Zs, int n, int s, const double* __restrict__ 
       wsm[c * sch + b] = (c < k && b < nb) ? (ACC)w[(size_t)(b0 + b) * k + c] : (ACC)0;
     }
     __syncthreads();
-    // US steps of 256 columns for all four rows: 4 US independent loads per
-    // lane before any is consumed
-    constexpr int US = KV <= 2 ? 2 : 1;
-    for (int bb0 = lane * 8; bb0 < nb; bb0 += US * 256) {
-      float z[ZW_ROWS_PER_WARP][US][8];
 #pragma unroll
-      for (int r = 0; r < ZW_ROWS_PER_WARP; ++r) {
-        const int i = row0 + r;
-#pragma unroll
-        for (int u = 0; u < US; ++u) {
-          const int bb = bb0 + u * 256;
-          if (i < n && bb < nb) {
-            load8<BF16>(Zs, (size_t)i * s + b0 + bb, min(8, nb - bb), vec != 0, z[r][u]);
-          } else {
-#pragma unroll
-            for (int q = 0; q < 8; ++q) z[r][u][q] = 0.f;
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < US; ++u) {
-        const int bb = bb0 + u * 256;
-        if (bb >= nb) break;
+    for (int r = 0; r < ZW_ROWS_PER_WARP; ++r) {
+      const int i = row0 + r;
+      if (i >= n) break;
+      for (int bb = lane * 8; bb < nb; bb += 256) {
+        float z[8];
+        load8<BF16>(Zs, (size_t)i * s + b0 + bb, min(8, nb - bb), vec != 0, z);
 #pragma unroll
         for (int c = 0; c < KV; ++c) {
           const ACC* wc = wsm + c * sch + bb;
-          ACC wv[8];
+          ACC a = acc[r][c];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) wv[q] = wc[q];
-#pragma unroll
-          for (int r = 0; r < ZW_ROWS_PER_WARP; ++r) {
-            ACC a = acc[r][c];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) a = fma((ACC)z[r][u][q], wv[q], a);
-            acc[r][c] = a;
-          }
+          for (int q = 0; q < 8; ++q) a = fma((ACC)z[q], wc[q], a);
+          acc[r][c] = a;
         }
       }
     }
