@@ -429,12 +429,23 @@ void precond_setup_impl(krr_handle* h, const float* Z, int n, int s, int ldz, do
     ensure_buf(pc.U, (size_t)s * n * sizeof(float));
     launch_form_u(st, (const double*)pc.Linv.p, pc.Z.p, z_bf16, n, s, (float*)pc.U.p);
   }
+  if (!pc.err.p) ensure_buf(pc.err, 16);
+  KRR_CUDA(cudaMemsetAsync(pc.err.p, 0, 16, st));
   pc.n = n;
   pc.s = s;
   pc.form = form;
   pc.z_bf16 = z_bf16;
   pc.lam_p = lambda_p;
   pc.ready = true;
+}
+
+// Nonzero if a streamed apply hit its bounded wait since the set-up.
+int precond_error(krr_handle* h) {
+  if (!h->pc.err.p) return 0;
+  int e = 0;
+  KRR_CUDA(cudaMemcpyAsync(&e, h->pc.err.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  KRR_CUDA(cudaStreamSynchronize(h->stream));
+  return e;
 }
 
 template <typename T>
@@ -837,6 +848,7 @@ krr_status solve_impl(krr_handle* h, const float* Xd, int n, int d, int ldx, dou
     status = solve_mixed(h, a, rep, matvecs);
   if (o.precision == KRR_MIXED && (tc_error(h->tc, st) || hp_error(h->hp, st)))
     status = KRR_ETIMEOUT;
+  if (o.precond && precond_error(h)) status = KRR_ETIMEOUT;
   return status;
 }
 
@@ -1290,7 +1302,7 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
     const size_t nk = (size_t)it.n * it.k;
     double* Cd = wsT<double>(g, "v_cd", nk);
     launch_convert<double, double>(g->stream, Cd, it.n, it.k, it.k, it.C, it.ldc, one);
-    if (tc_error(g->tc, g->stream) || hp_error(g->hp, g->stream)) {
+    if (tc_error(g->tc, g->stream) || hp_error(g->hp, g->stream) || precond_error(g)) {
       it.status = KRR_ETIMEOUT;
     }
   }
@@ -1368,6 +1380,7 @@ krr_status krr_destroy(krr_handle* h) {
   free_buf(h->pc.Linv);
   free_buf(h->pc.LinvT);
   free_buf(h->pc.U);
+  free_buf(h->pc.err);
   for (krr_handle* sub : h->subs) krr_destroy(sub);
   h->subs.clear();
   tc_release(h->tc);

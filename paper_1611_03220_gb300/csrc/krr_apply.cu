@@ -11,6 +11,7 @@
 //                               shared memory
 // Both GEMVs stream Z once with 16-byte loads (8 BF16 or 4 FP32 values), so
 // the apply is bound by HBM: about 2 n s b_Z bytes per application.
+#include <algorithm>
 #include <type_traits>
 
 #include "krr_internal.cuh"
@@ -217,11 +218,255 @@ zw_kernel(const void* __restrict__ Zs, int n, int s, const double* __restrict__ 
 #pragma unroll
     for (int c = 0; c < KV; ++c) {
       if (c >= k) break;
-      double v = (double)acc[r][c];
+      ACC v = acc[r][c];
       for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
       if (lane == 0)
-        Zo[(size_t)i * ldo + c] = (T)(((double)R[(size_t)i * ldr + c] - v) * inv_lam);
+        Zo[(size_t)i * ldo + c] = (T)(((double)R[(size_t)i * ldr + c] - (double)v) * inv_lam);
     }
+  }
+}
+
+// --------------------------------------------------- streamed GEMVs -------
+// The same two GEMVs with Z streamed through shared memory by bulk copies
+// (cp.async.bulk into a ring of 64 KiB stages, completion on mbarriers), so
+// the bytes in flight per SM no longer depend on registers or occupancy.
+// One persistent CTA per SM walks a contiguous range of rows.  Used when the
+// rows' byte offsets are 16-byte aligned.
+constexpr int SBYTES = 64 * 1024;   // bytes per stage
+constexpr int NSTG = 3;             // stages
+constexpr uint32_t APPLY_WAIT = 1u << 24;
+
+__device__ __forceinline__ bool stg_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t it = 0; it < APPLY_WAIT; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ uint32_t sh_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Issue the copies of stage `st` (rows [row0, row0 + nrow), columns
+// [c0, c0 + seg)) and return; thread 0 only.
+__device__ __forceinline__ void stg_issue(uint8_t* ring, uint64_t* full, int st, const uint8_t* Z,
+                                          size_t row_bytes, size_t c0_bytes, uint32_t seg_bytes,
+                                          int row0, int nrow) {
+  const uint32_t bar = sh_u32(&full[st]);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+               "r"(seg_bytes * (uint32_t)nrow)
+               : "memory");
+  for (int rr = 0; rr < nrow; ++rr) {
+    const uint8_t* src = Z + (size_t)(row0 + rr) * row_bytes + c0_bytes;
+    const uint32_t dst = sh_u32(ring + (size_t)st * SBYTES + (size_t)rr * seg_bytes);
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+        "[%3];" ::"r"(dst),
+        "l"((uint64_t)src), "r"(seg_bytes), "r"(bar)
+        : "memory");
+  }
+}
+
+// part[cta, col, c] = sum over the CTA's rows of Z[i, col] R[i, c]; thread t
+// owns columns c0 + 8t .. c0 + 8t + 7 of the column block blockIdx.x.
+template <int BF16, typename T, typename ACC, int KV>
+__global__ void __launch_bounds__(AT, 1)
+zt_stream_kernel(const void* __restrict__ Zs, int n, int s, const T* __restrict__ R, int ldr,
+                 int k, ACC* __restrict__ part, int* err) {
+  extern __shared__ __align__(128) uint8_t ring[];
+  __shared__ __align__(8) uint64_t full[NSTG];
+  constexpr int ES = BF16 ? 2 : 4;
+  const int cb = blockIdx.x;
+  const int c0 = cb * AT * 8;
+  const int seg = min(AT * 8, s - c0);                 // columns in this block (multiple of 8)
+  const uint32_t seg_bytes = (uint32_t)seg * ES;
+  const int rps = SBYTES / (int)seg_bytes;             // rows per stage
+  const int rows_per_cta = (n + gridDim.y - 1) / gridDim.y;
+  const int r0 = blockIdx.y * rows_per_cta, r1 = min(n, r0 + rows_per_cta);
+  const int nstage = r0 < r1 ? (r1 - r0 + rps - 1) / rps : 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NSTG; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sh_u32(&full[i])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int g = 0; g < NSTG && g < nstage; ++g)
+      stg_issue(ring, full, g, (const uint8_t*)Zs, (size_t)s * ES, (size_t)c0 * ES, seg_bytes,
+                r0 + g * rps, min(rps, r1 - r0 - g * rps));
+  }
+  // the CTA's rows of R, staged once (the per-row loads would each expose
+  // a memory round trip)
+  ACC* rsm = reinterpret_cast<ACC*>(ring + (size_t)NSTG * SBYTES);
+  for (int e = threadIdx.x; e < (r1 - r0) * KV; e += AT) {
+    const int rr = e / KV, c = e % KV;
+    rsm[e] = (r0 < r1 && c < k) ? (ACC)R[(size_t)(r0 + rr) * ldr + c] : (ACC)0;
+  }
+  __syncthreads();
+  const int col = threadIdx.x * 8;  // within the block
+  const bool mine = col < seg;
+  ACC acc[8][KV];
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+#pragma unroll
+    for (int c = 0; c < KV; ++c) acc[q][c] = (ACC)0;
+  bool ok = true;
+  int g = 0;
+  for (; g < nstage; ++g) {
+    const int st = g % NSTG;
+    const uint32_t parity = (uint32_t)((g / NSTG) & 1);
+    ok = __syncthreads_and(ok && stg_wait(sh_u32(&full[st]), parity));
+    if (!ok) break;
+    const int row0 = r0 + g * rps, nrow = min(rps, r1 - row0);
+    const uint8_t* base = ring + (size_t)st * SBYTES;
+    if (mine) {
+      for (int rr = 0; rr < nrow; ++rr) {
+        float z[8];
+        if (BF16) {
+          const uint4 v = *reinterpret_cast<const uint4*>(base + (size_t)rr * seg_bytes + col * 2);
+          const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 f = __bfloat1622float2(h2[q]);
+            z[2 * q] = f.x;
+            z[2 * q + 1] = f.y;
+          }
+        } else {
+          const float4* p4 = reinterpret_cast<const float4*>(base + (size_t)rr * seg_bytes + col * 4);
+          const float4 a = p4[0], b = p4[1];
+          z[0] = a.x; z[1] = a.y; z[2] = a.z; z[3] = a.w;
+          z[4] = b.x; z[5] = b.y; z[6] = b.z; z[7] = b.w;
+        }
+#pragma unroll
+        for (int c = 0; c < KV; ++c) {
+          const ACC rv = rsm[(row0 - r0 + rr) * KV + c];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) acc[q][c] = fma((ACC)z[q], rv, acc[q][c]);
+        }
+      }
+    }
+    __syncthreads();  // every thread is done with the stage
+    if (threadIdx.x == 0 && g + NSTG < nstage)
+      stg_issue(ring, full, st, (const uint8_t*)Zs, (size_t)s * ES, (size_t)c0 * ES, seg_bytes,
+                r0 + (g + NSTG) * rps, min(rps, r1 - r0 - (g + NSTG) * rps));
+  }
+  if (!ok) {
+    // stages g .. g + NSTG - 1 may still have copies in flight: let them land
+    if (threadIdx.x == 0) {
+      atomicOr(err, 1);
+      for (int gg = g; gg < nstage && gg < g + NSTG; ++gg)
+        stg_wait(sh_u32(&full[gg % NSTG]), (uint32_t)((gg / NSTG) & 1));
+    }
+    return;
+  }
+  if (!mine) return;
+  ACC* out = part + (size_t)blockIdx.y * s * KV;
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+#pragma unroll
+    for (int c = 0; c < KV; ++c) out[(size_t)(c0 + col + q) * KV + c] = acc[q][c];
+}
+
+// Zo[i, c] = (R[i, c] - sum_b Z[i, b] w[b, c]) / lambda_p with whole rows of Z
+// streamed; w (s x KV) in shared memory; each warp takes rows of a stage.
+template <int BF16, typename T, typename ACC, int KV>
+__global__ void __launch_bounds__(AT, 1)
+zw_stream_kernel(const void* __restrict__ Zs, int n, int s, const double* __restrict__ w, int k,
+                 const T* __restrict__ R, int ldr, double inv_lam, T* __restrict__ Zo, int ldo,
+                 int* err) {
+  extern __shared__ __align__(128) uint8_t ring[];
+  __shared__ __align__(8) uint64_t full[NSTG];
+  constexpr int ES = BF16 ? 2 : 4;
+  ACC* wsm = reinterpret_cast<ACC*>(ring + (size_t)NSTG * SBYTES);  // [c][b]
+  const uint32_t row_bytes = (uint32_t)s * ES;
+  const int rps = SBYTES / (int)row_bytes;
+  const int rows_per_cta = (n + gridDim.x - 1) / gridDim.x;
+  const int r0 = blockIdx.x * rows_per_cta, r1 = min(n, r0 + rows_per_cta);
+  const int nstage = r0 < r1 ? (r1 - r0 + rps - 1) / rps : 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NSTG; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sh_u32(&full[i])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int g = 0; g < NSTG && g < nstage; ++g)
+      stg_issue(ring, full, g, (const uint8_t*)Zs, row_bytes, 0, row_bytes, r0 + g * rps,
+                min(rps, r1 - r0 - g * rps));
+  }
+  for (int e = threadIdx.x; e < s * KV; e += AT) {
+    const int b = e / KV, c = e % KV;
+    wsm[c * s + b] = c < k ? (ACC)w[(size_t)b * k + c] : (ACC)0;
+  }
+  // the CTA's rows of R, staged once (a per-row load after the reduction
+  // would expose a memory round trip per row)
+  double* rsm = reinterpret_cast<double*>(wsm + (size_t)s * KV);
+  for (int e = threadIdx.x; e < (r1 - r0) * KV; e += AT) {
+    const int rr = e / KV, c = e % KV;
+    rsm[e] = (r0 < r1 && c < k) ? (double)R[(size_t)(r0 + rr) * ldr + c] : 0.0;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  bool ok = true;
+  int g = 0;
+  for (; g < nstage; ++g) {
+    const int st = g % NSTG;
+    const uint32_t parity = (uint32_t)((g / NSTG) & 1);
+    ok = __syncthreads_and(ok && stg_wait(sh_u32(&full[st]), parity));
+    if (!ok) break;
+    const int row0 = r0 + g * rps, nrow = min(rps, r1 - row0);
+    const uint8_t* base = ring + (size_t)st * SBYTES;
+    for (int rr = warp; rr < nrow; rr += AT / 32) {
+      ACC acc[KV];
+#pragma unroll
+      for (int c = 0; c < KV; ++c) acc[c] = (ACC)0;
+      for (int b0 = lane * 8; b0 < s; b0 += 256) {
+        float z[8];
+        if (BF16) {
+          const uint4 v = *reinterpret_cast<const uint4*>(base + (size_t)rr * row_bytes + b0 * 2);
+          const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 f = __bfloat1622float2(h2[q]);
+            z[2 * q] = f.x;
+            z[2 * q + 1] = f.y;
+          }
+        } else {
+          const float4* p4 = reinterpret_cast<const float4*>(base + (size_t)rr * row_bytes + b0 * 4);
+          const float4 a = p4[0], bb = p4[1];
+          z[0] = a.x; z[1] = a.y; z[2] = a.z; z[3] = a.w;
+          z[4] = bb.x; z[5] = bb.y; z[6] = bb.z; z[7] = bb.w;
+        }
+#pragma unroll
+        for (int c = 0; c < KV; ++c) {
+          const ACC* wc = wsm + c * s + b0;
+          ACC a = acc[c];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) a = fma((ACC)z[q], wc[q], a);
+          acc[c] = a;
+        }
+      }
+      const int i = row0 + rr;
+#pragma unroll
+      for (int c = 0; c < KV; ++c) {
+        if (c >= k) break;
+        // reduce in the accumulator type (FP64 adds are slow on this GPU)
+        ACC v = acc[c];
+        for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) Zo[(size_t)i * ldo + c] = (T)((rsm[(i - r0) * KV + c] - (double)v) * inv_lam);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && g + NSTG < nstage)
+      stg_issue(ring, full, st, (const uint8_t*)Zs, row_bytes, 0, row_bytes,
+                r0 + (g + NSTG) * rps, min(rps, r1 - r0 - (g + NSTG) * rps));
+  }
+  if (!ok && threadIdx.x == 0) {
+    atomicOr(err, 1);
+    for (int gg = g; gg < nstage && gg < g + NSTG; ++gg)
+      stg_wait(sh_u32(&full[gg % NSTG]), (uint32_t)((gg / NSTG) & 1));
   }
 }
 
@@ -302,17 +547,47 @@ void apply_zl(cudaStream_t st, const Precond& pc, const ApplyPlan& pl, const T* 
               T* Zo, int ldo, double* t1, double* t2, void* part) {
   const int n = pc.n, s = pc.s;
   const int vec = (s % 8 == 0) ? 1 : 0;
-  zt_kernel<BF16, T, ACC, KV><<<dim3(pl.colblocks, pl.nchunk), AT, 0, st>>>(
-      pc.Z.p, n, s, R, ldr, k, reinterpret_cast<ACC*>(part), pl.rpc, vec);
+  int* err = reinterpret_cast<int*>(pc.err.p);
+  // streamed GEMVs: rows 16-byte aligned; zw also needs w beside the ring
+  const size_t w_bytes = (size_t)s * KV * sizeof(ACC);
+  const size_t ring_bytes = (size_t)NSTG * SBYTES;
+  const int nchunk_s = std::min(pl.nchunk, std::max(1, sm_count() / pl.colblocks));
+  const size_t zt_bytes = ring_bytes + (size_t)((n + nchunk_s - 1) / nchunk_s) * KV * sizeof(ACC);
+  const size_t zw_bytes = ring_bytes + w_bytes +
+                          (size_t)((n + sm_count() - 1) / sm_count()) * KV * sizeof(double);
+  const bool stream = vec && err != nullptr && zt_bytes <= (size_t)220 * 1024;
+  const bool stream_zw = vec && err != nullptr && (size_t)s * (BF16 ? 2 : 4) <= (size_t)SBYTES &&
+                         zw_bytes <= (size_t)220 * 1024;
+  int nchunk = pl.nchunk;
+  if (stream) {
+    nchunk = nchunk_s;
+    auto kz = zt_stream_kernel<BF16, T, ACC, KV>;
+    KRR_CUDA(cudaFuncSetAttribute(kz, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)zt_bytes));
+    kz<<<dim3(pl.colblocks, nchunk), AT, zt_bytes, st>>>(pc.Z.p, n, s, R, ldr, k,
+                                                         reinterpret_cast<ACC*>(part), err);
+  } else {
+    zt_kernel<BF16, T, ACC, KV><<<dim3(pl.colblocks, pl.nchunk), AT, 0, st>>>(
+        pc.Z.p, n, s, R, ldr, k, reinterpret_cast<ACC*>(part), pl.rpc, vec);
+  }
   KRR_CHECK_LAUNCH();
   const int sb = (int)(((size_t)s * KV + 31) / 32);
-  sum_kernel<ACC><<<sb, 256, 0, st>>>(reinterpret_cast<const ACC*>(part), pl.nchunk, s, KV, k, t1);
+  sum_kernel<ACC><<<sb, 256, 0, st>>>(reinterpret_cast<const ACC*>(part), nchunk, s, KV, k, t1);
   KRR_CHECK_LAUNCH();
   const int tb = (s * 32 + AT - 1) / AT;
   trmv_kernel<0, KV><<<tb, AT, 0, st>>>(reinterpret_cast<const double*>(pc.Linv.p), s, t1, k, t2);
   KRR_CHECK_LAUNCH();
   trmv_kernel<1, KV><<<tb, AT, 0, st>>>(reinterpret_cast<const double*>(pc.LinvT.p), s, t2, k, t1);
   KRR_CHECK_LAUNCH();
+  if (stream_zw) {
+    auto kw = zw_stream_kernel<BF16, T, ACC, KV>;
+    KRR_CUDA(cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)zw_bytes));
+    kw<<<sm_count(), AT, zw_bytes, st>>>(pc.Z.p, n, s, t1, k, R, ldr, 1.0 / pc.lam_p, Zo, ldo,
+                                         err);
+    KRR_CHECK_LAUNCH();
+    return;
+  }
   auto kern = zw_kernel<BF16, T, ACC, KV>;
   if (pl.zw_smem > 48 * 1024)
     KRR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -88,6 +88,7 @@ struct Precond {
   DevBuf Linv;   // s x s FP64 lower inverse of L (ZL form)
   DevBuf LinvT;  // s x s FP64, (L^-1)^T, upper (ZL form)
   DevBuf U;      // s x n FP32, U = L^-1 Z^T (U form)
+  DevBuf err;    // device flag: a streamed apply's bounded wait expired
 };
 
 // ------------------------------------------------------ kernel launchers --
