@@ -418,44 +418,74 @@ zw_stream_kernel(const void* __restrict__ Zs, int n, int s, const double* __rest
     if (!ok) break;
     const int row0 = r0 + g * rps, nrow = min(rps, r1 - row0);
     const uint8_t* base = ring + (size_t)st * SBYTES;
-    for (int rr = warp; rr < nrow; rr += AT / 32) {
-      ACC acc[KV];
+    // with BF16 Z each warp takes two rows at a time (one read of w serves
+    // both); FP32 rows are twice as long and fill the registers alone
+    constexpr int RW = BF16 ? 2 : 1;
+    for (int rr = warp; rr < nrow; rr += RW * (AT / 32)) {
+      const int rb = rr + AT / 32;
+      const bool two = RW == 2 && rb < nrow;
+      ACC acc[RW][KV];
 #pragma unroll
-      for (int c = 0; c < KV; ++c) acc[c] = (ACC)0;
+      for (int h = 0; h < RW; ++h)
+#pragma unroll
+        for (int c = 0; c < KV; ++c) acc[h][c] = (ACC)0;
       for (int b0 = lane * 8; b0 < s; b0 += 256) {
-        float z[8];
-        if (BF16) {
-          const uint4 v = *reinterpret_cast<const uint4*>(base + (size_t)rr * row_bytes + b0 * 2);
-          const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&v);
+        float z[RW][8];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float2 f = __bfloat1622float2(h2[q]);
-            z[2 * q] = f.x;
-            z[2 * q + 1] = f.y;
+        for (int h = 0; h < RW; ++h) {
+          const int row = h ? (two ? rb : rr) : rr;
+          if (BF16) {
+            const uint4 v =
+                *reinterpret_cast<const uint4*>(base + (size_t)row * row_bytes + b0 * 2);
+            const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float2 f = __bfloat1622float2(h2[q]);
+              z[h][2 * q] = f.x;
+              z[h][2 * q + 1] = f.y;
+            }
+          } else {
+            const float4* p4 =
+                reinterpret_cast<const float4*>(base + (size_t)row * row_bytes + b0 * 4);
+            const float4 a4 = p4[0], b4 = p4[1];
+            z[h][0] = a4.x; z[h][1] = a4.y; z[h][2] = a4.z; z[h][3] = a4.w;
+            z[h][4] = b4.x; z[h][5] = b4.y; z[h][6] = b4.z; z[h][7] = b4.w;
           }
-        } else {
-          const float4* p4 = reinterpret_cast<const float4*>(base + (size_t)rr * row_bytes + b0 * 4);
-          const float4 a = p4[0], bb = p4[1];
-          z[0] = a.x; z[1] = a.y; z[2] = a.z; z[3] = a.w;
-          z[4] = bb.x; z[5] = bb.y; z[6] = bb.z; z[7] = bb.w;
         }
 #pragma unroll
         for (int c = 0; c < KV; ++c) {
-          const ACC* wc = wsm + c * s + b0;
-          ACC a = acc[c];
+          ACC wv[8];
+          if (sizeof(ACC) == 4) {
+            const float4* w4 = reinterpret_cast<const float4*>(wsm + c * s + b0);
+            const float4 x0 = w4[0], x1 = w4[1];
+            wv[0] = x0.x; wv[1] = x0.y; wv[2] = x0.z; wv[3] = x0.w;
+            wv[4] = x1.x; wv[5] = x1.y; wv[6] = x1.z; wv[7] = x1.w;
+          } else {
 #pragma unroll
-          for (int q = 0; q < 8; ++q) a = fma((ACC)z[q], wc[q], a);
-          acc[c] = a;
+            for (int q = 0; q < 8; ++q) wv[q] = wsm[c * s + b0 + q];
+          }
+#pragma unroll
+          for (int h = 0; h < RW; ++h) {
+            ACC x = acc[h][c];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) x = fma((ACC)z[h][q], wv[q], x);
+            acc[h][c] = x;
+          }
         }
       }
-      const int i = row0 + rr;
 #pragma unroll
-      for (int c = 0; c < KV; ++c) {
-        if (c >= k) break;
-        // reduce in the accumulator type (FP64 adds are slow on this GPU)
-        ACC v = acc[c];
-        for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane == 0) Zo[(size_t)i * ldo + c] = (T)((rsm[(i - r0) * KV + c] - (double)v) * inv_lam);
+      for (int h = 0; h < RW; ++h) {
+        if (h == 1 && !two) break;
+        const int i = row0 + (h ? rb : rr);
+#pragma unroll
+        for (int c = 0; c < KV; ++c) {
+          if (c >= k) break;
+          // reduce in the accumulator type (FP64 adds are slow on this GPU)
+          ACC v = acc[h][c];
+          for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+          if (lane == 0)
+            Zo[(size_t)i * ldo + c] = (T)((rsm[(i - r0) * KV + c] - (double)v) * inv_lam);
+        }
       }
     }
     __syncthreads();
