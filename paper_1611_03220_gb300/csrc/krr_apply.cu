@@ -135,32 +135,61 @@ sum_kernel(const P* __restrict__ part, int nchunk, int s, int kv, int k, double*
   }
 }
 
-// y[a, c] = sum_b A[a, b] x[b, c], b <= a (lower) or b >= a (upper); one warp per row.
+// y[a, c] = sum_b A[a, b] x[b, c], b <= a (lower) or b >= a (upper).  A CTA
+// takes two rows; four warps share a row (a quarter of its span each), every
+// lane keeps eight loads in flight, and the quarters are added in order.
+constexpr int TR_ROWS = 2;
+constexpr int TR_SPLIT = (AT / 32) / TR_ROWS;
+
 template <int UPPER, int KV>
 __global__ void __launch_bounds__(AT)
 trmv_kernel(const double* __restrict__ A, int s, const double* __restrict__ x, int k,
             double* __restrict__ y) {
-  const int warp = (blockIdx.x * AT + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= s) return;
-  const int a = warp;
-  const int lo = UPPER ? a : 0, hi = UPPER ? s : a + 1;
-  double acc[KV];
+  __shared__ double red[AT / 32][KV];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int a = blockIdx.x * TR_ROWS + warp / TR_SPLIT;
+  const int q = warp % TR_SPLIT;
+  double acc[2][KV];
 #pragma unroll
-  for (int c = 0; c < KV; ++c) acc[c] = 0.0;
-  const double* row = A + (size_t)a * s;
-#pragma unroll 4
-  for (int b = lo + lane; b < hi; b += 32) {
-    const double av = __ldg(row + b);
+  for (int c = 0; c < KV; ++c) acc[0][c] = acc[1][c] = 0.0;
+  if (a < s) {
+    const int lo = UPPER ? a : 0, hi = UPPER ? s : a + 1;
+    const int per = (hi - lo + TR_SPLIT - 1) / TR_SPLIT;
+    const int qlo = lo + q * per, qhi = min(hi, qlo + per);
+    const double* row = A + (size_t)a * s;
+    int b = qlo + lane;
+    for (; b + 7 * 32 < qhi; b += 8 * 32) {
+      double av[8];
 #pragma unroll
-    for (int c = 0; c < KV; ++c)
-      if (c < k) acc[c] = fma(av, __ldg(x + (size_t)b * k + c), acc[c]);
+      for (int u = 0; u < 8; ++u) av[u] = __ldg(row + b + 32 * u);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int c = 0; c < KV; ++c)
+          if (c < k) acc[u & 1][c] = fma(av[u], __ldg(x + (size_t)(b + 32 * u) * k + c), acc[u & 1][c]);
+    }
+    for (; b < qhi; b += 32) {
+      const double av = __ldg(row + b);
+#pragma unroll
+      for (int c = 0; c < KV; ++c)
+        if (c < k) acc[0][c] = fma(av, __ldg(x + (size_t)b * k + c), acc[0][c]);
+    }
   }
 #pragma unroll
   for (int c = 0; c < KV; ++c) {
-    if (c >= k) break;
-    double v = acc[c];
+    double v = acc[0][c] + acc[1][c];
     for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) y[(size_t)a * k + c] = v;
+    if (lane == 0) red[warp][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < TR_ROWS * KV) {
+    const int r = threadIdx.x / KV, c = threadIdx.x % KV;
+    const int row = blockIdx.x * TR_ROWS + r;
+    if (row < s && c < k) {
+      double v = 0.0;
+      for (int w = 0; w < TR_SPLIT; ++w) v += red[r * TR_SPLIT + w][c];
+      y[(size_t)row * k + c] = v;
+    }
   }
 }
 
@@ -604,7 +633,7 @@ void apply_zl(cudaStream_t st, const Precond& pc, const ApplyPlan& pl, const T* 
   const int sb = (int)(((size_t)s * KV + 31) / 32);
   sum_kernel<ACC><<<sb, 256, 0, st>>>(reinterpret_cast<const ACC*>(part), nchunk, s, KV, k, t1);
   KRR_CHECK_LAUNCH();
-  const int tb = (s * 32 + AT - 1) / AT;
+  const int tb = (s + TR_ROWS - 1) / TR_ROWS;
   trmv_kernel<0, KV><<<tb, AT, 0, st>>>(reinterpret_cast<const double*>(pc.Linv.p), s, t1, k, t2);
   KRR_CHECK_LAUNCH();
   trmv_kernel<1, KV><<<tb, AT, 0, st>>>(reinterpret_cast<const double*>(pc.LinvT.p), s, t2, k, t1);
