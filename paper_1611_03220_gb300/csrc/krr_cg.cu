@@ -26,7 +26,9 @@ int cg_blocks(int n) {
 }
 
 // Sum v[c] over the grid.  Returns true in thread 0 of the last CTA to
-// finish, with tot[c] the column totals added in CTA order.
+// finish, with tot[c] the column totals.  The last CTA adds the per-CTA
+// partials with all its threads (thread t takes CTAs t, t + CT, ...) and a
+// fixed tree, so the result does not depend on the order the CTAs finish in.
 __device__ bool grid_colsum(double (&v)[KRR_MAX_RHS], int k, double* part,
                             unsigned int* counter, double (&tot)[KRR_MAX_RHS]) {
   __shared__ double red[NW][KRR_MAX_RHS];
@@ -51,14 +53,28 @@ __device__ bool grid_colsum(double (&v)[KRR_MAX_RHS], int k, double* part,
   __syncthreads();
   if (!last) return false;
   __threadfence();
-  if (threadIdx.x < k) {
-    double s = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&part[b * KRR_MAX_RHS + threadIdx.x]);
-    red[0][threadIdx.x] = s;
+  double loc[KRR_MAX_RHS];
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c) loc[c] = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += CT) {
+#pragma unroll
+    for (int c = 0; c < KRR_MAX_RHS; ++c)
+      if (c < k) loc[c] += __ldcg(&part[b * KRR_MAX_RHS + c]);
+  }
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c) {
+    if (c >= k) break;
+    double x = loc[c];
+    for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if (lane == 0) red[w][c] = x;
   }
   __syncthreads();
   if (threadIdx.x != 0) return false;
-  for (int c = 0; c < k; ++c) tot[c] = red[0][c];
+  for (int c = 0; c < k; ++c) {
+    double t = 0.0;
+    for (int q = 0; q < NW; ++q) t += red[q][c];
+    tot[c] = t;
+  }
   *counter = 0u;
   return true;
 }
