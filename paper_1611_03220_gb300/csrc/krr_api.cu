@@ -700,7 +700,9 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
           status = KRR_ENOTCONV;
           break;
         }
-        level = next_level(level, a.d);
+        // a correction that made things worse means the system is far too
+        // ill-conditioned for FP32-accurate kernel entries: straight to HP
+        level = INNER_HP;
       } else if (now > keep_below(level) * rel_prev && level != INNER_HP) {
         level = next_level(level, a.d);
       }
@@ -1216,7 +1218,8 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
             it.done = true;
             continue;
           }
-          it.level = next_level(it.level, it.d);
+          // worse, not just slow: straight to HP (see solve_mixed)
+          it.level = INNER_HP;
         } else if (now > keep_below(it.level) * it.rel_prev && it.level != INNER_HP) {
           it.level = next_level(it.level, it.d);
         }
