@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=None, help="override n (smaller instance)")
+    ap.add_argument("--points", "--n", dest="n", type=int, default=None,
+                    help="override n (smaller instance)")
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--profile", default=None, choices=["step", "bf16", "hp", "fp32", "apply"],
@@ -72,6 +73,37 @@ def parse():
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(value: float, world: int, device="cpu") -> float:
+    """The largest `value` over the ranks of the initialised process group."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def bench_config(P, n: int, world: int) -> dict:
+    """The `config` object of the bench line (both arms)."""
+    return {"workload": WORKLOAD, "n": n, "d": P.d, "s": P.s, "sigma": P.sigma,
+            "lambda": P.lam, "tol": P.tol, "m_predict": M_TEST,
+            "l2": "flushed between steps (512 MiB write)",
+            "parallelism": "replicas" if world > 1 else "single-gpu"}
+
+
+def blas_threads() -> int:
+    """Threads the oracle's BLAS calls use (threadpoolctl when present)."""
+    try:
+        from threadpoolctl import threadpool_info
+        n = sum(i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas")
+        if n > 0:
+            return n
+    except Exception:
+        pass
+    return int(os.environ.get("OMP_NUM_THREADS", "0")) or (os.cpu_count() or 1)
 
 
 # ----------------------------------------------------------------- clocks --
@@ -138,7 +170,7 @@ def oracle_sample(P, rows: int, reps: int = 1) -> tuple[float, int]:
         t0 = time.perf_counter()
         O.kernel_matvec_blocked(P.X[:rows], P.X, V, P.sigma)
         best = min(best, time.perf_counter() - t0)
-    return best, os.cpu_count() or 1
+    return best, blas_threads()
 
 
 def cpu_baseline(P, matvecs: int, rows: int = 4096) -> dict:
@@ -151,15 +183,19 @@ def cpu_baseline(P, matvecs: int, rows: int = 4096) -> dict:
                        f"{matvecs} kernel products of the GPU solve")}
 
 
+# Kernel products of one Algorithm 1 solve of the bench workload to 1e-6 as the GPU run
+# counts them (its report's matvecs: about 4,370 PCG iterations + 7 refinement residuals).
+REF_MATVECS = 4376
+
+
 def run_reference(args, rank, world):
+    """The oracle, timed on the host cores (rank 0 only; other ranks exit at once)."""
     if rank != 0:
         return
     n = args.n or ks.CONFIGS[2]
-    P = ks.make_config(2, n=n)
-    rows = 1024
-    # kernel products of one Algorithm 1 solve of this workload to 1e-6, as the GPU run
-    # counts them (report field solve.matvecs: 4340 PCG iterations + 7 refinement residuals)
-    matvecs = 4347
+    P = ks.make_config(2, n=n, m=M_TEST)
+    rows = min(1024, n)
+    matvecs = REF_MATVECS
     times = []
     for i in range(args.warmup + args.steps):
         t, cores = oracle_sample(P, rows)
@@ -169,10 +205,10 @@ def run_reference(args, rank, world):
     sample = (f"FP64 oracle kernel product on {rows} of {n} rows per step, scaled to "
               f"{matvecs} full products")
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": 0,
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "n": n},
+        "data": "synthetic", "config": bench_config(P, n, world),
         "cpu_baseline": {"value": v, "unit": "ms", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
@@ -336,11 +372,8 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     launches = K._lib.krr_launch_count() - launches0
     clk = clocks.stop()
-    ms = statistics.mean(times)
+    ms = max_over_ranks(statistics.mean(times), world, dev)
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
         torch.distributed.barrier()
     rep = reps[-1]
 
@@ -441,10 +474,7 @@ def run_ours(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "d": P.d, "s": P.s, "sigma": P.sigma,
-                       "lambda": P.lam, "tol": P.tol, "m_predict": M_TEST,
-                       "l2": "flushed between steps (512 MiB write)",
-                       "parallelism": "replicas" if world > 1 else "single-gpu"},
+            "config": bench_config(P, n, world),
             "solve": {"status": rep["status"], "iters": rep["iters"][0],
                       "outer_steps": rep["outer_steps"], "matvecs": rep["matvecs"],
                       "rel_res_fp64": rep["rel_res"][0], "ms_setup": rep["ms_setup"],
