@@ -42,9 +42,10 @@ WORKLOAD = ("gaussian-mixture n=65536 d=64 (10 centres N(0,4I), unit spread), si
             "lambda=1e-4, s=2048 RFF, tol 1e-6, predict m=8192")
 M_TEST = 8192
 L2_FLUSH_BYTES = 512 << 20
-# DRAM bytes (read + write) of one tc_matvec_kernel<1> launch at n = 65536, d = 64, from the
-# ncu capture summarised in profiles/tc_matvec_kernel_n65536_d64.md
-TC_DRAM_BYTES_N65536 = 8679680
+# DRAM bytes (read + write) of one tc_matvec_kernel<1> launch on FP16 points at n = 65536,
+# d = 64, from the ncu capture summarised in profiles/tc_matvec_kernel_n65536_d64.md (None
+# until the current kernel has been captured)
+TC_DRAM_BYTES_N65536 = None
 
 
 def parse():
@@ -57,7 +58,8 @@ def parse():
                     help="override n (smaller instance)")
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--profile", default=None, choices=["step", "bf16", "hp", "fp32", "apply"],
+    ap.add_argument("--profile", default=None,
+                    choices=["step", "bf16", "fp16", "hp", "fp32", "apply"],
                     help="short run for ncu: 'step' = one mixed and one FP32 solve of "
                          "--profile-iters PCG iterations with the host-driven loop (every "
                          "launch listed); otherwise 3 launches of that kernel product / apply")
@@ -66,7 +68,7 @@ def parse():
                          "one JSON line of its results instead of the bench line")
     ap.add_argument("--profile-iters", type=int, default=12)
     ap.add_argument("--profile-k", type=int, default=1,
-                    help="right-hand sides of the --profile bf16/hp/fp32 products")
+                    help="right-hand sides of the --profile bf16/fp16/hp/fp32 products")
     return ap.parse_args()
 
 
@@ -184,8 +186,8 @@ def cpu_baseline(P, matvecs: int, rows: int = 4096) -> dict:
 
 
 # Kernel products of one Algorithm 1 solve of the bench workload to 1e-6 as the GPU run
-# counts them (its report's matvecs: about 4,370 PCG iterations + 7 refinement residuals).
-REF_MATVECS = 4376
+# counts them (its report's matvecs: 2,876 PCG iterations + 4 refinement residuals).
+REF_MATVECS = 2880
 
 
 def run_reference(args, rank, world):
@@ -378,16 +380,17 @@ def run_ours(args, rank, world, local):
     rep = reps[-1]
 
     # ------------------------------------------ fused product, timed alone
+    # (the inner solves' product: FP16 points on the tensor cores)
     Vf = torch.randn((n, 1), dtype=torch.float32, device=dev)
     Qf = torch.empty_like(Vf)
     for _ in range(3):
-        K.krr_kernel_matvec(h, X, X, P.sigma, P.lam, Vf, Qf, "bf16")
+        K.krr_kernel_matvec(h, X, X, P.sigma, P.lam, Vf, Qf, "fp16")
     mv_ms = []
     for _ in range(10):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        K.krr_kernel_matvec(h, X, X, P.sigma, P.lam, Vf, Qf, "bf16")
+        K.krr_kernel_matvec(h, X, X, P.sigma, P.lam, Vf, Qf, "fp16")
         e1.record(st)
         e1.synchronize()
         mv_ms.append(e0.elapsed_time(e1))
@@ -409,7 +412,7 @@ def run_ours(args, rank, world, local):
         lanes = 2 ** round(math.log2(ex2_rate / (sms * clk_mhz * 1e6)))
     peak = (lanes or 16) * sms * 2070e6
     achieved = pairs / t_mv
-    # algorithmic bytes of one product: the BF16 points once, w, and the row sums
+    # algorithmic bytes of one product: the FP16 points once, w, and the row sums
     alg_bytes = n_pad * d_pad * 2 + n * 4 + n * 4
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
                 "unit": "Gexp/s", "frac": achieved / peak,
@@ -472,7 +475,7 @@ def run_ours(args, rank, world, local):
         out = {
             "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp16+f64",
             "data": "synthetic",
             "config": bench_config(P, n, world),
             "solve": {"status": rep["status"], "iters": rep["iters"][0],

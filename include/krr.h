@@ -54,13 +54,15 @@ typedef enum {
   KRR_FP32 = 1,        /* FP32 SIMT: the plain single-precision path        */
   KRR_BF16 = 2,        /* tcgen05 BF16 tensor cores, FP32 accumulation      */
   KRR_HP = 3,          /* extended precision for refinement residuals       */
-  KRR_MIXED = 4,       /* solver only: BF16 inner PCG + HP refinement       */
+  KRR_MIXED = 4,       /* solver only: FP16/BF16 inner PCG + HP refinement  */
   KRR_BF16X3 = 5,      /* tcgen05 BF16 on split points (hi + lo, d <= 64):  */
                        /* hi.hi + lo.hi + hi.lo, about 2^-16 relative dots  */
-  KRR_BF16P = 6        /* KRR_BF16 with the contraction with V on the tensor */
+  KRR_BF16P = 6,       /* KRR_BF16 with the contraction with V on the tensor */
                        /* cores (exp2 values rounded to BF16, 2^-9 each);    */
                        /* products only: the entrywise rounding can make    */
                        /* K + lambda I indefinite, so solvers never use it   */
+  KRR_FP16 = 7         /* KRR_BF16 on FP16-rounded points: same tensor rate, */
+                       /* 2^-12 instead of 2^-9 relative point rounding     */
 } krr_precision;
 
 /* How the preconditioner is applied (Section 3.1). */
@@ -79,10 +81,12 @@ typedef struct {
   int precision;       /* krr_precision; KRR_MIXED adds refinement           */
   int apply_form;      /* krr_apply_form                                     */
   int use_graph;       /* 1: PCG loop as a CUDA-graph while node             */
-  double inner_tol;    /* KRR_MIXED: inner PCG relative tolerance            */
+  double inner_tol;    /* KRR_MIXED: inner PCG relative tolerance (0.03)     */
   int max_outer;       /* KRR_MIXED: refinement step cap                     */
   int z_bf16;          /* store Z in BF16 (-1 auto: BF16 for BF16/MIXED)     */
   int warm_start;      /* 1: C holds x0 on entry                             */
+  int inner_precision; /* KRR_MIXED: product of the inner PCG, KRR_FP16 or   */
+                       /* KRR_BF16 (0: the default, KRR_FP16)                */
 } krr_opts;
 
 typedef struct {
@@ -113,6 +117,22 @@ const char* krr_last_error(const krr_handle* h);
 const char* krr_status_string(krr_status s);
 
 /*
+ * Tile-plan autotuning of the tensor-core product (KRR_BF16, KRR_FP16,
+ * KRR_BF16X3; the paper has no counterpart, its kernel products are library
+ * calls).  With on = 1 the first product of each shape (row tiles, column
+ * tiles, K-blocks, RHS bucket, operand format) on this handle times the
+ * candidate plans -- column chunks per row tile x TMA ring stages -- on
+ * scratch right-hand sides and keeps the fastest for the rest of the
+ * process; the first product of a shape therefore synchronises the stream.
+ * Solves time their shapes before they capture a graph.  Off (0) by
+ * default: the plan then follows a fixed wave-balance rule, and results do
+ * not depend on timing.  Batched solves pass the setting to their problems.
+ * `shapes` (may be NULL) receives the number of shapes tuned so far in this
+ * process.  Errors: KRR_EINVAL for a NULL handle.
+ */
+krr_status krr_set_autotune(krr_handle* h, int on, int* shapes);
+
+/*
  * Random Fourier features, Section 2.2:
  *   Z[i, j] = sqrt(2/s) * cos(sum_t X[i, t] W[t, j] + b[j]).
  * X: n x d (ldx), W: d x s (lds = s), b: s, Z: n x s output (ldz), all FP32.
@@ -129,7 +149,8 @@ krr_status krr_rff_features(krr_handle* h, const float* X, int n, int d, int ldx
  *   Q[i, :] = sum_j k(xr_i, xc_j) V[j, :] + shift * V[i, :]
  * Xr: nr x d (ldxr), Xc: nc x d (ldxc), FP32.  V: nc x k (ldv), Q: nr x k
  * (ldq).  V and Q are double for KRR_FP64 and KRR_HP and float for KRR_FP32,
- * KRR_BF16, KRR_BF16X3 and KRR_BF16P.  `shift` (lambda of Eq. (1)) needs nr == nc and is added
+ * KRR_BF16, KRR_FP16, KRR_BF16X3 and KRR_BF16P.  `shift` (lambda of Eq. (1))
+ * needs nr == nc and is added
  * only when it is nonzero; pass Xr == Xc for the training system.
  * 1 <= k <= KRR_MAX_RHS.
  */
@@ -166,8 +187,9 @@ krr_status krr_precond_apply(krr_handle* h, const double* R, int k, int ldr,
  * stopping when ||y - (K + lambda I) c|| <= tol ||y|| for every column
  * (Section 5).  X: n x d (ldx) FP32; W: d x s FP32; b: s FP32;
  * Y, C: n x k double (ldy, ldc).  X, W, b, Y and C may be host or device
- * pointers.  With opts->precision == KRR_MIXED the inner PCG runs the BF16
- * tensor-core product and an outer refinement loop recomputes the residual
+ * pointers.  With opts->precision == KRR_MIXED the inner PCG runs the
+ * tensor-core product of opts->inner_precision (FP16 points by default, or
+ * BF16) and an outer refinement loop recomputes the residual
  * in KRR_HP arithmetic and FP64 vectors; when a correction contracts the
  * residual by less than a half, later inner solves use KRR_BF16X3 (d <= 64)
  * and then KRR_HP products.  `rep` (may be NULL) receives the

@@ -28,7 +28,7 @@ STATUS = {0: "KRR_OK", 1: "KRR_EINVAL", 2: "KRR_ENOMEM", 3: "KRR_ECUDA", 4: "KRR
 KRR_OK, KRR_EINVAL, KRR_ENOMEM, KRR_ECUDA, KRR_ECHOL = 0, 1, 2, 3, 4
 KRR_ENOTCONV, KRR_EBREAKDOWN, KRR_ENAN, KRR_ETIMEOUT, KRR_EUNSUPPORTED = 5, 6, 7, 8, 9
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2, "hp": 3, "mixed": 4, "bf16x3": 5,
-             "bf16p": 6}
+             "bf16p": 6, "fp16": 7}
 APPLY_FORM = {"zl": 0, "u": 1}
 
 
@@ -36,7 +36,7 @@ class krr_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("lambda_p", C.c_double),
                 ("precond", C.c_int), ("precision", C.c_int), ("apply_form", C.c_int),
                 ("use_graph", C.c_int), ("inner_tol", C.c_double), ("max_outer", C.c_int),
-                ("z_bf16", C.c_int), ("warm_start", C.c_int)]
+                ("z_bf16", C.c_int), ("warm_start", C.c_int), ("inner_precision", C.c_int)]
 
 
 class krr_report(C.Structure):
@@ -68,6 +68,7 @@ _SIGS = {
     "krr_set_stream": (_i, [_vp, _vp]),
     "krr_last_error": (C.c_char_p, [_vp]),
     "krr_status_string": (C.c_char_p, [_i]),
+    "krr_set_autotune": (_i, [_vp, _i, C.POINTER(_i)]),
     "krr_rff_features": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _i, _vp, _i]),
     "krr_kernel_matvec": (_i, [_vp, _vp, _i, _i, _vp, _i, _i, _i, _d, _d, _vp, _i, _i, _vp, _i, _i]),
     "krr_precond_setup": (_i, [_vp, _vp, _i, _i, _i, _d, _i, _i]),
@@ -140,6 +141,12 @@ class Handle:
     def set_stream(self, stream=None):
         self._check(_lib.krr_set_stream(self._h, _stream_ptr(stream)))
 
+    def set_autotune(self, on: bool = True) -> int:
+        """Turn tile-plan autotuning on or off; returns the shapes tuned so far."""
+        n = _i(0)
+        self._check(_lib.krr_set_autotune(self._h, 1 if on else 0, C.byref(n)))
+        return n.value
+
     def _check(self, st: int):
         if st != KRR_OK:
             raise KrrError(st, _lib.krr_last_error(self._h).decode())
@@ -166,7 +173,7 @@ def default_opts(**kw) -> krr_opts:
     o = krr_opts()
     _lib.krr_default_opts(C.byref(o))
     for k, v in kw.items():
-        if k == "precision" and isinstance(v, str):
+        if k in ("precision", "inner_precision") and isinstance(v, str):
             v = PRECISION[v]
         if k == "apply_form" and isinstance(v, str):
             v = APPLY_FORM[v]

@@ -202,10 +202,12 @@ void matvec_dispatch(krr_handle* h, cudaStream_t st, const float* Xr, int nr, in
       return;
     }
     case KRR_BF16:
+    case KRR_FP16:
     case KRR_BF16X3:
     case KRR_BF16P: {
       tc_matvec(h->tc, st, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, shift, (const float*)V, k, ldv,
-                (float*)Q, ldq, prec == KRR_BF16X3 ? 1 : 0, prec == KRR_BF16P ? 1 : 0);
+                (float*)Q, ldq, prec == KRR_BF16X3 ? 1 : 0, prec == KRR_BF16P ? 1 : 0,
+                prec == KRR_FP16 ? 1 : 0);
       return;
     }
     default:
@@ -235,9 +237,11 @@ void matvec_reserve(krr_handle* h, int n, int k, int prec) {
       wsT<float>(h, "mv_nrm_c", (size_t)n);
       return;
     case KRR_BF16:
+    case KRR_FP16:
     case KRR_BF16X3:
     case KRR_BF16P:
-      tc_reserve(h->tc, h->stream, k, prec == KRR_BF16P ? 1 : 0);
+      tc_reserve(h->tc, h->stream, k, prec == KRR_BF16P ? 1 : 0,
+                 prec == KRR_BF16X3 ? 1 : (prec == KRR_FP16 ? 2 : 0));
       return;
     default:
       return;
@@ -568,30 +572,38 @@ krr_status solve_plain(krr_handle* h, const SolveArgs& a, int prec, krr_report* 
 }
 
 // Inner-solve arithmetic of the mixed solve, in the order it is tried: the
-// BF16 product, the split-point BF16 product (d <= 64), the HP product.
-enum InnerLevel { INNER_BF16 = 0, INNER_SPLIT = 1, INNER_HP = 2 };
+// FP16 (or BF16) product, the split-point BF16 product (d <= 64), the HP
+// product.
+enum InnerLevel { INNER_LOW = 0, INNER_SPLIT = 1, INNER_HP = 2 };
 
 int next_level(int level, int d) {
-  if (level == INNER_BF16 && d <= 64) return INNER_SPLIT;
+  if (level == INNER_LOW && d <= 64) return INNER_SPLIT;
   return INNER_HP;
 }
 
 // Largest contraction per outer step that keeps the inner arithmetic at its
-// level: a split-level solve costs several BF16 steps, and when it contracts
+// level: a split-level solve costs several low-level steps, and when it contracts
 // poorly the system is so ill-conditioned that only HP inner solves converge.
-double keep_below(int level) { return level == INNER_BF16 ? 0.5 : 0.2; }
+double keep_below(int level) { return level == INNER_LOW ? 0.5 : 0.2; }
 
-// Relative tolerance of an inner solve: the BF16 solve stops at inner_tol;
-// the more accurate ones go as far as the outer test needs (0.5 tol / rel)
-// within what their arithmetic can reach.
+// Relative tolerance of an inner solve: the FP16/BF16 solve stops at inner_tol,
+// or sooner on the last step if the outer test needs less (0.3 tol / rel:
+// the rest of the margin is for the product's own error); the more accurate
+// ones go as far as the outer test needs (0.5 tol / rel) within what their
+// arithmetic can reach.
 double inner_tol_for(int level, const krr_opts& o, double rel) {
-  if (level == INNER_BF16) return o.inner_tol;
+  if (level == INNER_LOW) return std::max(o.inner_tol, std::min(0.5, 0.3 * o.tol / rel));
   const double want = 0.5 * o.tol / rel;
   return std::min(o.inner_tol, std::max(level == INNER_SPLIT ? 1e-5 : 1e-11, want));
 }
 
+// Product of the lowest inner level: FP16 points unless BF16 was asked for.
+int low_precision(const krr_opts& o) {
+  return o.inner_precision == KRR_BF16 ? KRR_BF16 : KRR_FP16;
+}
+
 const char* level_name(int level) {
-  return level == INNER_BF16 ? "BF16" : (level == INNER_SPLIT ? "BF16x3" : "HP");
+  return level == INNER_LOW ? "FP16/BF16" : (level == INNER_SPLIT ? "BF16x3" : "HP");
 }
 
 // Operators of an FP64-vector inner solve at the split or HP level: the
@@ -671,7 +683,7 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
   int remaining = a.o.max_iter;
   // the inner arithmetic moves up a level (BF16 -> BF16x3 -> HP) once a
   // correction contracts the residual by less than a half (see batched_mixed)
-  int level = INNER_BF16;
+  int level = INNER_LOW;
   double rel_prev = 0.0;
   double rel[KRR_MAX_RHS] = {0}, rel_saved[KRR_MAX_RHS] = {0};
   for (;;) {
@@ -731,8 +743,8 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
     KRR_CUDA(cudaMemcpyAsync(Rp, Rd, nk * sizeof(double), cudaMemcpyDeviceToDevice, st));
     launch_convert<double, double>(st, Rd, n, k, k, Rs, k, sc);
     LoopOut lo;
-    if (level == INNER_BF16) {
-      const int prec = KRR_BF16;
+    if (level == INNER_LOW) {
+      const int prec = low_precision(a.o);
       PcgSpec<float> S;
       S.n = n; S.k = k; S.Ytol = Rs; S.ldy = k;
       S.x = wsT<float>(h, "v_xf", nk); S.r = wsT<float>(h, "v_rf", nk);
@@ -802,6 +814,9 @@ void check_solve_args(const krr_opts& o, int n, int d, int ldx, double sigma, do
   }
   if (o.precision == KRR_MIXED) {
     KRR_REQUIRE(o.inner_tol > 0.0 && o.inner_tol < 1.0, "pcg_solve: inner_tol in (0, 1)");
+    KRR_REQUIRE(o.inner_precision == 0 || o.inner_precision == KRR_FP16 ||
+                    o.inner_precision == KRR_BF16,
+                "pcg_solve: inner_precision must be 0, KRR_FP16 or KRR_BF16");
   }
 }
 
@@ -818,7 +833,10 @@ void setup_impl(krr_handle* h, const float* Xd, int n, int d, int ldx, double si
     precond_setup_impl(h, Z, n, s, s, lp, o.apply_form, zb);
   }
   if (o.precision == KRR_MIXED) {
-    tc_prepare(h->tc, st, Xd, n, ldx, d, sigma);
+    if (low_precision(o) == KRR_FP16)
+      tc_prepare_f16(h->tc, st, Xd, n, ldx, d, sigma);
+    else
+      tc_prepare(h->tc, st, Xd, n, ldx, d, sigma);
     tc_clear_error(h->tc, st);
     if (hp_supported(d)) {
       hp_prepare(h->hp, st, Xd, n, ldx, d, sigma);
@@ -1016,7 +1034,7 @@ struct BItem {
   ColScale inv;
   // mixed precision: the inner arithmetic moves up a level (BF16 -> BF16x3
   // -> HP) when a correction contracts the residual by less than a half
-  int level = INNER_BF16;
+  int level = INNER_LOW;
   double rel_prev = 0.0;
   double rel_saved[KRR_MAX_RHS] = {0};
 };
@@ -1246,8 +1264,10 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
           it.inv.v[c] = std::sqrt(rr[c]);
         }
       launch_convert<double, double>(g->stream, Rd, it.n, it.k, it.k, Rs, it.k, sc);
-      if (it.level == INNER_BF16) {
-        PcgSpec<float> S = item_spec<float>(it, Rs, o.inner_tol, KRR_BF16, o.precond != 0);
+      if (it.level == INNER_LOW) {
+        PcgSpec<float> S =
+            item_spec<float>(it, Rs, inner_tol_for(INNER_LOW, o, it.rel_prev), low_precision(o),
+                             o.precond != 0);
         launch_convert<double, float>(g->stream, Rs, it.n, it.k, it.k, S.r, it.k, one);
         KRR_CUDA(cudaMemsetAsync(S.x, 0, nk * sizeof(float), g->stream));
         pcg_begin<float>(g, S);
@@ -1287,7 +1307,7 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
       // a NaN in the inner solve leaves Cd unchanged; the next round takes
       // the correction back and moves the inner arithmetic up a level
       if (!(lo.flags & FLAG_NAN)) {
-        if (it.level != INNER_BF16)
+        if (it.level != INNER_LOW)
           launch_axpy_d<double>(g->stream, wsT<double>(g, "v_x", nk), it.n, it.k, it.k, Cd, it.k,
                                 it.inv);
         else
@@ -1316,6 +1336,14 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
 // ======================================================================= ABI
 extern "C" {
 
+krr_status krr_set_autotune(krr_handle* h, int on, int* shapes) {
+  if (!h) return KRR_EINVAL;
+  tc_set_autotune(h->tc, on);
+  for (krr_handle* sub : h->subs) tc_set_autotune(sub->tc, on);
+  if (shapes) *shapes = tc_tuned_shapes();
+  return KRR_OK;
+}
+
 void krr_default_opts(krr_opts* o) {
   if (!o) return;
   memset(o, 0, sizeof(*o));
@@ -1326,10 +1354,11 @@ void krr_default_opts(krr_opts* o) {
   o->precision = KRR_FP64;
   o->apply_form = KRR_APPLY_ZL;
   o->use_graph = 1;
-  o->inner_tol = 1e-2;
+  o->inner_tol = 3e-2;
   o->max_outer = 30;
   o->z_bf16 = -1;
   o->warm_start = 0;
+  o->inner_precision = KRR_FP16;
 }
 
 const char* krr_status_string(krr_status s) {
@@ -1431,11 +1460,13 @@ krr_status krr_kernel_matvec(krr_handle* h, const float* Xr, int nr, int ldxr, c
     KRR_REQUIRE(sigma > 0.0 && std::isfinite(sigma), "kernel_matvec: sigma must be > 0");
     KRR_REQUIRE(shift == 0.0 || nr == nc, "kernel_matvec: shift needs a square product");
     KRR_REQUIRE(precision == KRR_FP64 || precision == KRR_FP32 || precision == KRR_BF16 ||
-                    precision == KRR_HP || precision == KRR_BF16X3 || precision == KRR_BF16P,
+                    precision == KRR_HP || precision == KRR_BF16X3 || precision == KRR_BF16P ||
+                    precision == KRR_FP16,
                 "kernel_matvec: bad precision");
     matvec_dispatch(h, h->stream, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, shift, V, k, ldv, Q, ldq,
                     precision);
-    if (((precision == KRR_BF16 || precision == KRR_BF16X3 || precision == KRR_BF16P) &&
+    if (((precision == KRR_BF16 || precision == KRR_BF16X3 || precision == KRR_BF16P ||
+          precision == KRR_FP16) &&
          tc_error(h->tc, h->stream)) ||
         (precision == KRR_HP && hp_error(h->hp, h->stream)))
       throw Error{KRR_ETIMEOUT, "tensor-core product: a pipeline wait hit its limit"};
@@ -1538,6 +1569,7 @@ krr_status krr_pcg_solve_batched(krr_handle* h, const krr_problem* probs, int np
       if (cs != KRR_OK) throw Error{cs, "pcg_solve_batched: could not create a problem handle"};
       h->subs.push_back(sub);
     }
+    for (krr_handle* sub : h->subs) tc_set_autotune(sub->tc, h->tc.autotune ? 1 : 0);
     KRR_CUDA(cudaEventRecord(h->ev[0], st));
     // largest problems first: their graph branches are issued first
     std::vector<int> order(nprob);

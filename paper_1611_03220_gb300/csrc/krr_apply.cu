@@ -284,6 +284,23 @@ __device__ __forceinline__ uint32_t sh_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// Rows of stage g of a CTA that owns rows [r0, r1), rps rows a stage: first
+// to last, or (rev) last to first.  zt walks its rows forwards and zw
+// backwards, so zw starts on the rows that zt read last, which are still in
+// L2 (Z is larger than L2, but only a little), and the next zt starts on the
+// rows that zw read last.
+__device__ __forceinline__ void stage_span(int g, int r0, int r1, int rps, bool rev, int& row0,
+                                           int& nrow) {
+  if (!rev) {
+    row0 = r0 + g * rps;
+    nrow = min(rps, r1 - row0);
+  } else {
+    const int hi = r1 - g * rps;
+    row0 = max(r0, hi - rps);
+    nrow = hi - row0;
+  }
+}
+
 // Issue the copies of stage `st` (rows [row0, row0 + nrow), columns
 // [c0, c0 + seg)) and return; thread 0 only.
 __device__ __forceinline__ void stg_issue(uint8_t* ring, uint64_t* full, int st, const uint8_t* Z,
@@ -421,9 +438,11 @@ zw_stream_kernel(const void* __restrict__ Zs, int n, int s, const double* __rest
     for (int i = 0; i < NSTG; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sh_u32(&full[i])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    for (int g = 0; g < NSTG && g < nstage; ++g)
-      stg_issue(ring, full, g, (const uint8_t*)Zs, row_bytes, 0, row_bytes, r0 + g * rps,
-                min(rps, r1 - r0 - g * rps));
+    for (int g = 0; g < NSTG && g < nstage; ++g) {
+      int a0, na;
+      stage_span(g, r0, r1, rps, true, a0, na);
+      stg_issue(ring, full, g, (const uint8_t*)Zs, row_bytes, 0, row_bytes, a0, na);
+    }
   }
   for (int e = threadIdx.x; e < s * KV; e += AT) {
     const int b = e / KV, c = e % KV;
@@ -445,7 +464,8 @@ zw_stream_kernel(const void* __restrict__ Zs, int n, int s, const double* __rest
     const uint32_t parity = (uint32_t)((g / NSTG) & 1);
     ok = __syncthreads_and(ok && stg_wait(sh_u32(&full[st]), parity));
     if (!ok) break;
-    const int row0 = r0 + g * rps, nrow = min(rps, r1 - row0);
+    int row0, nrow;
+    stage_span(g, r0, r1, rps, true, row0, nrow);
     const uint8_t* base = ring + (size_t)st * SBYTES;
     // with BF16 Z each warp takes two rows at a time (one read of w serves
     // both); FP32 rows are twice as long and fill the registers alone
@@ -495,10 +515,14 @@ zw_stream_kernel(const void* __restrict__ Zs, int n, int s, const double* __rest
           }
 #pragma unroll
           for (int h = 0; h < RW; ++h) {
-            ACC x = acc[h][c];
+            // two chains of four (the loop is latency-bound at eight warps)
+            ACC x = acc[h][c], y = (ACC)0;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) x = fma((ACC)z[h][q], wv[q], x);
-            acc[h][c] = x;
+            for (int q = 0; q < 8; q += 2) {
+              x = fma((ACC)z[h][q], wv[q], x);
+              y = fma((ACC)z[h][q + 1], wv[q + 1], y);
+            }
+            acc[h][c] = x + y;
           }
         }
       }
@@ -518,9 +542,11 @@ zw_stream_kernel(const void* __restrict__ Zs, int n, int s, const double* __rest
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0 && g + NSTG < nstage)
-      stg_issue(ring, full, st, (const uint8_t*)Zs, row_bytes, 0, row_bytes,
-                r0 + (g + NSTG) * rps, min(rps, r1 - r0 - (g + NSTG) * rps));
+    if (threadIdx.x == 0 && g + NSTG < nstage) {
+      int a0, na;
+      stage_span(g + NSTG, r0, r1, rps, true, a0, na);
+      stg_issue(ring, full, st, (const uint8_t*)Zs, row_bytes, 0, row_bytes, a0, na);
+    }
   }
   if (!ok && threadIdx.x == 0) {
     atomicOr(err, 1);

@@ -39,9 +39,15 @@
 // expiry the kernel raises an error flag, drains its own copies and MMAs,
 // frees TMEM and returns.
 #include <cuda.h>
+#include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "krr_tc.cuh"
 #include "krr_tc_ptx.cuh"
@@ -61,7 +67,6 @@ constexpr int A_BYTES = BM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int TMEM_COLS = 512;
-constexpr uint32_t IDESC = idesc_bf16(BM, BN);
 
 // Per-RHS-width configuration: epilogue warps, w-ring slots, accumulator
 // chains, FMA-pipe exponentials per 32 entries.  Chosen by a sweep at
@@ -86,6 +91,7 @@ struct TcParams {
   int a_res;        // 1: one K-block, the row tile stays in shared memory per item
   int x3;           // split points xh = hi + lo: S = hi.hi + lo.hi + hi.lo (a_res only)
   int ns;           // stages in the ring (<= NS_MAX)
+  uint32_t idesc;   // MMA instruction descriptor (BF16 or FP16 operands)
   const float* w;   // n_ct*BN x KV
   float* part;      // nchunk x n_rpad x KV
   int* err;
@@ -256,13 +262,14 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             const uint32_t sb = p.a_res ? ss : ss + A_BYTES;
 #pragma unroll
             for (int kk = 0; kk < BK / UK; ++kk)
-              mma_bf16(d, sdesc(sa + kk * UK * 2), sdesc(sb + kk * UK * 2), IDESC,
+              mma_bf16(d, sdesc(sa + kk * UK * 2), sdesc(sb + kk * UK * 2), p.idesc,
                        (kb > 0 || kk > 0) ? 1u : 0u);
             if (p.x3 && kb == 0) {
               // lo rows against the hi columns
 #pragma unroll
               for (int kk = 0; kk < BK / UK; ++kk)
-                mma_bf16(d, sdesc(sa + A_BYTES + kk * UK * 2), sdesc(sb + kk * UK * 2), IDESC, 1u);
+                mma_bf16(d, sdesc(sa + A_BYTES + kk * UK * 2), sdesc(sb + kk * UK * 2), p.idesc,
+                         1u);
             }
             any = true;
             mma_commit(smem_u32(&empty[st]));
@@ -750,13 +757,14 @@ tc_matvec2_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant
 }
 
 // ------------------------------------------------------------ helpers ----
-// xh = bf16(scale (x - mu)) padded to n_pad x kp, nh = ||xh||^2, ra = exp2(-nh/2).
-// With Xlo the points are split, xh = hi + lo with lo = bf16(u - hi), and nh
-// is taken of hi + lo.
+// xh = bf16(scale (x - mu)) (fp16 with f16) padded to n_pad x kp,
+// nh = ||xh||^2, ra = exp2(-nh/2).  With Xlo the points are split,
+// xh = hi + lo with lo = bf16(u - hi), and nh is taken of hi + lo.
 __global__ void prep_rows_kernel(const float* __restrict__ X, int n, int ld, int d,
                                  const double* __restrict__ mu, double scale, int n_pad, int kp,
-                                 __nv_bfloat16* __restrict__ Xa, __nv_bfloat16* __restrict__ Xlo,
-                                 float* __restrict__ ra, float* __restrict__ nh_out) {
+                                 int f16, __nv_bfloat16* __restrict__ Xa,
+                                 __nv_bfloat16* __restrict__ Xlo, float* __restrict__ ra,
+                                 float* __restrict__ nh_out) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= n_pad) return;
   const int i = warp;
@@ -764,9 +772,16 @@ __global__ void prep_rows_kernel(const float* __restrict__ X, int n, int ld, int
   for (int t = lane; t < kp; t += 32) {
     double u = 0.0;
     if (i < n && t < d) u = scale * ((double)X[(size_t)i * ld + t] - mu[t]);
-    const __nv_bfloat16 b = __float2bfloat16_rn((float)u);
-    Xa[(size_t)i * kp + t] = b;
-    double bv = (double)__bfloat162float(b);
+    double bv;
+    if (f16) {
+      const __half hb = __float2half_rn((float)u);
+      reinterpret_cast<__half*>(Xa)[(size_t)i * kp + t] = hb;
+      bv = (double)__half2float(hb);
+    } else {
+      const __nv_bfloat16 b = __float2bfloat16_rn((float)u);
+      Xa[(size_t)i * kp + t] = b;
+      bv = (double)__bfloat162float(b);
+    }
     if (Xlo) {
       const __nv_bfloat16 l = __float2bfloat16_rn((float)(u - bv));
       Xlo[(size_t)i * kp + t] = l;
@@ -857,12 +872,13 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-void make_map(CUtensorMap* m, const void* base, int rows, int kp, int box_rows) {
+void make_map(CUtensorMap* m, const void* base, int rows, int kp, int box_rows, bool f16) {
   cuuint64_t gdim[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
   cuuint64_t gstride[1] = {(cuuint64_t)kp * 2};
   cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim,
+  CUresult r = encode_fn()(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                           2, const_cast<void*>(base), gdim,
                            gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -978,9 +994,10 @@ void make_vt_map(CUtensorMap* m, const void* base, int n_pad) {
     throw Error{KRR_ECUDA, "cuTensorMapEncodeTiled (Vt) failed: " + std::to_string((int)r)};
 }
 
-// Prepare one operand set into `op` (split into hi + lo when `split`).
+// Prepare one operand set into `op` (split into hi + lo when `split`, FP16
+// points when `f16`).
 void prep_operand(TcOperand& op, cudaStream_t st, const float* X, int n, int ld, int d,
-                  const double* mu, double scale, bool split) {
+                  const double* mu, double scale, bool split, bool f16 = false) {
   const int kp = (d + BK - 1) / BK * BK;
   const int n_pad = (n + PAD - 1) / PAD * PAD;
   ensure(op.Xa, (size_t)n_pad * kp * 2);
@@ -988,36 +1005,76 @@ void prep_operand(TcOperand& op, cudaStream_t st, const float* X, int n, int ld,
   ensure(op.ra, (size_t)n_pad * 4);
   ensure(op.nh, (size_t)n_pad * 4 + 16);
   prep_rows_kernel<<<(n_pad * 32 + 255) / 256, 256, 0, st>>>(
-      X, n, ld, d, mu, scale, n_pad, kp, (__nv_bfloat16*)op.Xa.p,
+      X, n, ld, d, mu, scale, n_pad, kp, f16 ? 1 : 0, (__nv_bfloat16*)op.Xa.p,
       split ? (__nv_bfloat16*)op.Xlo.p : nullptr, (float*)op.ra.p, (float*)op.nh.p);
   KRR_CHECK_LAUNCH();
   op.split = split;
+  op.f16 = f16;
   op.src = X;
   op.n = n;
   op.ld = ld;
   op.d = d;
   op.kp = kp;
   op.n_pad = n_pad;
-  make_map(&op.map_a, op.Xa.p, n_pad, kp, BM);
-  make_map(&op.map_b, op.Xa.p, n_pad, kp, BN);
-  make_map(&op.map_a2, split ? op.Xlo.p : op.Xa.p, n_pad, kp, BM);
-  make_map(&op.map_b2, split ? op.Xlo.p : op.Xa.p, n_pad, kp, BN);
+  make_map(&op.map_a, op.Xa.p, n_pad, kp, BM, f16);
+  make_map(&op.map_b, op.Xa.p, n_pad, kp, BN, f16);
+  make_map(&op.map_a2, split ? op.Xlo.p : op.Xa.p, n_pad, kp, BM, f16);
+  make_map(&op.map_b2, split ? op.Xlo.p : op.Xa.p, n_pad, kp, BN, f16);
 }
 
 struct Plan {
   int kv, n_rt, n_ct, cpc, nchunk;
+  int ns = 0;   // ring stages (0: the default for the operand)
 };
 
-Plan plan_for(const TcOperand& op, int k, int gemm2) {
+// The tile plan: column chunks per row tile from the wave-balance rule, or
+// `req` chunks when req > 0.
+Plan plan_for(const TcOperand& op, int k, int gemm2, int req = 0) {
   Plan pl;
   pl.kv = kv_bucket(k);
   pl.n_rt = op.n_pad / BM;
   pl.n_ct = op.n_pad / (gemm2 ? BN2 : BN);
-  const int req = choose_nchunk(pl.n_rt, pl.n_ct, sm_count());
+  if (req <= 0) req = choose_nchunk(pl.n_rt, pl.n_ct, sm_count());
+  req = std::max(1, std::min(req, pl.n_ct));
   pl.cpc = (pl.n_ct + req - 1) / req;
   pl.nchunk = (pl.n_ct + pl.cpc - 1) / pl.cpc;
   return pl;
 }
+
+size_t smem_for(int kv, int a_res, int ns, int x3) {
+  switch (kv) {
+    case 1: return smem_bytes<1>(a_res, ns, x3);
+    case 2: return smem_bytes<2>(a_res, ns, x3);
+    case 4: return smem_bytes<4>(a_res, ns, x3);
+    case 8: return smem_bytes<8>(a_res, ns, x3);
+    case 12: return smem_bytes<12>(a_res, ns, x3);
+    default: return smem_bytes<16>(a_res, ns, x3);
+  }
+}
+
+// ------------------------------------------------------------ autotuner --
+// Per problem shape (row tiles, column tiles, K-blocks, RHS bucket, operand
+// format) the tuner times the fused product under each candidate plan --
+// column chunks per row tile x ring stages -- and keeps the fastest in a
+// process-wide table, so each shape is timed once per process.  Plans that
+// would need more than 227 KiB of shared memory are skipped.  The chunk
+// count changes the order of the FP32 partial sums, so a tuned product can
+// differ from the default one in the last bits.
+struct TuneKey {
+  int n_rt, n_ct, nkb, kv, fmt;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(n_rt, n_ct, nkb, kv, fmt) < std::tie(o.n_rt, o.n_ct, o.nkb, o.kv, o.fmt);
+  }
+};
+struct Tuned {
+  int req, ns;
+  float ms;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, Tuned> g_tuned;
+constexpr size_t SMEM_LIMIT = 227 * 1024;
+
+int default_ns(int a_res) { return a_res ? 4 : 3; }
 
 }  // namespace
 
@@ -1062,9 +1119,161 @@ void tc_prepare_split(TcState& t, cudaStream_t st, const float* X, int n, int ld
   t.split_ready = true;
 }
 
-void tc_reserve(TcState& t, cudaStream_t st, int k, int gemm2) {
+void tc_prepare_f16(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int d,
+                    double sigma) {
+  tc_prepare(t, st, X, n, ldx, d, sigma);
+  if (t.half_ready && t.half.src == X && t.half.n == n && t.half.ld == ldx && t.half.d == d &&
+      t.half_sigma == sigma)
+    return;
+  const double c = 1.4426950408889634 / (2.0 * sigma * sigma);
+  // the BF16 set passed the exp2 range check (nh <= 120, so every component
+  // is below 11 in magnitude): FP16 holds these points without overflow
+  prep_operand(t.half, st, X, n, ldx, d, (const double*)t.mu.p, std::sqrt(2.0 * c), false, true);
+  t.half_sigma = sigma;
+  t.half_ready = true;
+}
+
+namespace {
+
+TcOperand& operand_of(TcState& t, int fmt) {
+  return fmt == 1 ? t.split : (fmt == 2 ? t.half : t.cols);
+}
+
+// Enqueue one fused product with plan `pl` (w, kernel, chunk sums).
+void run_fused(TcState& t, cudaStream_t st, TcOperand& op, const Plan& pl, int split, int f16,
+               int nr, const float* V, int k, int ldv, double shift, float* Q, int ldq) {
+  const int nkb = split ? 2 : op.kp / BK;
+  const int a_res = (split || nkb == 1) ? 1 : 0;
+  make_w_kernel<<<std::min(8 * sm_count(), (int)(((size_t)op.n_pad * pl.kv + 255) / 256)), 256,
+                  0, st>>>(V, op.n, k, ldv, (const float*)op.ra.p, op.n_pad, pl.kv,
+                           (float*)t.w.p);
+  KRR_CHECK_LAUNCH();
+  TcParams p;
+  p.n_rt = pl.n_rt;
+  p.n_ct = pl.n_ct;
+  p.nchunk = pl.nchunk;
+  p.cpc = pl.cpc;
+  p.nkb = nkb;
+  p.a_res = a_res;
+  p.ns = pl.ns > 0 ? pl.ns : default_ns(a_res);
+  p.x3 = split;
+  p.idesc = f16 ? idesc_f16(BM, BN) : idesc_bf16(BM, BN);
+  p.n_rpad = op.n_pad;
+  p.w = (const float*)t.w.p;
+  p.part = (float*)t.part.p;
+  p.err = (int*)t.err.p;
+  const int items = pl.n_rt * pl.nchunk;
+  const int grid = std::min(items, sm_count());
+  dispatch(pl.kv, st, op, p, grid);
+  const size_t total = (size_t)nr * k;
+  tc_reduce_kernel<<<std::min(8 * sm_count(), (int)((total + 255) / 256)), 256, 0, st>>>(
+      (const float*)t.part.p, pl.nchunk, op.n_pad, pl.kv, (const float*)op.ra.p, nr, k, V, ldv,
+      shift, Q, ldq);
+  KRR_CHECK_LAUNCH();
+}
+
+// Time the candidate plans of one shape on the prepared operand (scratch
+// right-hand sides) and return the fastest.
+Tuned tune_shape(TcState& t, cudaStream_t st, TcOperand& op, int k, int fmt) {
+  const int split = fmt == 1, f16 = fmt == 2;
+  const int nkb = split ? 2 : op.kp / BK;
+  const int a_res = (split || nkb == 1) ? 1 : 0;
+  const Plan base = plan_for(op, k, 0);
+  ensure(t.tune_v, (size_t)op.n * k * 4);
+  ensure(t.tune_q, (size_t)op.n * k * 4);
+  KRR_CUDA(cudaMemsetAsync(t.tune_v.p, 0, (size_t)op.n * k * 4, st));
+  std::vector<int> reqs;
+  const int cand[] = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32};
+  std::vector<int> seen;
+  for (int r : cand) {
+    const Plan pl = plan_for(op, k, 0, r);
+    if (std::find(seen.begin(), seen.end(), pl.nchunk) != seen.end()) continue;
+    seen.push_back(pl.nchunk);
+    reqs.push_back(r == 0 ? base.nchunk : r);
+  }
+  cudaEvent_t e0, e1;
+  KRR_CUDA(cudaEventCreate(&e0));
+  KRR_CUDA(cudaEventCreate(&e1));
+  Tuned best{0, default_ns(a_res), 1e30f};
+  try {
+    for (int r : reqs) {
+      for (int ns = 2; ns <= NS_MAX; ++ns) {
+        if (smem_for(base.kv, a_res, ns, split) > SMEM_LIMIT) continue;
+        Plan pl = plan_for(op, k, 0, r);
+        pl.ns = ns;
+        ensure(t.part, (size_t)pl.nchunk * op.n_pad * pl.kv * 4);
+        float ms = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+          KRR_CUDA(cudaEventRecord(e0, st));
+          run_fused(t, st, op, pl, split, f16, op.n, (const float*)t.tune_v.p, k, k, 0.0,
+                    (float*)t.tune_q.p, k);
+          KRR_CUDA(cudaEventRecord(e1, st));
+          KRR_CUDA(cudaEventSynchronize(e1));
+          float m = 0.f;
+          KRR_CUDA(cudaEventElapsedTime(&m, e0, e1));
+          if (rep > 0) ms = std::min(ms, m);   // the first run is a warm-up
+        }
+        if (ms < best.ms) best = Tuned{r, ns, ms};
+      }
+    }
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
+// The plan of the fused product for this shape: the tuned one when the
+// handle autotunes (timing it now unless the stream is being captured), else
+// the wave-balance rule.
+Plan resolve_plan(TcState& t, cudaStream_t st, TcOperand& op, int k, int gemm2, int fmt) {
+  Plan pl = plan_for(op, k, gemm2);
+  if (gemm2 || !t.autotune) return pl;
+  const int nkb = fmt == 1 ? 2 : op.kp / BK;
+  const TuneKey key{pl.n_rt, pl.n_ct, nkb, pl.kv, fmt};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      Plan q = plan_for(op, k, 0, it->second.req);
+      q.ns = it->second.ns;
+      return q;
+    }
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  KRR_CUDA(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return pl;
+  const Tuned tu = tune_shape(t, st, op, k, fmt);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = tu;
+  }
+  Plan q = plan_for(op, k, 0, tu.req);
+  q.ns = tu.ns;
+  return q;
+}
+
+}  // namespace
+
+void tc_set_autotune(TcState& t, int on) { t.autotune = on != 0; }
+
+int tc_tuned_shapes() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return (int)g_tuned.size();
+}
+
+void tc_reserve(TcState& t, cudaStream_t st, int k, int gemm2, int fmt) {
   if (!t.ready) throw Error{KRR_EINVAL, "tensor-core product used before tc_prepare"};
-  const Plan pl = plan_for(t.cols, k, gemm2);
+  TcOperand* op = &operand_of(t, fmt);
+  int f = fmt;
+  if (op->n_pad == 0) {  // that operand set is not prepared yet: size for the plain one
+    op = &t.cols;
+    f = 0;
+  }
+  const Plan pl = resolve_plan(t, st, *op, k, gemm2, f);
   ensure(t.w, (size_t)t.cols.n_pad * pl.kv * 4);
   ensure(t.part, (size_t)pl.nchunk * t.cols.n_pad * pl.kv * 4);
   if (gemm2 && t.vt.bytes < (size_t)N2 * t.cols.n_pad * 2) {
@@ -1083,16 +1292,21 @@ void tc_clear_error(TcState& t, cudaStream_t st) {
 
 void tc_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
                int nc, int ldxc, int d, double sigma, double shift, const float* V, int k,
-               int ldv, float* Q, int ldq, int split, int gemm2) {
+               int ldv, float* Q, int ldq, int split, int gemm2, int f16) {
   const bool same = (Xr == Xc && nr == nc && ldxr == ldxc);
   if (!same) throw Error{KRR_EUNSUPPORTED, "BF16 product supports the training system (Xr == Xc)"};
+  if (f16 && (split || gemm2))
+    throw Error{KRR_EUNSUPPORTED, "FP16 points: plain product only (no split, no second GEMM)"};
   if (split)
     tc_prepare_split(t, st, Xc, nc, ldxc, d, sigma);
+  else if (f16)
+    tc_prepare_f16(t, st, Xc, nc, ldxc, d, sigma);
   else
     tc_prepare(t, st, Xc, nc, ldxc, d, sigma);
-  tc_reserve(t, st, k, gemm2);
-  TcOperand& op = split ? t.split : t.cols;
-  const Plan pl = plan_for(op, k, gemm2);
+  const int fmt = split ? 1 : (f16 ? 2 : 0);
+  tc_reserve(t, st, k, gemm2, fmt);
+  TcOperand& op = operand_of(t, fmt);
+  const Plan pl = resolve_plan(t, st, op, k, gemm2, fmt);
   // split points: the row tile's hi and lo stay resident, each column tile
   // streams its hi and lo slices as two stages
   const int nkb = split ? 2 : op.kp / BK;
@@ -1124,30 +1338,7 @@ void tc_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr, c
     KRR_CHECK_LAUNCH();
     return;
   }
-  make_w_kernel<<<std::min(8 * sm_count(), (int)(((size_t)op.n_pad * pl.kv + 255) / 256)), 256,
-                  0, st>>>(V, nc, k, ldv, (const float*)op.ra.p, op.n_pad, pl.kv, (float*)t.w.p);
-  KRR_CHECK_LAUNCH();
-  TcParams p;
-  p.n_rt = pl.n_rt;
-  p.n_ct = pl.n_ct;
-  p.nchunk = pl.nchunk;
-  p.cpc = pl.cpc;
-  p.nkb = nkb;
-  p.a_res = a_res;
-  p.ns = a_res ? 4 : 3;
-  p.x3 = split;
-  p.n_rpad = op.n_pad;
-  p.w = (const float*)t.w.p;
-  p.part = (float*)t.part.p;
-  p.err = (int*)t.err.p;
-  const int items = pl.n_rt * pl.nchunk;
-  const int grid = std::min(items, sm_count());
-  dispatch(pl.kv, st, op, p, grid);
-  const size_t total = (size_t)nr * k;
-  tc_reduce_kernel<<<std::min(8 * sm_count(), (int)((total + 255) / 256)), 256, 0, st>>>(
-      (const float*)t.part.p, pl.nchunk, op.n_pad, pl.kv, (const float*)op.ra.p, nr, k, V, ldv,
-      shift, Q, ldq);
-  KRR_CHECK_LAUNCH();
+  run_fused(t, st, op, pl, split, f16, nr, V, k, ldv, shift, Q, ldq);
 }
 
 int tc_error(TcState& t, cudaStream_t st) {
@@ -1161,7 +1352,8 @@ int tc_error(TcState& t, cudaStream_t st) {
 void tc_release(TcState& t) {
   DevBuf* bufs[] = {&t.cols.Xa, &t.cols.ra, &t.cols.nh, &t.mu,        &t.scal,
                     &t.w,       &t.part,    &t.err,     &t.vt,        &t.split.Xa,
-                    &t.split.Xlo, &t.split.ra, &t.split.nh};
+                    &t.split.Xlo, &t.split.ra, &t.split.nh, &t.half.Xa,   &t.half.ra,
+                    &t.half.nh, &t.tune_v,  &t.tune_q};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   t = TcState();

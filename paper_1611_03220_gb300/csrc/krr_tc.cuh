@@ -6,14 +6,16 @@
 
 namespace krr {
 
-// One prepared operand set: xh = bf16(sqrt(2c)(x - mu)) padded to n_pad x kp
-// (K-major, 128-byte rows per 64-element K-block), nh = ||xh||^2 and
-// ra = exp2(-nh / 2), with TMA descriptors for 128-row and 256-row boxes.
+// One prepared operand set: xh = bf16(sqrt(2c)(x - mu)) (or fp16, f16 set)
+// padded to n_pad x kp (K-major, 128-byte rows per 64-element K-block),
+// nh = ||xh||^2 and ra = exp2(-nh / 2), with TMA descriptors for 128-row and
+// 256-row boxes.
 struct TcOperand {
   DevBuf Xa, Xlo, ra, nh;   // Xlo: low BF16 parts of split points (else unused)
   const float* src = nullptr;
   int n = 0, ld = 0, d = 0, kp = 0, n_pad = 0;
   bool split = false;
+  bool f16 = false;
   CUtensorMap map_a;
   CUtensorMap map_b;
   CUtensorMap map_a2;       // the low parts (split), else the same as map_a / map_b
@@ -32,6 +34,11 @@ struct TcState {
   TcOperand split;      // split points xh = hi + lo (KRR_BF16X3, d <= 64)
   double split_sigma = 0.0;
   bool split_ready = false;
+  TcOperand half;       // FP16-rounded points (KRR_FP16)
+  double half_sigma = 0.0;
+  bool half_ready = false;
+  bool autotune = false;  // time candidate tile plans per shape (process-wide cache)
+  DevBuf tune_v, tune_q;  // the tuner's scratch right-hand sides and products
   double sigma = 0.0;
   bool rows_same = false;
   bool ready = false;
@@ -66,16 +73,25 @@ void tc_prepare(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int
 // Also the split operands xh = bf16(u) + bf16(u - bf16(u)) (d <= 64).
 void tc_prepare_split(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int d,
                       double sigma);
+// Also the FP16-rounded points (same range check as the BF16 set).
+void tc_prepare_f16(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int d,
+                    double sigma);
 // Q = K(X, X) V + shift V through the tensor cores (Xr must equal Xc); with
 // `split` the dot products use split points (hi.hi + lo.hi + hi.lo); with
-// `gemm2` the contraction with V runs on the tensor cores on BF16-rounded
-// kernel entries.
+// `f16` the points are rounded to FP16 instead of BF16; with `gemm2` the
+// contraction with V runs on the tensor cores on BF16-rounded kernel entries.
 void tc_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
                int nc, int ldxc, int d, double sigma, double shift, const float* V, int k,
-               int ldv, float* Q, int ldq, int split = 0, int gemm2 = 0);
+               int ldv, float* Q, int ldq, int split = 0, int gemm2 = 0, int f16 = 0);
 // Allocate the product's workspace for k right-hand sides (call before a
-// graph capture; tc_prepare must have run).
-void tc_reserve(TcState& t, cudaStream_t st, int k, int gemm2 = 0);
+// graph capture; tc_prepare must have run).  fmt: 0 BF16 points, 1 split
+// points, 2 FP16 points.  With autotuning on, this is where an untimed shape
+// gets timed (the tuner launches and synchronises, so never during capture).
+void tc_reserve(TcState& t, cudaStream_t st, int k, int gemm2 = 0, int fmt = 0);
+// Autotuning of the fused product's tile plan (off by default).
+void tc_set_autotune(TcState& t, int on);
+// Number of shapes the process has tuned so far.
+int tc_tuned_shapes();
 // Reset the error flag (enqueued on st).
 void tc_clear_error(TcState& t, cudaStream_t st);
 // Nonzero if any launch hit a bounded-wait limit since the state was created.

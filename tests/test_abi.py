@@ -67,9 +67,9 @@ def test_struct_layout_matches_c_compiler(lib_path):
 #include <stddef.h>
 #include "krr.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(krr_opts), offsetof(krr_opts, inner_tol),
-         offsetof(krr_opts, warm_start), sizeof(krr_report), offsetof(krr_report, rel_res),
-         offsetof(krr_report, ms_total));
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(krr_opts), offsetof(krr_opts, inner_tol),
+         offsetof(krr_opts, warm_start), offsetof(krr_opts, inner_precision), sizeof(krr_report),
+         offsetof(krr_report, rel_res), offsetof(krr_report, ms_total));
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(krr_problem), offsetof(krr_problem, sigma),
          offsetof(krr_problem, s), offsetof(krr_problem, Y), offsetof(krr_problem, C),
          offsetof(krr_problem, ldc));
@@ -84,7 +84,8 @@ int main(void) {
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True,
                                                check=True).stdout.split()]
     O, R, P = _krr.krr_opts, _krr.krr_report, _krr.krr_problem
-    assert vals == [ctypes.sizeof(O), O.inner_tol.offset, O.warm_start.offset, ctypes.sizeof(R),
-                    R.rel_res.offset, R.ms_total.offset,
+    assert vals == [ctypes.sizeof(O), O.inner_tol.offset, O.warm_start.offset,
+                    O.inner_precision.offset, ctypes.sizeof(R), R.rel_res.offset,
+                    R.ms_total.offset,
                     ctypes.sizeof(P), P.sigma.offset, P.s.offset, P.Y.offset, P.C.offset,
                     P.ldc.offset]

@@ -46,13 +46,14 @@ def bf16_round(a):
     return t.to(torch.bfloat16).to(torch.float64).numpy()
 
 
-def rounded_points(X, sigma):
-    """xh = bf16(sqrt(log2 e)/sigma * (x - mean)) in FP64 (mean in FP64)."""
+def rounded_points(X, sigma, dtype=None):
+    """xh = bf16(sqrt(log2 e)/sigma * (x - mean)) in FP64 (mean in FP64); fp16 with
+    ``dtype=torch.float16``."""
     X64 = X.astype(np.float64)
     mu = X64.mean(axis=0)
     scale = math.sqrt(LOG2E) / sigma
     xf = (scale * (X64 - mu)).astype(np.float32)
-    return torch.from_numpy(xf).to(torch.bfloat16).to(torch.float64).numpy()
+    return torch.from_numpy(xf).to(dtype or torch.bfloat16).to(torch.float64).numpy()
 
 
 @pytest.mark.parametrize("n,d,k", [(1000, 37, 1), (777, 64, 3), (1300, 100, 10), (300, 8, 16),
@@ -77,6 +78,32 @@ def test_matvec_bf16_matches_rounded_oracle(K, h, n, d, k):
     # moves -||x_i - x_j||^2/(2 sigma^2) by about 2^-8 of its size
     exact = O.gaussian_kernel(X, X, sigma) @ V.astype(np.float64)
     assert np.all(np.abs(got - exact) <= 3e-2 * scale)
+
+
+@pytest.mark.parametrize("n,d,k", [(1000, 37, 1), (777, 64, 3), (1300, 100, 10), (300, 8, 16)])
+def test_matvec_fp16_matches_rounded_oracle(K, h, n, d, k):
+    """KRR_FP16: the same product on FP16-rounded points (11-bit significands)."""
+    rng = np.random.default_rng(7 * n + d + k)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    V = rng.standard_normal((n, k)).astype(np.float32)
+    sigma = math.sqrt(d)
+    Q = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    Xd = torch.from_numpy(X).cuda()
+    K.krr_kernel_matvec(h, Xd, Xd, sigma, 0.0, torch.from_numpy(V).cuda(), Q, "fp16")
+    Xh = rounded_points(X, sigma, torch.float16)
+    sig_h = 1.0 / math.sqrt(math.log(2.0))
+    Kh = O.gaussian_kernel(Xh, Xh, sig_h)
+    ref = Kh @ V.astype(np.float64)
+    scale = Kh @ np.abs(V.astype(np.float64))
+    got = Q.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got - ref) <= 1e-5 * scale), np.max(np.abs(got - ref) / scale)
+    # eight times finer point rounding than BF16 (2^-11 against 2^-8 relative)
+    exact = O.gaussian_kernel(X, X, sigma) @ V.astype(np.float64)
+    err16 = np.max(np.abs(got - exact) / scale)
+    Qb = torch.empty_like(Q)
+    K.krr_kernel_matvec(h, Xd, Xd, sigma, 0.0, torch.from_numpy(V).cuda(), Qb, "bf16")
+    err_b = np.max(np.abs(Qb.cpu().numpy().astype(np.float64) - exact) / scale)
+    assert err16 <= 5e-3 and err16 < err_b / 3, (err16, err_b)
 
 
 @pytest.mark.parametrize("n,d,k", [(777, 64, 3), (300, 8, 16), (2000, 784, 10), (400, 64, 1)])
@@ -207,16 +234,20 @@ def test_matvec_bf16_shift(K, h):
     np.testing.assert_allclose((Q1 - Q0).cpu().numpy(), 0.25 * V, rtol=1e-5, atol=1e-5)
 
 
-@pytest.mark.parametrize("cfg,n,s,tol", [(2, 4096, 128, 1e-6), (5, 3000, 256, 1e-6), (5, 8192, 512, 1e-6),
-                                         (1, 2000, 200, 1e-8)])
-def test_pcg_mixed_reaches_tolerance(K, h, cfg, n, s, tol):
-    """BF16 inner PCG + refinement with an FP64 residual reaches the FP64 target.
+@pytest.mark.parametrize("cfg,n,s,tol,inner", [(2, 4096, 128, 1e-6, "fp16"),
+                                               (2, 4096, 128, 1e-6, "bf16"),
+                                               (5, 3000, 256, 1e-6, "fp16"),
+                                               (5, 8192, 512, 1e-6, "fp16"),
+                                               (5, 8192, 512, 1e-6, "bf16"),
+                                               (1, 2000, 200, 1e-8, "fp16")])
+def test_pcg_mixed_reaches_tolerance(K, h, cfg, n, s, tol, inner):
+    """FP16 (or BF16) inner PCG + refinement with an FP64 residual reaches the FP64 target.
 
     The oracle recomputes ||y - (K + lambda I) c|| / ||y|| of the returned c.
     Workload 1's weak preconditioner needs ~1800 iterations in all (cap 6000)."""
     P = ks.make_config(cfg, n=n, s=s)
     C = torch.zeros((n, 1), dtype=torch.float64, device="cuda")
-    o = K.default_opts(tol=tol, precision="mixed", max_iter=6000)
+    o = K.default_opts(tol=tol, precision="mixed", max_iter=6000, inner_precision=inner)
     rep = K.krr_pcg_solve(h, torch.from_numpy(P.X).cuda(), P.sigma, P.lam,
                           torch.from_numpy(P.W).cuda(), torch.from_numpy(P.b).cuda(),
                           torch.from_numpy(P.Y).cuda(), C, o, check=False)
@@ -224,3 +255,39 @@ def test_pcg_mixed_reaches_tolerance(K, h, cfg, n, s, tol):
     res = O.true_rel_residual(P.X, P.Y, C.cpu().numpy(), P.sigma, P.lam)[0]
     assert res <= tol, (res, rep)
     assert rep["outer_steps"] >= 1
+
+
+@pytest.mark.parametrize("n,d,k,prec", [(3000, 64, 1, "fp16"), (2000, 100, 10, "bf16"),
+                                        (2500, 40, 3, "bf16x3")])
+def test_autotuned_plan_computes_the_same_product(K, h, n, d, k, prec):
+    """The tuner only changes how the column tiles are split into chunks and the
+    TMA ring depth: the product matches the default plan's up to FP32 summation
+    order, and the shape lands in the tuner's table."""
+    rng = np.random.default_rng(n + 3 * d + k)
+    X = torch.from_numpy(rng.standard_normal((n, d)).astype(np.float32)).cuda()
+    V = torch.from_numpy(rng.standard_normal((n, k)).astype(np.float32)).cuda()
+    sigma = math.sqrt(d)
+    Q0 = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    Q1 = torch.empty_like(Q0)
+    K.krr_kernel_matvec(h, X, X, sigma, 0.0, V, Q0, prec)
+    before = h.set_autotune(True)
+    K.krr_kernel_matvec(h, X, X, sigma, 0.0, V, Q1, prec)
+    after = h.set_autotune(False)
+    assert after >= before + (0 if before else 1)
+    scale = (torch.from_numpy(O.gaussian_kernel(X.cpu().numpy(), X.cpu().numpy(), sigma)).cuda()
+             @ V.abs().double()).float()
+    assert torch.all((Q1 - Q0).abs() <= 1e-5 * scale), float(((Q1 - Q0).abs() / scale).max())
+
+
+def test_mixed_solve_with_autotuning(K, h):
+    """A mixed solve on an autotuning handle still reaches the FP64 target."""
+    P = ks.make_config(2, n=4096, s=128)
+    h.set_autotune(True)
+    C = torch.zeros((P.n, 1), dtype=torch.float64, device="cuda")
+    o = K.default_opts(tol=1e-6, precision="mixed", max_iter=6000)
+    rep = K.krr_pcg_solve(h, torch.from_numpy(P.X).cuda(), P.sigma, P.lam,
+                          torch.from_numpy(P.W).cuda(), torch.from_numpy(P.b).cuda(),
+                          torch.from_numpy(P.Y).cuda(), C, o, check=False)
+    h.set_autotune(False)
+    assert rep["status"] == "KRR_OK", rep
+    assert O.true_rel_residual(P.X, P.Y, C.cpu().numpy(), P.sigma, P.lam)[0] <= 1e-6
