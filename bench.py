@@ -43,9 +43,8 @@ WORKLOAD = ("gaussian-mixture n=65536 d=64 (10 centres N(0,4I), unit spread), si
 M_TEST = 8192
 L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) of one tc_matvec_kernel<1> launch on FP16 points at n = 65536,
-# d = 64, from the ncu capture summarised in profiles/tc_matvec_kernel_n65536_d64.md (None
-# until the current kernel has been captured)
-TC_DRAM_BYTES_N65536 = None
+# d = 64, from the ncu capture summarised in profiles/tc_matvec_kernel_n65536_d64.md
+TC_DRAM_BYTES_N65536 = 8679168
 
 
 def parse():
@@ -59,7 +58,7 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--profile", default=None,
-                    choices=["step", "bf16", "fp16", "hp", "fp32", "apply"],
+                    choices=["step", "bf16", "fp16", "fp16sym", "hp", "fp32", "apply"],
                     help="short run for ncu: 'step' = one mixed and one FP32 solve of "
                          "--profile-iters PCG iterations with the host-driven loop (every "
                          "launch listed); otherwise 3 launches of that kernel product / apply")
@@ -251,8 +250,12 @@ def run_profile(args):
         dt = torch.float64 if args.profile == "hp" else torch.float32
         V = torch.randn((n, args.profile_k), dtype=dt, device="cuda")
         Q = torch.empty_like(V)
+        prec = args.profile
+        if prec == "fp16sym":   # the symmetric product (plan mode 2)
+            h.set_autotune(2)
+            prec = "fp16"
         for _ in range(3):
-            K.krr_kernel_matvec(h, X, X, P.sigma, P.lam, V, Q, args.profile)
+            K.krr_kernel_matvec(h, X, X, P.sigma, P.lam, V, Q, prec)
     torch.cuda.synchronize()
     h.close()
 

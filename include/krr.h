@@ -126,9 +126,14 @@ const char* krr_status_string(krr_status s);
  * process; the first product of a shape therefore synchronises the stream.
  * Solves time their shapes before they capture a graph.  Off (0) by
  * default: the plan then follows a fixed wave-balance rule, and results do
- * not depend on timing.  Batched solves pass the setting to their problems.
- * `shapes` (may be NULL) receives the number of shapes tuned so far in this
- * process.  Errors: KRR_EINVAL for a NULL handle.
+ * not depend on timing.  on = 2 selects, without timing, the symmetric
+ * product where it applies (one right-hand side, d <= 64, BF16 or FP16
+ * points): only the tiles on and above the block diagonal, each exponential
+ * serving K_ij and K_ji -- half the exponentials, though on GB300 it runs
+ * slower than the full product.  Batched solves pass the setting to their
+ * problems.  `shapes` (may be NULL) receives the number of shapes tuned so
+ * far in this process.  Errors: KRR_EINVAL for a NULL handle or on outside
+ * 0..2.
  */
 krr_status krr_set_autotune(krr_handle* h, int on, int* shapes);
 

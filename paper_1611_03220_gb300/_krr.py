@@ -141,10 +141,14 @@ class Handle:
     def set_stream(self, stream=None):
         self._check(_lib.krr_set_stream(self._h, _stream_ptr(stream)))
 
-    def set_autotune(self, on: bool = True) -> int:
-        """Turn tile-plan autotuning on or off; returns the shapes tuned so far."""
+    def set_autotune(self, on=True) -> int:
+        """Tile-plan selection: False/0 the fixed rule, True/1 autotune, 2 the
+        symmetric product where it applies; returns the shapes tuned so far."""
         n = _i(0)
-        self._check(_lib.krr_set_autotune(self._h, 1 if on else 0, C.byref(n)))
+        mode = int(on) if not isinstance(on, bool) else (1 if on else 0)
+        st = _lib.krr_set_autotune(self._h, mode, C.byref(n))
+        if st != KRR_OK:
+            raise KrrError(st, "krr_set_autotune: mode must be 0, 1 or 2")
         return n.value
 
     def _check(self, st: int):

@@ -1337,7 +1337,7 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
 extern "C" {
 
 krr_status krr_set_autotune(krr_handle* h, int on, int* shapes) {
-  if (!h) return KRR_EINVAL;
+  if (!h || on < 0 || on > 2) return KRR_EINVAL;
   tc_set_autotune(h->tc, on);
   for (krr_handle* sub : h->subs) tc_set_autotune(sub->tc, on);
   if (shapes) *shapes = tc_tuned_shapes();
@@ -1569,7 +1569,7 @@ krr_status krr_pcg_solve_batched(krr_handle* h, const krr_problem* probs, int np
       if (cs != KRR_OK) throw Error{cs, "pcg_solve_batched: could not create a problem handle"};
       h->subs.push_back(sub);
     }
-    for (krr_handle* sub : h->subs) tc_set_autotune(sub->tc, h->tc.autotune ? 1 : 0);
+    for (krr_handle* sub : h->subs) tc_set_autotune(sub->tc, h->tc.autotune);
     KRR_CUDA(cudaEventRecord(h->ev[0], st));
     // largest problems first: their graph branches are issued first
     std::vector<int> order(nprob);

@@ -37,8 +37,13 @@ struct TcState {
   TcOperand half;       // FP16-rounded points (KRR_FP16)
   double half_sigma = 0.0;
   bool half_ready = false;
-  bool autotune = false;  // time candidate tile plans per shape (process-wide cache)
+  int autotune = 0;       // 1: time candidate tile plans per shape (process-wide
+                          // cache); 2: the symmetric kernel where it applies
   DevBuf tune_v, tune_q;  // the tuner's scratch right-hand sides and products
+  // symmetric product (krr_matvec_sym.cu): per-tile row sums, per-item
+  // column sums and the device item list for (n_t, C)
+  DevBuf sym_rowpart, sym_colpart, sym_items;
+  int sym_items_nt = 0, sym_items_c = 0, sym_n_items = 0;
   double sigma = 0.0;
   bool rows_same = false;
   bool ready = false;
@@ -57,6 +62,17 @@ struct HpState {
   CUtensorMap map_a;
   CUtensorMap map_b;
 };
+
+// Grow a device buffer to at least `bytes` (contents not kept).
+void tc_ensure(DevBuf& b, size_t bytes);
+
+// Symmetric product (k = 1, d <= 64, no split): only tiles I <= J of 128 x 128,
+// each exponential serving K_ij and K_ji.  C: row blocks per work item,
+// ns: TMA ring stages.
+bool sym_supported(const TcOperand& op, int k, int split);
+void sym_reserve(TcState& t, cudaStream_t st, const TcOperand& op, int C);
+void sym_matvec(TcState& t, cudaStream_t st, const TcOperand& op, int f16, int C, int ns,
+                int nr, const float* V, int ldv, double shift, float* Q, int ldq);
 
 bool hp_supported(int d);
 void hp_prepare(HpState& t, cudaStream_t st, const float* X, int n, int ldx, int d, double sigma);
@@ -88,8 +104,9 @@ void tc_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr, c
 // points, 2 FP16 points.  With autotuning on, this is where an untimed shape
 // gets timed (the tuner launches and synchronises, so never during capture).
 void tc_reserve(TcState& t, cudaStream_t st, int k, int gemm2 = 0, int fmt = 0);
-// Autotuning of the fused product's tile plan (off by default).
-void tc_set_autotune(TcState& t, int on);
+// Plan selection of the fused product: 0 the fixed rule (default), 1 autotune,
+// 2 the symmetric kernel where it applies (k = 1, d <= 64, no split).
+void tc_set_autotune(TcState& t, int mode);
 // Number of shapes the process has tuned so far.
 int tc_tuned_shapes();
 // Reset the error flag (enqueued on st).

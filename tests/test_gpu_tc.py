@@ -291,3 +291,32 @@ def test_mixed_solve_with_autotuning(K, h):
     h.set_autotune(False)
     assert rep["status"] == "KRR_OK", rep
     assert O.true_rel_residual(P.X, P.Y, C.cpu().numpy(), P.sigma, P.lam)[0] <= 1e-6
+
+
+@pytest.mark.parametrize("n,d,prec", [(3000, 64, "fp16"), (1000, 37, "bf16"), (517, 8, "fp16")])
+def test_symmetric_product_matches_rounded_oracle(K, h, n, d, prec):
+    """The symmetric product (tiles I <= J only, each exponential used for K_ij
+    and K_ji) is the same kernel of the rounded points as the full product."""
+    rng = np.random.default_rng(11 * n + d)
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    V = rng.standard_normal((n, 1)).astype(np.float32)
+    sigma = math.sqrt(d)
+    Xd, Vd = torch.from_numpy(X).cuda(), torch.from_numpy(V).cuda()
+    Qs = torch.empty((n, 1), dtype=torch.float32, device="cuda")
+    Qf = torch.empty_like(Qs)
+    h.set_autotune(2)
+    K.krr_kernel_matvec(h, Xd, Xd, sigma, 0.5, Vd, Qs, prec)
+    h.set_autotune(0)
+    K.krr_kernel_matvec(h, Xd, Xd, sigma, 0.5, Vd, Qf, prec)
+    Xh = rounded_points(X, sigma, torch.float16 if prec == "fp16" else None)
+    Kh = O.gaussian_kernel(Xh, Xh, 1.0 / math.sqrt(math.log(2.0)))
+    ref = Kh @ V.astype(np.float64) + 0.5 * V.astype(np.float64)
+    scale = Kh @ np.abs(V.astype(np.float64)) + 0.5 * np.abs(V.astype(np.float64))
+    gs = Qs.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(gs - ref) <= 1e-5 * scale), np.max(np.abs(gs - ref) / scale)
+    assert np.all(np.abs(gs - Qf.cpu().numpy()) <= 1e-5 * scale)
+
+
+def test_set_autotune_rejects_bad_mode(K, h):
+    with pytest.raises(K.KrrError):
+        h.set_autotune(3)
