@@ -87,6 +87,9 @@ typedef struct {
   int warm_start;      /* 1: C holds x0 on entry                             */
   int inner_precision; /* KRR_MIXED: product of the inner PCG, KRR_FP16 or   */
                        /* KRR_BF16 (0: the default, KRR_FP16)                */
+  int keep_direction;  /* KRR_MIXED: 1 continues the previous inner solve's  */
+                       /* search direction after the residual is replaced   */
+                       /* (k <= 5); 0 (default) restarts each at p = z      */
 } krr_opts;
 
 typedef struct {

@@ -36,7 +36,8 @@ class krr_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("lambda_p", C.c_double),
                 ("precond", C.c_int), ("precision", C.c_int), ("apply_form", C.c_int),
                 ("use_graph", C.c_int), ("inner_tol", C.c_double), ("max_outer", C.c_int),
-                ("z_bf16", C.c_int), ("warm_start", C.c_int), ("inner_precision", C.c_int)]
+                ("z_bf16", C.c_int), ("warm_start", C.c_int), ("inner_precision", C.c_int),
+                ("keep_direction", C.c_int)]
 
 
 class krr_report(C.Structure):

@@ -269,6 +269,10 @@ struct PcgSpec {
   int max_iter = 0;
   std::function<void(cudaStream_t, const T*, T*)> matvec, apply;
   int prec = KRR_FP64;
+  // keep the previous solve's last direction (p holds it, in units s times
+  // smaller than these) instead of starting from p = z
+  bool restart = false;
+  ColScale rscale{};
 };
 
 // Everything before the first iteration: ||y||, z0 = M^-1 r0, p0 = z0.
@@ -282,7 +286,10 @@ void pcg_begin(krr_handle* h, const PcgSpec<T>& S) {
     S.apply(st, S.r, S.z);
   else
     KRR_CUDA(cudaMemcpyAsync(S.z, S.r, (size_t)S.n * S.k * sizeof(T), cudaMemcpyDeviceToDevice, st));
-  launch_cg_rz_first<T>(st, h->sc, S.r, S.z, S.p, S.n, S.k, part);
+  if (S.restart && 3 * S.k <= KRR_MAX_RHS)
+    launch_cg_restart<T>(st, h->sc, S.r, S.z, S.p, S.n, S.k, S.rscale, part);
+  else
+    launch_cg_rz_first<T>(st, h->sc, S.r, S.z, S.p, S.n, S.k, part);
 }
 
 // One PCG iteration of Algorithm 1: q = A p, alpha, x and r updates,
@@ -686,6 +693,10 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
   int level = INNER_LOW;
   double rel_prev = 0.0;
   double rel[KRR_MAX_RHS] = {0}, rel_saved[KRR_MAX_RHS] = {0};
+  // consecutive low-level inner solves continue the previous search
+  // direction (residual replacement) unless a step was taken back
+  bool keep_ok = false;
+  double norm_prev[KRR_MAX_RHS] = {0};
   for (;;) {
     double rr[KRR_MAX_RHS];
     host_colnorm2<double>(h, Rd, n, k, k, rr);
@@ -703,6 +714,7 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
     if (outer > 0) {
       if (!finite || !(now < rel_prev)) {
         // the last correction did not help: take it back
+        keep_ok = false;
         KRR_CUDA(cudaMemcpyAsync(Cd, Cp, nk * sizeof(double), cudaMemcpyDeviceToDevice, st));
         KRR_CUDA(cudaMemcpyAsync(Rd, Rp, nk * sizeof(double), cudaMemcpyDeviceToDevice, st));
         host_colnorm2<double>(h, Rd, n, k, k, rr);
@@ -759,11 +771,18 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
         S.apply = [&](cudaStream_t s2, const float* R, float* Zo) {
           apply_precond<float>(h, s2, R, k, k, Zo, k);
         };
+      S.restart = keep_ok && a.o.keep_direction != 0;
+      for (int c = 0; c < KRR_MAX_RHS; ++c)
+        S.rscale.v[c] = (c < k && norm_prev[c] > 0.0 && inv.v[c] > 0.0)
+                            ? norm_prev[c] / inv.v[c] : 0.0;
       launch_convert<double, float>(st, Rs, n, k, k, S.r, k, one);
       KRR_CUDA(cudaMemsetAsync(S.x, 0, nk * sizeof(float), st));
       pcg_loop<float>(h, S, a.o.use_graph != 0, &lo, matvecs);
       if (!(lo.flags & FLAG_NAN)) launch_axpy_d<float>(st, S.x, n, k, k, Cd, k, inv);
+      keep_ok = !(lo.flags & (FLAG_NAN | FLAG_BREAKDOWN));
+      for (int c = 0; c < KRR_MAX_RHS; ++c) norm_prev[c] = inv.v[c];
     } else {
+      keep_ok = false;
       PcgSpec<double> S;
       S.n = n; S.k = k; S.Ytol = Rs; S.ldy = k;
       S.x = wsT<double>(h, "v_x", nk); S.r = wsT<double>(h, "v_r", nk);
@@ -1359,6 +1378,7 @@ void krr_default_opts(krr_opts* o) {
   o->z_bf16 = -1;
   o->warm_start = 0;
   o->inner_precision = KRR_FP16;
+  o->keep_direction = 0;
 }
 
 const char* krr_status_string(krr_status s) {

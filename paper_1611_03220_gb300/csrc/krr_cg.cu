@@ -118,6 +118,7 @@ cg_init_kernel(CgScalars* sc, const double* __restrict__ Y, int ldy, const T* __
       sc->active[c] = 0;
     }
     sc->iters[c] = 0;
+    sc->rz_keep[c] = sc->rz[c];
     sc->alpha[c] = sc->beta[c] = sc->rz[c] = sc->pq[c] = 0.0;
   }
   sc->run = (any && max_iter > 0 && !(sc->flags & FLAG_NAN)) ? 1 : 0;
@@ -168,6 +169,72 @@ cg_rz_first_kernel(CgScalars* sc, const T* __restrict__ R, const T* __restrict__
         sc->active[c] = 0;
       }
     }
+  }
+}
+
+// Restart with the previous direction kept: sums r.z, r.r and r.P (P in the
+// previous units), then per column the coefficients of p = a_z z + a_p P,
+// stored in alpha (a_z) and beta (a_p) until the first iteration overwrites
+// them.  With P' = s P and beta = r.z / (s^2 rz_keep):
+//   p = z + beta (P' - (r.P' / r.z) z),  so  r.p = r.z  exactly.
+template <typename T>
+__global__ void __launch_bounds__(CT)
+cg_restart_kernel(CgScalars* sc, const T* __restrict__ R, const T* __restrict__ Z,
+                  const T* __restrict__ P, int n, int k, ColScale s, double* part) {
+  double v[KRR_MAX_RHS], tot[KRR_MAX_RHS];
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c) v[c] = 0.0;
+  for (int i = blockIdx.x * CT + threadIdx.x; i < n; i += gridDim.x * CT) {
+    for (int c = 0; c < k; ++c) {
+      const size_t e = (size_t)i * k + c;
+      const double r = (double)R[e];
+      v[c] = fma(r, (double)Z[e], v[c]);
+      v[k + c] = fma(r, r, v[k + c]);
+      v[2 * k + c] = fma(r, (double)P[e], v[2 * k + c]);
+    }
+  }
+  if (!grid_colsum(v, 3 * k, part, &sc->counter[C_RZ], tot)) return;
+  for (int c = 0; c < k; ++c) {
+    const double rz = tot[c], rr = tot[k + c], rp = s.v[c] * tot[2 * k + c];
+    const double rzk = s.v[c] * s.v[c] * sc->rz_keep[c];
+    sc->rz[c] = rz;
+    sc->rr[c] = rr;
+    double az = 1.0, ap = 0.0;
+    if (bad(rz) || bad(rr)) sc->flags |= FLAG_NAN;
+    if (sc->active[c]) {
+      if (rr <= sc->tol2[c]) {
+        sc->active[c] = 0;
+      } else if (!(rz > 0.0)) {
+        sc->flags |= FLAG_BREAKDOWN;
+        sc->active[c] = 0;
+      } else if (rzk > 0.0 && !bad(rzk) && !bad(rp)) {
+        const double beta = rz / rzk;
+        az = 1.0 - beta * rp / rz;
+        ap = beta * s.v[c];
+      }
+    }
+    sc->alpha[c] = az;
+    sc->beta[c] = ap;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CT)
+cg_restart_p_kernel(const CgScalars* sc, T* __restrict__ P, const T* __restrict__ Z, int n,
+                    int k) {
+  double az[KRR_MAX_RHS], ap[KRR_MAX_RHS];
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c) {
+    az[c] = c < k ? sc->alpha[c] : 0.0;
+    ap[c] = c < k ? sc->beta[c] : 0.0;
+  }
+  for (int i = blockIdx.x * CT + threadIdx.x; i < n; i += gridDim.x * CT) {
+#pragma unroll
+    for (int c = 0; c < KRR_MAX_RHS; ++c)
+      if (c < k) {
+        const size_t e = (size_t)i * k + c;
+        P[e] = (T)(az[c] * (double)Z[e] + ap[c] * (double)P[e]);
+      }
   }
 }
 
@@ -437,6 +504,17 @@ void launch_cg_rz_first(cudaStream_t st, CgScalars* sc, const T* R, const T* Z, 
 }
 
 template <typename T>
+void launch_cg_restart(cudaStream_t st, CgScalars* sc, const T* R, const T* Z, T* P, int n,
+                       int k, const ColScale& s, double* part) {
+  if (3 * k > KRR_MAX_RHS)
+    throw Error{KRR_EINVAL, "cg_restart: needs 3 k <= KRR_MAX_RHS"};
+  cg_restart_kernel<T><<<cg_blocks(n), CT, 0, st>>>(sc, R, Z, P, n, k, s, part);
+  KRR_CHECK_LAUNCH();
+  cg_restart_p_kernel<T><<<ew_blocks((size_t)n), CT, 0, st>>>(sc, P, Z, n, k);
+  KRR_CHECK_LAUNCH();
+}
+
+template <typename T>
 void launch_cg_alpha(cudaStream_t st, CgScalars* sc, const T* P, const T* Q, int n, int k,
                      double* part) {
   cg_alpha_kernel<T><<<cg_blocks(n), CT, 0, st>>>(sc, P, Q, n, k, part);
@@ -527,6 +605,8 @@ void launch_colnorm2(cudaStream_t st, const T* a, int n, int k, int lda, double*
                                   int, double, int, double*);                                 \
   template void launch_cg_rz_first<T>(cudaStream_t, CgScalars*, const T*, const T*, T*, int,  \
                                       int, double*);                                          \
+  template void launch_cg_restart<T>(cudaStream_t, CgScalars*, const T*, const T*, T*, int,   \
+                                     int, const ColScale&, double*);                          \
   template void launch_cg_alpha<T>(cudaStream_t, CgScalars*, const T*, const T*, int, int,     \
                                    double*);                                                  \
   template void launch_cg_update_xr<T>(cudaStream_t, CgScalars*, T*, T*, const T*, const T*,   \

@@ -60,6 +60,7 @@ namespace krr {
 // Device scalar block used by the PCG loop (one per handle).
 struct CgScalars {
   double rz[KRR_MAX_RHS];      // r.z of the current iteration
+  double rz_keep[KRR_MAX_RHS]; // r.z of the previous solve's last step (kept by cg_init)
   double pq[KRR_MAX_RHS];      // p.q
   double alpha[KRR_MAX_RHS];
   double beta[KRR_MAX_RHS];
@@ -153,6 +154,14 @@ void launch_cg_init(cudaStream_t st, CgScalars* sc, const double* Y, int ldy, co
 template <typename T>
 void launch_cg_rz_first(cudaStream_t st, CgScalars* sc, const T* R, const T* Z, T* P, int n,
                         int k, double* part);
+// Restart that keeps the previous search direction (a residual replacement):
+// with r and z = M^-1 r the replaced residual, P the previous solve's last
+// direction and s[c] the factor from the previous solve's units to these,
+// p = z + beta (s P - (r.(s P) / r.z) z), beta = r.z / (s^2 r.z_previous).
+// Needs 3 k <= KRR_MAX_RHS; columns without a usable previous step get p = z.
+template <typename T>
+void launch_cg_restart(cudaStream_t st, CgScalars* sc, const T* R, const T* Z, T* P, int n,
+                       int k, const ColScale& s, double* part);
 template <typename T>
 void launch_cg_alpha(cudaStream_t st, CgScalars* sc, const T* P, const T* Q, int n, int k,
                      double* part);

@@ -320,3 +320,17 @@ def test_symmetric_product_matches_rounded_oracle(K, h, n, d, prec):
 def test_set_autotune_rejects_bad_mode(K, h):
     with pytest.raises(K.KrrError):
         h.set_autotune(3)
+
+
+def test_mixed_solve_keeping_the_search_direction(K, h):
+    """keep_direction = 1 (residual replacement instead of a fresh restart) still
+    reaches the FP64 target."""
+    P = ks.make_config(2, n=4096, s=128)
+    C = torch.zeros((P.n, 1), dtype=torch.float64, device="cuda")
+    o = K.default_opts(tol=1e-6, precision="mixed", max_iter=6000, keep_direction=1)
+    rep = K.krr_pcg_solve(h, torch.from_numpy(P.X).cuda(), P.sigma, P.lam,
+                          torch.from_numpy(P.W).cuda(), torch.from_numpy(P.b).cuda(),
+                          torch.from_numpy(P.Y).cuda(), C, o, check=False)
+    assert rep["status"] == "KRR_OK", rep
+    assert rep["outer_steps"] >= 2
+    assert O.true_rel_residual(P.X, P.Y, C.cpu().numpy(), P.sigma, P.lam)[0] <= 1e-6
