@@ -157,22 +157,18 @@ trmv_kernel(const double* __restrict__ A, int s, const double* __restrict__ x, i
     const int per = (hi - lo + TR_SPLIT - 1) / TR_SPLIT;
     const int qlo = lo + q * per, qhi = min(hi, qlo + per);
     const double* row = A + (size_t)a * s;
-    int b = qlo + lane;
-    for (; b + 7 * 32 < qhi; b += 8 * 32) {
+    // eight predicated loads in flight per lane, also on the short rows of
+    // the triangle (a one-load-at-a-time tail made them latency-bound)
+    for (int b = qlo + lane; b < qhi; b += 8 * 32) {
       double av[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) av[u] = __ldg(row + b + 32 * u);
+      for (int u = 0; u < 8; ++u) av[u] = b + 32 * u < qhi ? __ldg(row + b + 32 * u) : 0.0;
 #pragma unroll
       for (int u = 0; u < 8; ++u)
 #pragma unroll
         for (int c = 0; c < KV; ++c)
-          if (c < k) acc[u & 1][c] = fma(av[u], __ldg(x + (size_t)(b + 32 * u) * k + c), acc[u & 1][c]);
-    }
-    for (; b < qhi; b += 32) {
-      const double av = __ldg(row + b);
-#pragma unroll
-      for (int c = 0; c < KV; ++c)
-        if (c < k) acc[0][c] = fma(av, __ldg(x + (size_t)b * k + c), acc[0][c]);
+          if (c < k && b + 32 * u < qhi)
+            acc[u & 1][c] = fma(av[u], __ldg(x + (size_t)(b + 32 * u) * k + c), acc[u & 1][c]);
     }
   }
 #pragma unroll
@@ -420,8 +416,12 @@ zt_stream_kernel(const void* __restrict__ Zs, int n, int s, const T* __restrict_
 
 // Zo[i, c] = (R[i, c] - sum_b Z[i, b] w[b, c]) / lambda_p with whole rows of Z
 // streamed; w (s x KV) in shared memory; each warp takes rows of a stage.
+// Sixteen warps (one BF16 row each per 64 KiB stage): with eight, the
+// shared-memory latency of each row's dot product set the pace.
+constexpr int ZAT = 512;
+
 template <int BF16, typename T, typename ACC, int KV>
-__global__ void __launch_bounds__(AT, 1)
+__global__ void __launch_bounds__(ZAT, 1)
 zw_stream_kernel(const void* __restrict__ Zs, int n, int s, const double* __restrict__ w, int k,
                  const T* __restrict__ R, int ldr, double inv_lam, T* __restrict__ Zo, int ldo,
                  int* err) {
@@ -444,19 +444,32 @@ zw_stream_kernel(const void* __restrict__ Zs, int n, int s, const double* __rest
       stg_issue(ring, full, g, (const uint8_t*)Zs, row_bytes, 0, row_bytes, a0, na);
     }
   }
-  for (int e = threadIdx.x; e < s * KV; e += AT) {
+  for (int e = threadIdx.x; e < s * KV; e += ZAT) {
     const int b = e / KV, c = e % KV;
     wsm[c * s + b] = c < k ? (ACC)w[(size_t)b * k + c] : (ACC)0;
   }
   // the CTA's rows of R, staged once (a per-row load after the reduction
   // would expose a memory round trip per row)
   double* rsm = reinterpret_cast<double*>(wsm + (size_t)s * KV);
-  for (int e = threadIdx.x; e < (r1 - r0) * KV; e += AT) {
+  for (int e = threadIdx.x; e < (r1 - r0) * KV; e += ZAT) {
     const int rr = e / KV, c = e % KV;
     rsm[e] = (r0 < r1 && c < k) ? (double)R[(size_t)(r0 + rr) * ldr + c] : 0.0;
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // One right-hand side in FP32 with s <= 2048: each lane keeps its 8 x 8
+  // entries of w (columns 8 lane + 256 it + q) in registers for the whole
+  // kernel, so a row costs its own bytes only (reading w from shared memory
+  // for every row cost twice the row's bytes).
+  constexpr bool REGW = KV == 1 && sizeof(ACC) == 4;
+  const int nit = s / 256;
+  const bool use_reg = REGW && s % 256 == 0 && nit <= 8;
+  float wr[8][8];
+#pragma unroll
+  for (int it = 0; it < 8; ++it)
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      wr[it][q] = (REGW && use_reg && it < nit) ? (float)wsm[lane * 8 + 256 * it + q] : 0.f;
   bool ok = true;
   int g = 0;
   for (; g < nstage; ++g) {
@@ -467,17 +480,52 @@ zw_stream_kernel(const void* __restrict__ Zs, int n, int s, const double* __rest
     int row0, nrow;
     stage_span(g, r0, r1, rps, true, row0, nrow);
     const uint8_t* base = ring + (size_t)st * SBYTES;
-    // with BF16 Z each warp takes two rows at a time (one read of w serves
-    // both); FP32 rows are twice as long and fill the registers alone
-    constexpr int RW = BF16 ? 2 : 1;
-    for (int rr = warp; rr < nrow; rr += RW * (AT / 32)) {
-      const int rb = rr + AT / 32;
+    if (REGW && use_reg) {
+      for (int rr = warp; rr < nrow; rr += ZAT / 32) {
+        float a[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          if (it < nit) {
+            float z[8];
+            if (BF16) {
+              const uint4 v = *reinterpret_cast<const uint4*>(base + (size_t)rr * row_bytes +
+                                                             (lane * 8 + 256 * it) * 2);
+              const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const float2 f = __bfloat1622float2(h2[q]);
+                z[2 * q] = f.x;
+                z[2 * q + 1] = f.y;
+              }
+            } else {
+              const float4* p4 = reinterpret_cast<const float4*>(
+                  base + (size_t)rr * row_bytes + (lane * 8 + 256 * it) * 4);
+              const float4 a4 = p4[0], b4 = p4[1];
+              z[0] = a4.x; z[1] = a4.y; z[2] = a4.z; z[3] = a4.w;
+              z[4] = b4.x; z[5] = b4.y; z[6] = b4.z; z[7] = b4.w;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) a[q & 3] = fmaf(z[q], wr[it][q], a[q & 3]);
+          }
+        }
+        float v = (a[0] + a[1]) + (a[2] + a[3]);
+        for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        const int i = row0 + rr;
+        if (lane == 0 && k > 0)
+          Zo[(size_t)i * ldo] = (T)((rsm[i - r0] - (double)v) * inv_lam);
+      }
+    } else
+    // one row per warp and pass (RW = 1): sixteen rows of a BF16 stage in one pass
+    for (int rr = warp; rr < nrow; rr += 1 * (ZAT / 32)) {
+      constexpr int RW = 1;
+      const int rb = rr + ZAT / 32;
       const bool two = RW == 2 && rb < nrow;
       ACC acc[RW][KV];
 #pragma unroll
       for (int h = 0; h < RW; ++h)
 #pragma unroll
         for (int c = 0; c < KV; ++c) acc[h][c] = (ACC)0;
+#pragma unroll 2
       for (int b0 = lane * 8; b0 < s; b0 += 256) {
         float z[RW][8];
 #pragma unroll
@@ -668,8 +716,8 @@ void apply_zl(cudaStream_t st, const Precond& pc, const ApplyPlan& pl, const T* 
     auto kw = zw_stream_kernel<BF16, T, ACC, KV>;
     KRR_CUDA(cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)zw_bytes));
-    kw<<<sm_count(), AT, zw_bytes, st>>>(pc.Z.p, n, s, t1, k, R, ldr, 1.0 / pc.lam_p, Zo, ldo,
-                                         err);
+    kw<<<sm_count(), ZAT, zw_bytes, st>>>(pc.Z.p, n, s, t1, k, R, ldr, 1.0 / pc.lam_p, Zo, ldo,
+                                          err);
     KRR_CHECK_LAUNCH();
     return;
   }
