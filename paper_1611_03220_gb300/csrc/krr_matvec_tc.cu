@@ -120,13 +120,15 @@ __device__ __forceinline__ float ex2_fma(float x) {
   return __int_as_float(__float_as_int(p) + (n << 23));
 }
 
-template <int KV>
+// EMU of every 32 exponentials run on the FMA pipe (a tuner dimension for
+// one right-hand side; Cfg<KV>::EMU otherwise).
+template <int KV, int EMU = Cfg<KV>::EMU>
 __global__ void __launch_bounds__(Cfg<KV>::THREADS, 1)
 tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
                  TcParams p) {
   constexpr int NEPI = Cfg<KV>::NEPI, NW = Cfg<KV>::NW, CH = Cfg<KV>::CH;
-  constexpr int EMU = Cfg<KV>::EMU, COLS = Cfg<KV>::COLS, NG = NEPI / 4;
+  constexpr int COLS = Cfg<KV>::COLS, NG = NEPI / 4;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int NS = p.ns;
@@ -955,23 +957,32 @@ size_t smem_bytes(int a_res, int ns, int x3) {
          (size_t)NW * BN * KV * 4 + (size_t)(NG - 1) * BM * KV * 4 + 256;
 }
 
-template <int KV>
+template <int KV, int EMU = Cfg<KV>::EMU>
 void launch_kernel(cudaStream_t st, const CUtensorMap& a, const CUtensorMap& b,
                    const CUtensorMap& a2, const CUtensorMap& b2, const TcParams& p, int grid) {
   static size_t attr = 0;
   const size_t sm = smem_bytes<KV>(p.a_res, p.ns, p.x3);
   if (attr < sm) {
-    KRR_CUDA(cudaFuncSetAttribute(tc_matvec_kernel<KV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sm));
+    KRR_CUDA(cudaFuncSetAttribute(tc_matvec_kernel<KV, EMU>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr = sm;
   }
-  tc_matvec_kernel<KV><<<grid, Cfg<KV>::THREADS, sm, st>>>(a, b, a2, b2, p);
+  tc_matvec_kernel<KV, EMU><<<grid, Cfg<KV>::THREADS, sm, st>>>(a, b, a2, b2, p);
   KRR_CHECK_LAUNCH();
 }
 
-void dispatch(int kv, cudaStream_t st, const TcOperand& op, const TcParams& p, int grid) {
+// emu: FMA-pipe exponentials per 32 for one right-hand side (0, 2 or 4).
+void dispatch(int kv, cudaStream_t st, const TcOperand& op, const TcParams& p, int grid,
+              int emu = 0) {
   switch (kv) {
-    case 1: launch_kernel<1>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid); break;
+    case 1:
+      if (emu == 4)
+        launch_kernel<1, 4>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid);
+      else if (emu == 2)
+        launch_kernel<1, 2>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid);
+      else
+        launch_kernel<1, 0>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid);
+      break;
     case 2: launch_kernel<2>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid); break;
     case 4: launch_kernel<4>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid); break;
     case 8: launch_kernel<8>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid); break;
@@ -1048,6 +1059,7 @@ struct Plan {
   int sym = 0;  // 1: the symmetric kernel (tiles I <= J), C row blocks per item
   int C = 16;
   int req = 0;  // the chunk request this plan was made from
+  int emu = 0;  // exponentials per 32 on the FMA pipe (one right-hand side)
 };
 
 // The tile plan: column chunks per row tile from the wave-balance rule, or
@@ -1079,11 +1091,13 @@ size_t smem_for(int kv, int a_res, int ns, int x3) {
 // ------------------------------------------------------------ autotuner --
 // Per problem shape (row tiles, column tiles, K-blocks, RHS bucket, operand
 // format) the tuner times the fused product under each candidate plan --
-// column chunks per row tile x ring stages -- and keeps the fastest in a
-// process-wide table, so each shape is timed once per process.  Plans that
-// would need more than 227 KiB of shared memory are skipped.  The chunk
-// count changes the order of the FP32 partial sums, so a tuned product can
-// differ from the default one in the last bits.
+// column chunks per row tile x ring stages x (one RHS) exponentials per 32
+// on the FMA pipe, and (one RHS, d <= 64) the symmetric kernel's item length
+// x ring stages -- and keeps the fastest in a process-wide table, so each
+// shape is timed once per process.  Plans that would need more than 227 KiB
+// of shared memory are skipped.  The chunk count changes the order of the
+// FP32 partial sums, so a tuned product can differ from the default one in
+// the last bits.
 struct TuneKey {
   int n_rt, n_ct, nkb, kv, fmt;
   bool operator<(const TuneKey& o) const {
@@ -1091,7 +1105,7 @@ struct TuneKey {
   }
 };
 struct Tuned {
-  int req, ns, sym, C;
+  int req, ns, sym, C, emu;
   float ms;
 };
 std::mutex g_tune_mu;
@@ -1194,7 +1208,7 @@ void run_fused(TcState& t, cudaStream_t st, TcOperand& op, const Plan& pl, int s
   p.err = (int*)t.err.p;
   const int items = pl.n_rt * pl.nchunk;
   const int grid = std::min(items, sm_count());
-  dispatch(pl.kv, st, op, p, grid);
+  dispatch(pl.kv, st, op, p, grid, pl.kv == 1 ? pl.emu : 0);
   const size_t total = (size_t)nr * k;
   tc_reduce_kernel<<<std::min(8 * sm_count(), (int)((total + 255) / 256)), 256, 0, st>>>(
       (const float*)t.part.p, pl.nchunk, op.n_pad, pl.kv, (const float*)op.ra.p, nr, k, V, ldv,
@@ -1225,9 +1239,13 @@ Tuned tune_shape(TcState& t, cudaStream_t st, TcOperand& op, int k, int fmt) {
   for (int r : reqs)
     for (int ns = 2; ns <= NS_MAX; ++ns) {
       if (smem_for(base.kv, a_res, ns, split) > SMEM_LIMIT) continue;
-      Plan pl = plan_for(op, k, 0, r);
-      pl.ns = ns;
-      plans.push_back(pl);
+      for (int emu : {0, 2, 4}) {
+        if (emu && base.kv != 1) continue;
+        Plan pl = plan_for(op, k, 0, r);
+        pl.ns = ns;
+        pl.emu = emu;
+        plans.push_back(pl);
+      }
     }
   if (sym_supported(op, k, split))
     for (int C : {8, 16, 32, 64})
@@ -1241,7 +1259,7 @@ Tuned tune_shape(TcState& t, cudaStream_t st, TcOperand& op, int k, int fmt) {
   cudaEvent_t e0, e1;
   KRR_CUDA(cudaEventCreate(&e0));
   KRR_CUDA(cudaEventCreate(&e1));
-  Tuned best{0, default_ns(a_res), 0, 16, 1e30f};
+  Tuned best{0, default_ns(a_res), 0, 16, 0, 1e30f};
   try {
     for (const Plan& pl : plans) {
       if (pl.sym)
@@ -1260,9 +1278,12 @@ Tuned tune_shape(TcState& t, cudaStream_t st, TcOperand& op, int k, int fmt) {
         if (rep > 0) ms = std::min(ms, m);   // the first run is a warm-up
       }
       if (getenv("KRR_TRACE"))
-        fprintf(stderr, "[krr] autotune n_pad=%d kp=%d k=%d fmt=%d: %s chunks=%d C=%d ns=%d %.4f ms\n",
-                op.n_pad, op.kp, k, fmt, pl.sym ? "sym" : "full", pl.nchunk, pl.C, pl.ns, ms);
-      if (ms < best.ms) best = Tuned{pl.req, pl.ns, pl.sym, pl.C, ms};
+        fprintf(stderr,
+                "[krr] autotune n_pad=%d kp=%d k=%d fmt=%d: %s chunks=%d C=%d ns=%d emu=%d "
+                "%.4f ms\n",
+                op.n_pad, op.kp, k, fmt, pl.sym ? "sym" : "full", pl.nchunk, pl.C, pl.ns, pl.emu,
+                ms);
+      if (ms < best.ms) best = Tuned{pl.req, pl.ns, pl.sym, pl.C, pl.emu, ms};
     }
   } catch (...) {
     cudaEventDestroy(e0);
@@ -1298,6 +1319,7 @@ Plan resolve_plan(TcState& t, cudaStream_t st, TcOperand& op, int k, int gemm2, 
       q.ns = it->second.ns;
       q.sym = it->second.sym;
       q.C = it->second.C;
+      q.emu = it->second.emu;
       return q;
     }
   }
@@ -1313,6 +1335,7 @@ Plan resolve_plan(TcState& t, cudaStream_t st, TcOperand& op, int k, int gemm2, 
   q.ns = tu.ns;
   q.sym = tu.sym;
   q.C = tu.C;
+  q.emu = tu.emu;
   return q;
 }
 
