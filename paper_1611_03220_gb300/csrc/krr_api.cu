@@ -656,8 +656,9 @@ void double_inner_ops(krr_handle* h, const float* X, int n, int ldx, int d, doub
     };
 }
 
-// Mixed precision: BF16 tensor-core inner PCG with FP32 vectors; outer
-// iterative refinement with the residual in HP arithmetic and FP64 vectors.
+// Mixed precision: FP16 (or BF16) tensor-core inner PCG with FP32 vectors;
+// outer iterative refinement with the residual in HP arithmetic and FP64
+// vectors.
 krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* matvecs) {
   cudaStream_t st = h->stream;
   const int n = a.n, k = a.k;
@@ -688,7 +689,7 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
   krr_status status = KRR_OK;
   int outer = 0;
   int remaining = a.o.max_iter;
-  // the inner arithmetic moves up a level (BF16 -> BF16x3 -> HP) once a
+  // the inner arithmetic moves up a level (FP16 -> BF16x3 -> HP) once a
   // correction contracts the residual by less than a half (see batched_mixed)
   int level = INNER_LOW;
   double rel_prev = 0.0;
@@ -840,7 +841,8 @@ void check_solve_args(const krr_opts& o, int n, int d, int ldx, double sigma, do
 }
 
 // The set-up of Algorithm 1 on device-resident operands: RFF features and the
-// preconditioner factors; for the mixed solve also the BF16 and HP operands.
+// preconditioner factors; for the mixed solve also the FP16 (or BF16) and HP
+// operands.
 void setup_impl(krr_handle* h, const float* Xd, int n, int d, int ldx, double sigma,
                 double lambda, const float* Wd, const float* bd, int s, const krr_opts& o) {
   cudaStream_t st = h->stream;
@@ -1051,7 +1053,7 @@ struct BItem {
   double rel[KRR_MAX_RHS] = {0};
   double yy[KRR_MAX_RHS] = {0};
   ColScale inv;
-  // mixed precision: the inner arithmetic moves up a level (BF16 -> BF16x3
+  // mixed precision: the inner arithmetic moves up a level (FP16 -> BF16x3
   // -> HP) when a correction contracts the residual by less than a half
   int level = INNER_LOW;
   double rel_prev = 0.0;

@@ -1138,7 +1138,7 @@ void tc_prepare(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int
   KRR_CUDA(cudaStreamSynchronize(st));
   if (!(mx <= 120.f))
     throw Error{KRR_EUNSUPPORTED,
-                "BF16 product: ||x - mean||^2 / (2 sigma^2) too large for the factored exp2 "
+                "tensor-core product: ||x - mean||^2 / (2 sigma^2) too large for the factored exp2 "
                 "(max " + std::to_string(mx) + " in log2 units); use FP32 or FP64"};
   t.sigma = sigma;
   t.rows_same = true;
@@ -1378,7 +1378,7 @@ void tc_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr, c
                int nc, int ldxc, int d, double sigma, double shift, const float* V, int k,
                int ldv, float* Q, int ldq, int split, int gemm2, int f16) {
   const bool same = (Xr == Xc && nr == nc && ldxr == ldxc);
-  if (!same) throw Error{KRR_EUNSUPPORTED, "BF16 product supports the training system (Xr == Xc)"};
+  if (!same) throw Error{KRR_EUNSUPPORTED, "tensor-core product supports the training system (Xr == Xc)"};
   if (f16 && (split || gemm2))
     throw Error{KRR_EUNSUPPORTED, "FP16 points: plain product only (no split, no second GEMM)"};
   if (split)

@@ -84,7 +84,7 @@ def test_hypergrad_matches_oracle(K, h, oracle_grads, k, precision):
     P, Y, Yte = _problem(k=k)
     ref = oracle_grads[k]
     # the mixed solve's residual is computed by the HP product (about 1e-13
-    # relative per kernel entry); its BF16 inner solves need more refinement
+    # relative per kernel entry); its FP16 inner solves need more refinement
     # steps for a tight tolerance
     tol, rel = (1e-10, 1e-6) if precision == "fp64" else (1e-9, 1e-5)
     opts = K.default_opts(tol=tol, max_iter=20000, precision=precision, max_outer=80)

@@ -1,6 +1,7 @@
-"""GPU parity of the tcgen05 BF16 fused kernel product and the mixed-precision solve.
+"""GPU parity of the tcgen05 fused kernel product and the mixed-precision solve.
 
-The BF16 product evaluates the Gaussian kernel of the BF16-rounded, centred,
+The BF16 product (and, with 11-bit significands, the FP16 one) evaluates the
+Gaussian kernel of the BF16-rounded, centred,
 scaled points xh = bf16(sqrt(log2(e))/sigma (x - mean)), i.e.
 K_ij = exp2(-||xh_i - xh_j||^2 / 2).  The oracle evaluates exactly that kernel
 on the same rounded points (rounding done on the CPU by torch, round to
