@@ -62,9 +62,11 @@ def parse():
                     help="short run for ncu: 'step' = one mixed and one FP32 solve of "
                          "--profile-iters PCG iterations with the host-driven loop (every "
                          "launch listed); otherwise 3 launches of that kernel product / apply")
-    ap.add_argument("--workload", type=int, default=None, choices=[3, 4, 5],
+    ap.add_argument("--workload", type=int, default=None, choices=[3, 4, 5, 6],
                     help="solve one other workload at full size (mixed, tol 1e-6) and print "
-                         "one JSON line of its results instead of the bench line")
+                         "one JSON line of its results instead of the bench line; 6 is the "
+                         "65,536-point workload with the random-features method and "
+                         "Algorithm 1 at several preconditioner ridges lambda_p")
     ap.add_argument("--profile-iters", type=int, default=12)
     ap.add_argument("--profile-k", type=int, default=1,
                     help="right-hand sides of the --profile bf16/fp16/hp/fp32 products")
@@ -275,6 +277,52 @@ def run_workload(args):
     h = K.Handle()
     opts = K.default_opts(tol=1e-6, precision="mixed", max_iter=60000, max_outer=60)
     out = {"workload": args.workload, "precision": "mixed", "tol": 1e-6}
+    if args.workload == 6:
+        # the random-features method (features as the model) against kernel
+        # ridge regression solved by Algorithm 1, and Algorithm 1 at larger
+        # preconditioner ridges (Table 2's lambda_p)
+        P = ks.make_config(2, m=M_TEST)
+        X, W, b, Y, Xte = dev(P.X), dev(P.W), dev(P.b), dev(P.Y), dev(P.Xte)
+        Yte = P.Yte
+        Wf = torch.empty((P.s, 1), dtype=torch.float64, device="cuda")
+        Fr = torch.empty((M_TEST, 1), dtype=torch.float64, device="cuda")
+        K.krr_rfm_fit(h, X, W, b, P.lam, Y, Wf)   # warm-up (allocations)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        K.krr_rfm_fit(h, X, W, b, P.lam, Y, Wf)
+        torch.cuda.synchronize()
+        t_fit = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        K.krr_rfm_predict(h, Xte, W, b, Wf, Fr)
+        torch.cuda.synchronize()
+        t_pred = time.perf_counter() - t0
+        fr = Fr.cpu().numpy()
+        sweep = []
+        fk = None
+        for lp in (P.lam, 1e-2, 1.0):
+            Cc = torch.zeros((P.n, 1), dtype=torch.float64, device="cuda")
+            o = K.default_opts(tol=1e-6, precision="mixed", max_iter=60000, max_outer=60,
+                               lambda_p=lp)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = K.krr_pcg_solve(h, X, P.sigma, P.lam, W, b, Y, Cc, o, check=False)
+            torch.cuda.synchronize()
+            sweep.append({"lambda_p": lp, "s": time.perf_counter() - t0, "iters": r["iters"][0],
+                          "outer_steps": r["outer_steps"], "status": r["status"],
+                          "rel_res": r["rel_res"][0]})
+            if fk is None:
+                Fk = torch.empty((M_TEST, 1), dtype=torch.float64, device="cuda")
+                K.krr_predict(h, X, Xte, P.sigma, Cc, Fk, "fp32")
+                fk = Fk.cpu().numpy()
+        rmse = lambda f: float(np.sqrt(np.mean((f - Yte) ** 2)))
+        out.update({"n": P.n, "d": P.d, "s": P.s, "lambda": P.lam, "m": M_TEST,
+                    "rfm_fit_s": t_fit, "rfm_predict_s": t_pred,
+                    "heldout_rmse_rfm": rmse(fr), "heldout_rmse_krr": rmse(fk),
+                    "rfm_vs_krr_rel": float(np.linalg.norm(fr - fk) / np.linalg.norm(fk)),
+                    "pcg_lambda_p": sweep})
+        h.close()
+        print(json.dumps(out))
+        return
     if args.workload == 4:
         probs = ks.make_uneven()
         items, cs = [], []
@@ -455,6 +503,19 @@ def run_ours(args, rank, world, local):
                           "iters": rc["iters"][0], "outer_steps": rc["outer_steps"],
                           "rel_res_fp64_check": rc["rel_res"][0]}
 
+    # --------------------- Algorithm 1 with a larger preconditioner ridge ---
+    # (Table 2's lambda_p; the timed headline keeps lambda_p = lambda)
+    Ct = torch.zeros_like(Y)
+    ot = K.default_opts(tol=P.tol, precision="mixed", max_iter=20000, max_outer=60, lambda_p=1.0)
+    flush.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rt = K.krr_pcg_solve(h, X, P.sigma, P.lam, W, b, Y, Ct, ot, check=False)
+    torch.cuda.synchronize()
+    tuned = {"lambda_p": 1.0, "ms": (time.perf_counter() - t0) * 1e3, "status": rt["status"],
+             "iters": rt["iters"][0], "outer_steps": rt["outer_steps"],
+             "rel_res_fp64_check": rt["rel_res"][0]}
+
     # ------------------------------------------------ end to end (host) ----
     Xh, Yh, Wh, bh = P.X, P.Y, P.W, P.b
     Xteh = P.Xte
@@ -485,7 +546,7 @@ def run_ours(args, rank, world, local):
                       "outer_steps": rep["outer_steps"], "matvecs": rep["matvecs"],
                       "rel_res_fp64": rep["rel_res"][0], "ms_setup": rep["ms_setup"],
                       "ms_solve": rep["ms_solve"], "step_ms_all": times},
-            "fp32": fp32, "plain_cg": plain_cg, "kernel_matvec": mv, "roofline": roofline,
+            "fp32": fp32, "plain_cg": plain_cg, "pcg_lambda_p_1": tuned, "kernel_matvec": mv, "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

@@ -245,6 +245,34 @@ krr_status krr_pcg_solve_batched(krr_handle* h, const krr_problem* probs, int np
                                  const krr_opts* opts, krr_report* reps);
 
 /*
+ * Random-features method (Section 2.2: the random Fourier features used as
+ * the model instead of as a preconditioner): the ridge regression in feature
+ * space
+ *   w = (Z^T Z + lambda I_s)^-1 Z^T Y,   Z = sqrt(2/s) cos(X W + b),
+ * computed with the preconditioner's set-up (FP32 Z, FP64 Gram and Cholesky
+ * of Algorithm 1, with lambda_p = lambda) and the first half of its apply
+ * (Z^T Y, then L^-1 and L^-T).  By the push-through identity its predictions
+ * at the training points are those of kernel ridge regression with the
+ * approximate kernel Z Z^T.  X: n x d (ldx) FP32; W: d x s, b: s FP32;
+ * Y: n x k double (ldy); Wf: s x k double (ldw) out.  Host or device
+ * pointers.  Replaces the handle's preconditioner factors.  Errors:
+ * KRR_EINVAL (sizes, lambda <= 0), KRR_ECHOL (Gram not positive definite).
+ */
+krr_status krr_rfm_fit(krr_handle* h, const float* X, int n, int d, int ldx,
+                       const float* W, const float* b, int s, double lambda,
+                       const double* Y, int k, int ldy, double* Wf, int ldw);
+
+/*
+ * The random-features predictor F = phi(Xte) Wf with
+ * phi(x) = sqrt(2/s) cos(x W + b): Xte m x d (ldx) FP32, W and b as for
+ * krr_rfm_fit, Wf s x k double (ldw), F m x k double (ldf); FP64 sums over
+ * the s features.  Host or device pointers.
+ */
+krr_status krr_rfm_predict(krr_handle* h, const float* Xte, int m, int d, int ldx,
+                           const float* W, const float* b, int s, const double* Wf,
+                           int k, int ldw, double* F, int ldf);
+
+/*
  * Predictor f(x) = sum_i c_i k(x_i, x) (Section 1) at m held-out points:
  *   F = K(Xte, Xtr) C.  Xtr: n x d (ldxtr), Xte: m x d (ldxte) FP32,
  * C: n x k double (ldc), F: m x k double (ldf); host or device pointers

@@ -24,6 +24,10 @@ Sketching and Preconditioning"):
                                  true relative residual (Section 5).
 * ``krr_pcg_solve``           -- Algorithm 1 end to end.
 * ``predict``                 -- f(x) = sum_i c_i k(x_i, x), Section 1.
+* ``rfm_fit/rfm_predict``     -- the random-features method: ridge regression on
+                                 the features of Section 2.2,
+                                 w = (Z^T Z + lambda I)^-1 Z^T y by Cholesky of
+                                 the s x s Gram matrix, f(x) = phi(x)^T w.
 * ``kernel_dlogsigma``        -- D o K, the derivative of K in log sigma.
 * ``hypergrad``               -- gradient of a held-out MSE with respect to
                                  log sigma and log lambda (not in the paper;
@@ -45,7 +49,7 @@ __all__ = [
     "sqdist_direct", "gaussian_kernel", "kernel_matrix_system", "direct_solve",
     "rff_features", "gram", "precond_setup", "precond_apply", "pcg",
     "krr_pcg_solve", "predict", "kernel_matvec_blocked", "true_rel_residual",
-    "lanczos_kappa", "hypergrad", "heldout_loss",
+    "lanczos_kappa", "hypergrad", "heldout_loss", "rfm_fit", "rfm_predict",
 ]
 
 
@@ -304,6 +308,24 @@ def krr_pcg_solve(X, Y, sigma: float, lam: float, W, b, lam_p: float | None = No
 def predict(Xtr, Xte, C, sigma: float) -> np.ndarray:
     """f(x) = sum_i c_i k(x_i, x) at each held-out point (Section 1)."""
     return gaussian_kernel(Xte, Xtr, sigma) @ np.asarray(C, np.float64).reshape(len(Xtr), -1)
+
+
+# ------------------------------------------------- random-features method ---
+
+def rfm_fit(X, W, b, lam: float, Y) -> np.ndarray:
+    """w = (Z^T Z + lambda I_s)^-1 Z^T Y with Z = rff_features(X, W, b) (Section 2.2's
+    features as the model: ridge regression in feature space), by Cholesky of G."""
+    Z = rff_features(X, W, b)
+    G = gram(Z, lam)
+    L = np.linalg.cholesky(G)
+    rhs = Z.T @ np.asarray(Y, np.float64).reshape(Z.shape[0], -1)
+    u = sla.solve_triangular(L, rhs, lower=True)
+    return sla.solve_triangular(L.T, u, lower=False)
+
+
+def rfm_predict(Xte, W, b, w) -> np.ndarray:
+    """f(x) = phi(x)^T w with phi the random Fourier features of Section 2.2."""
+    return rff_features(Xte, W, b) @ np.asarray(w, np.float64)
 
 
 # ------------------------------------------------------------- gradient ---

@@ -79,6 +79,8 @@ _SIGS = {
     "krr_pcg_solve_batched": (_i, [_vp, C.POINTER(krr_problem), _i, C.POINTER(krr_opts),
                                    C.POINTER(krr_report)]),
     "krr_predict": (_i, [_vp, _vp, _i, _i, _vp, _i, _i, _i, _d, _vp, _i, _i, _vp, _i, _i]),
+    "krr_rfm_fit": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _i, _d, _vp, _i, _i, _vp, _i]),
+    "krr_rfm_predict": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _i, _vp, _i, _i, _vp, _i]),
     "krr_kernel_matvec_fp64_noalloc": (_i, [_vp, _i, _i, _vp, _i, _i, _i, _d, _d, _vp, _i, _i,
                                             _vp, _i, _vp]),
     "krr_kernel_dsigma_matvec": (_i, [_vp, _vp, _i, _i, _vp, _i, _i, _i, _d, _vp, _i, _i, _vp,
@@ -293,6 +295,24 @@ def krr_predict(h: Handle, Xtr, Xte, sigma: float, Cc, F, precision="fp64"):
     h._check(_lib.krr_predict(h.ptr, _ptr(Xtr), n, _ld(Xtr), _ptr(Xte), m, _ld(Xte), d,
                               float(sigma), _ptr(Cc), k, _ld(Cc), _ptr(F), _ld(F), prec))
     return F
+
+
+def krr_rfm_fit(h: Handle, X, W, b, lam: float, Y, Wf):
+    """Random-features ridge solution Wf = (Z^T Z + lam I)^-1 Z^T Y into Wf (s x k)."""
+    n, d = X.shape
+    s = W.shape[1]
+    k = Y.shape[1]
+    h._check(_lib.krr_rfm_fit(h.ptr, _ptr(X), n, d, _ld(X), _ptr(W), _ptr(b), s, float(lam),
+                              _ptr(Y), k, _ld(Y), _ptr(Wf), _ld(Wf)))
+
+
+def krr_rfm_predict(h: Handle, Xte, W, b, Wf, F):
+    """F = phi(Xte) Wf, the random-features predictor."""
+    m, d = Xte.shape
+    s = W.shape[1]
+    k = Wf.shape[1]
+    h._check(_lib.krr_rfm_predict(h.ptr, _ptr(Xte), m, d, _ld(Xte), _ptr(W), _ptr(b), s,
+                                  _ptr(Wf), k, _ld(Wf), _ptr(F), _ld(F)))
 
 
 def krr_kernel_dsigma_matvec(h: Handle, Xr, Xc, sigma: float, V, Q, precision="fp64"):

@@ -1716,6 +1716,70 @@ krr_status krr_predict(krr_handle* h, const float* Xtr, int n, int ldxtr, const 
   });
 }
 
+krr_status krr_rfm_fit(krr_handle* h, const float* X, int n, int d, int ldx, const float* W,
+                       const float* b, int s, double lambda, const double* Y, int k, int ldy,
+                       double* Wf, int ldw) {
+  return guard(h, [&]() -> krr_status {
+    KRR_REQUIRE(X && W && b && Y && Wf, "rfm_fit: null pointer");
+    KRR_REQUIRE(n > 0 && d > 0 && s > 0 && k >= 1 && k <= KRR_MAX_RHS, "rfm_fit: bad sizes");
+    KRR_REQUIRE(ldx >= d && ldy >= k && ldw >= k, "rfm_fit: bad leading dims");
+    KRR_REQUIRE(lambda > 0.0 && std::isfinite(lambda), "rfm_fit: lambda must be > 0");
+    cudaStream_t st = h->stream;
+    const float* Xd = (const float*)stage_in(h, X, (size_t)n * ldx * sizeof(float), "X");
+    const float* Wd = (const float*)stage_in(h, W, (size_t)d * s * sizeof(float), "W");
+    const float* bd = (const float*)stage_in(h, b, (size_t)s * sizeof(float), "b");
+    const double* Yd = (const double*)stage_in(h, Y, (size_t)n * ldy * sizeof(double), "Y");
+    // features, then the preconditioner set-up with lambda_p = lambda (FP32 Z):
+    // G = Z^T Z + lambda I, L L^T = G, L^-1
+    float* Z = wsT<float>(h, "rff_Z", (size_t)n * s);
+    launch_rff(st, Xd, n, d, ldx, Wd, bd, s, Z, s);
+    precond_setup_impl(h, Z, n, s, s, lambda, KRR_APPLY_ZL, 0);
+    double* t1 = wsT<double>(h, "ap_t1", (size_t)s * k);
+    double* t2 = wsT<double>(h, "ap_t2", (size_t)s * k);
+    double* part = wsT<double>(h, "ap_part", apply_part_elems(n, s, k));
+    launch_ginv_zt(st, h->pc, Yd, k, ldy, t1, t2, part);
+    ColScale one;
+    for (int c = 0; c < KRR_MAX_RHS; ++c) one.v[c] = 1.0;
+    const bool w_host = !on_device(Wf);
+    double* Wd_out = w_host ? wsT<double>(h, "rfm_w", (size_t)s * ldw) : Wf;
+    launch_convert<double, double>(st, t1, s, k, k, Wd_out, ldw, one);
+    if (w_host)
+      KRR_CUDA(cudaMemcpyAsync(Wf, Wd_out, (size_t)s * ldw * sizeof(double),
+                               cudaMemcpyDeviceToHost, st));
+    if (precond_error(h)) throw Error{KRR_ETIMEOUT, "rfm_fit: a streamed pass hit its wait limit"};
+    return KRR_OK;
+  });
+}
+
+krr_status krr_rfm_predict(krr_handle* h, const float* Xte, int m, int d, int ldx,
+                           const float* W, const float* b, int s, const double* Wf, int k,
+                           int ldw, double* F, int ldf) {
+  return guard(h, [&]() -> krr_status {
+    KRR_REQUIRE(Xte && W && b && Wf && F, "rfm_predict: null pointer");
+    KRR_REQUIRE(m > 0 && d > 0 && s > 0 && k >= 1 && k <= KRR_MAX_RHS, "rfm_predict: bad sizes");
+    KRR_REQUIRE(ldx >= d && ldw >= k && ldf >= k, "rfm_predict: bad leading dims");
+    cudaStream_t st = h->stream;
+    const float* Xd = (const float*)stage_in(h, Xte, (size_t)m * ldx * sizeof(float), "rXte");
+    const float* Wd = (const float*)stage_in(h, W, (size_t)d * s * sizeof(float), "W");
+    const float* bd = (const float*)stage_in(h, b, (size_t)s * sizeof(float), "b");
+    const double* wd = (const double*)stage_in(h, Wf, (size_t)s * ldw * sizeof(double), "rW");
+    ColScale one;
+    for (int c = 0; c < KRR_MAX_RHS; ++c) one.v[c] = 1.0;
+    double* wc = wsT<double>(h, "rfm_wc", (size_t)s * k);
+    launch_convert<double, double>(st, wd, s, k, ldw, wc, k, one);
+    float* Zte = wsT<float>(h, "rfm_Zte", (size_t)m * s);
+    launch_rff(st, Xd, m, d, ldx, Wd, bd, s, Zte, s);
+    const bool f_host = !on_device(F);
+    double* Fd = f_host ? wsT<double>(h, "rfm_F", (size_t)m * ldf) : F;
+    launch_feature_gemv(st, Zte, m, s, wc, k, Fd, ldf);
+    if (f_host) {
+      KRR_CUDA(cudaMemcpyAsync(F, Fd, (size_t)m * ldf * sizeof(double), cudaMemcpyDeviceToHost, st));
+      KRR_CUDA(cudaStreamSynchronize(st));
+    }
+    return KRR_OK;
+  });
+}
+
 krr_status krr_kernel_dsigma_matvec(krr_handle* h, const float* Xr, int nr, int ldxr,
                                     const float* Xc, int nc, int ldxc, int d, double sigma,
                                     const double* V, int k, int ldv, double* Q, int ldq,

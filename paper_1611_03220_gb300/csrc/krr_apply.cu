@@ -677,7 +677,7 @@ ApplyPlan plan(int n, int s, int k) {
 
 template <int BF16, typename T, typename ACC, int KV>
 void apply_zl(cudaStream_t st, const Precond& pc, const ApplyPlan& pl, const T* R, int k, int ldr,
-              T* Zo, int ldo, double* t1, double* t2, void* part) {
+              T* Zo, int ldo, double* t1, double* t2, void* part, bool ginv_only = false) {
   const int n = pc.n, s = pc.s;
   const int vec = (s % 8 == 0) ? 1 : 0;
   int* err = reinterpret_cast<int*>(pc.err.p);
@@ -712,6 +712,7 @@ void apply_zl(cudaStream_t st, const Precond& pc, const ApplyPlan& pl, const T* 
   KRR_CHECK_LAUNCH();
   trmv_kernel<1, KV><<<tb, AT, 0, st>>>(reinterpret_cast<const double*>(pc.LinvT.p), s, t2, k, t1);
   KRR_CHECK_LAUNCH();
+  if (ginv_only) return;  // t1 = G^-1 Z^T R (the random-features solution)
   if (stream_zw) {
     auto kw = zw_stream_kernel<BF16, T, ACC, KV>;
     KRR_CUDA(cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -732,11 +733,37 @@ void apply_zl(cudaStream_t st, const Precond& pc, const ApplyPlan& pl, const T* 
 
 template <typename T, typename ACC, int KV>
 void apply_zl_kv(cudaStream_t st, const Precond& pc, const ApplyPlan& pl, const T* R, int k,
-                 int ldr, T* Zo, int ldo, double* t1, double* t2, void* part) {
+                 int ldr, T* Zo, int ldo, double* t1, double* t2, void* part,
+                 bool ginv_only = false) {
   if (pc.z_bf16)
-    apply_zl<1, T, ACC, KV>(st, pc, pl, R, k, ldr, Zo, ldo, t1, t2, part);
+    apply_zl<1, T, ACC, KV>(st, pc, pl, R, k, ldr, Zo, ldo, t1, t2, part, ginv_only);
   else
-    apply_zl<0, T, ACC, KV>(st, pc, pl, R, k, ldr, Zo, ldo, t1, t2, part);
+    apply_zl<0, T, ACC, KV>(st, pc, pl, R, k, ldr, Zo, ldo, t1, t2, part, ginv_only);
+}
+
+// F[i, c] = sum_b Zf[i, b] w[b, c] (FP64 sums): one warp per row.
+template <int KV>
+__global__ void __launch_bounds__(AT)
+feature_gemv_kernel(const float* __restrict__ Zf, int m, int s, const double* __restrict__ w,
+                    int k, double* __restrict__ F, int ldf) {
+  const int row = (blockIdx.x * AT + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (row >= m) return;
+  double acc[KV];
+#pragma unroll
+  for (int c = 0; c < KV; ++c) acc[c] = 0.0;
+  const float* zr = Zf + (size_t)row * s;
+  for (int b = lane; b < s; b += 32) {
+    const double z = (double)zr[b];
+#pragma unroll
+    for (int c = 0; c < KV; ++c)
+      if (c < k) acc[c] = fma(z, w[(size_t)b * k + c], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < KV; ++c) {
+    double v = acc[c];
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0 && c < k) F[(size_t)row * ldf + c] = v;
+  }
 }
 
 }  // namespace
@@ -745,6 +772,34 @@ size_t apply_part_elems(int n, int s, int k) {
   // in doubles (large enough for either accumulator type)
   ApplyPlan p = plan<double>(n, s, k);
   return (size_t)p.nchunk * s * p.kv;
+}
+
+void launch_ginv_zt(cudaStream_t st, const Precond& pc, const double* R, int k, int ldr,
+                    double* t1, double* t2, double* part) {
+  if (pc.form != KRR_APPLY_ZL) throw Error{KRR_EINVAL, "G^-1 Z^T r needs the ZL factors"};
+  const ApplyPlan pl = plan<double>(pc.n, pc.s, k);
+  switch (pl.kv) {
+    case 1: apply_zl_kv<double, double, 1>(st, pc, pl, R, k, ldr, nullptr, 0, t1, t2, part, true); break;
+    case 2: apply_zl_kv<double, double, 2>(st, pc, pl, R, k, ldr, nullptr, 0, t1, t2, part, true); break;
+    case 4: apply_zl_kv<double, double, 4>(st, pc, pl, R, k, ldr, nullptr, 0, t1, t2, part, true); break;
+    case 8: apply_zl_kv<double, double, 8>(st, pc, pl, R, k, ldr, nullptr, 0, t1, t2, part, true); break;
+    case 12: apply_zl_kv<double, double, 12>(st, pc, pl, R, k, ldr, nullptr, 0, t1, t2, part, true); break;
+    default: apply_zl_kv<double, double, 16>(st, pc, pl, R, k, ldr, nullptr, 0, t1, t2, part, true); break;
+  }
+}
+
+void launch_feature_gemv(cudaStream_t st, const float* Zf, int m, int s, const double* w, int k,
+                         double* F, int ldf) {
+  const int blocks = (int)(((size_t)m * 32 + AT - 1) / AT);
+  switch (kv_of(k)) {
+    case 1: feature_gemv_kernel<1><<<blocks, AT, 0, st>>>(Zf, m, s, w, k, F, ldf); break;
+    case 2: feature_gemv_kernel<2><<<blocks, AT, 0, st>>>(Zf, m, s, w, k, F, ldf); break;
+    case 4: feature_gemv_kernel<4><<<blocks, AT, 0, st>>>(Zf, m, s, w, k, F, ldf); break;
+    case 8: feature_gemv_kernel<8><<<blocks, AT, 0, st>>>(Zf, m, s, w, k, F, ldf); break;
+    case 12: feature_gemv_kernel<12><<<blocks, AT, 0, st>>>(Zf, m, s, w, k, F, ldf); break;
+    default: feature_gemv_kernel<16><<<blocks, AT, 0, st>>>(Zf, m, s, w, k, F, ldf); break;
+  }
+  KRR_CHECK_LAUNCH();
 }
 
 template <typename T>

@@ -139,6 +139,13 @@ void launch_form_u(cudaStream_t st, const double* Linv, const void* Zs, int bf16
 // R, Zo: n x k with leading dimension ldr / ldo, element type T (float or double).
 // t1, t2: s*k doubles of scratch; part: apply_part_elems doubles of scratch.
 size_t apply_part_elems(int n, int s, int k);
+// t1 = G^-1 Z^T R (s x k, ld k) with the ZL factors: the first half of the
+// apply, which is the random-features ridge solution when R = Y.
+void launch_ginv_zt(cudaStream_t st, const Precond& pc, const double* R, int k, int ldr,
+                    double* t1, double* t2, double* part);
+// F = Zf w: Zf m x s FP32 (ld s), w s x k double (ld k), F m x k (ldf); FP64 sums.
+void launch_feature_gemv(cudaStream_t st, const float* Zf, int m, int s, const double* w, int k,
+                         double* F, int ldf);
 template <typename T>
 void launch_apply(cudaStream_t st, const Precond& pc, const T* R, int k, int ldr, T* Zo,
                   int ldo, double* t1, double* t2, double* part);

@@ -256,6 +256,39 @@ def test_predict_at_training_points():
     np.testing.assert_allclose(F, P.Y - P.lam * C, rtol=1e-9, atol=1e-10)
 
 
+def test_rfm_push_through_identity():
+    """The random-features fit seen at the training points is kernel ridge
+    regression with the approximate kernel Z Z^T: Z (Z^T Z + lam I)^-1 Z^T y =
+    (Z Z^T)(Z Z^T + lam I)^-1 y.  The right side is an n x n solve, a different
+    route from the oracle's s x s Cholesky."""
+    P = ks.make_config(1, n=300, s=40)
+    Z = O.rff_features(P.X, P.W, P.b)
+    w = O.rfm_fit(P.X, P.W, P.b, 0.05, P.Y)
+    Kt = Z @ Z.T
+    c = np.linalg.solve(Kt + 0.05 * np.eye(300), P.Y)
+    np.testing.assert_allclose(O.rfm_predict(P.X, P.W, P.b, w), Kt @ c, rtol=1e-9, atol=1e-10)
+    # and the normal equations' residual is orthogonal to the features
+    r = P.Y - Z @ w
+    np.testing.assert_allclose(Z.T @ r, 0.05 * w, rtol=1e-8, atol=1e-10)
+
+
+def test_rfm_converges_to_kernel_ridge_regression():
+    """With s growing, Z Z^T -> K (Section 2.2), so the random-features predictor
+    approaches the exact kernel ridge regression predictor of Eq. (1)."""
+    P = ks.make_config(1, n=200)
+    rng = _rng(5)
+    C = O.direct_solve(P.X, P.Y, P.sigma, 0.1)
+    f_exact = O.predict(P.X, P.X[:50], C, P.sigma)
+    errs = []
+    for s in (32, 256, 2048):
+        W = rng.standard_normal((P.X.shape[1], s)) / P.sigma
+        b = rng.uniform(0.0, 2.0 * math.pi, s)
+        w = O.rfm_fit(P.X, W, b, 0.1, P.Y)
+        errs.append(np.linalg.norm(O.rfm_predict(P.X[:50], W, b, w) - f_exact)
+                    / np.linalg.norm(f_exact))
+    assert errs[2] < errs[1] < errs[0] and errs[2] < 0.1, errs
+
+
 def test_kernel_dlogsigma_central_differences():
     """D o K against Richardson-extrapolated central differences of K in log sigma."""
     rng = np.random.default_rng(31)
