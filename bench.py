@@ -543,6 +543,7 @@ def run_ours(args, rank, world, local):
             "data": "synthetic",
             "config": bench_config(P, n, world),
             "solve": {"status": rep["status"], "iters": rep["iters"][0],
+                      "kappa_estimate": rep["kappa"][0],
                       "outer_steps": rep["outer_steps"], "matvecs": rep["matvecs"],
                       "rel_res_fp64": rep["rel_res"][0], "ms_setup": rep["ms_setup"],
                       "ms_solve": rep["ms_solve"], "step_ms_all": times},

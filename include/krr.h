@@ -104,6 +104,13 @@ typedef struct {
   double ms_setup;                  /* features + Gram + Cholesky + factors  */
   double ms_solve;                  /* PCG (and refinement)                  */
   double ms_total;
+  double kappa[KRR_MAX_RHS];        /* Lanczos estimate of cond(M^-1 A) per  */
+                                    /* column from the CG coefficients of    */
+                                    /* its first 4096 steps (the largest     */
+                                    /* over a solve's inner loops; 0: none)  */
+  double rel_res_rec[KRR_MAX_RHS];  /* relative residual the last loop's     */
+                                    /* recurrence reached (in units of ||y|| */
+                                    /* for refined solves)                   */
 } krr_report;
 
 typedef struct krr_handle krr_handle;

@@ -44,14 +44,16 @@ class krr_report(C.Structure):
     _fields_ = [("status", C.c_int), ("k", C.c_int), ("iters", C.c_int * KRR_MAX_RHS),
                 ("rel_res", C.c_double * KRR_MAX_RHS), ("outer_steps", C.c_int),
                 ("matvecs", C.c_int), ("ms_setup", C.c_double), ("ms_solve", C.c_double),
-                ("ms_total", C.c_double)]
+                ("ms_total", C.c_double), ("kappa", C.c_double * KRR_MAX_RHS),
+                ("rel_res_rec", C.c_double * KRR_MAX_RHS)]
 
     def as_dict(self) -> dict:
         k = self.k
         return {"status": STATUS.get(self.status, self.status), "k": k,
                 "iters": list(self.iters[:k]), "rel_res": list(self.rel_res[:k]),
                 "outer_steps": self.outer_steps, "matvecs": self.matvecs,
-                "ms_setup": self.ms_setup, "ms_solve": self.ms_solve, "ms_total": self.ms_total}
+                "ms_setup": self.ms_setup, "ms_solve": self.ms_solve, "ms_total": self.ms_total,
+                "kappa": list(self.kappa[:k]), "rel_res_rec": list(self.rel_res_rec[:k])}
 
 
 class krr_problem(C.Structure):

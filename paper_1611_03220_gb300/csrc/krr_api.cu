@@ -253,9 +253,56 @@ struct LoopOut {
   int iters[KRR_MAX_RHS];
   double rr[KRR_MAX_RHS];
   double yy[KRR_MAX_RHS];
+  double kappa[KRR_MAX_RHS];   // Lanczos estimate of cond(M^-1 A) (0: none)
   int flags;
   int iter;
 };
+
+// Eigenvalues of the symmetric tridiagonal (d, e) below x: the Sturm count
+// (the number of negative pivots of T - x I).
+int sturm_count(const std::vector<double>& d, const std::vector<double>& e, double x) {
+  int cnt = 0;
+  double q = 1.0;
+  for (size_t i = 0; i < d.size(); ++i) {
+    const double off = i ? e[i - 1] * e[i - 1] : 0.0;
+    q = d[i] - x - (i ? off / q : 0.0);
+    if (q == 0.0) q = -1e-300;   // step past an exact zero pivot
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// Condition estimate of the preconditioned operator from m PCG steps: the
+// Lanczos tridiagonal of CG (diagonal 1/a_0, 1/a_j + b_{j-1}/a_{j-1},
+// off-diagonal sqrt(b_j)/a_j) and its extreme eigenvalues by bisection on
+// the Sturm count.  0 when fewer than two steps were taken or the estimate
+// is not positive.
+double lanczos_kappa_est(const std::vector<double>& a, const std::vector<double>& b) {
+  const size_t m = a.size();
+  if (m < 2) return 0.0;
+  std::vector<double> d(m), e(m - 1);
+  for (size_t j = 0; j < m; ++j) {
+    if (!(a[j] > 0.0)) return 0.0;
+    d[j] = 1.0 / a[j] + (j ? b[j - 1] / a[j - 1] : 0.0);
+    if (j + 1 < m) e[j] = std::sqrt(std::max(b[j], 0.0)) / a[j];
+  }
+  double lo = d[0], hi = d[0];
+  for (size_t j = 0; j < m; ++j) {
+    const double r = (j ? std::fabs(e[j - 1]) : 0.0) + (j + 1 < m ? std::fabs(e[j]) : 0.0);
+    lo = std::min(lo, d[j] - r);
+    hi = std::max(hi, d[j] + r);
+  }
+  auto kth = [&](int k) {  // the k-th smallest eigenvalue (1-based)
+    double l = lo, u = hi;
+    for (int it = 0; it < 200 && u - l > 1e-15 * std::max(std::fabs(l), std::fabs(u)); ++it) {
+      const double mid = 0.5 * (l + u);
+      if (sturm_count(d, e, mid) >= k) u = mid; else l = mid;
+    }
+    return 0.5 * (l + u);
+  };
+  const double emin = kth(1), emax = kth((int)m);
+  return emin > 0.0 ? emax / emin : 0.0;
+}
 
 // One PCG solve's operands: the loop vectors (n x k, ld = k), the right-hand
 // side whose norm sets the stopping test, and the two operators.
@@ -280,8 +327,10 @@ template <typename T>
 void pcg_begin(krr_handle* h, const PcgSpec<T>& S) {
   cudaStream_t st = h->stream;
   double* part = wsT<double>(h, "cg_part", cg_part_elems(S.n, S.k));
+  double* hist = wsT<double>(h, "cg_hist", (size_t)CG_HIST_CAP * 2 * KRR_MAX_RHS);
   matvec_reserve(h, S.n, S.k, S.prec);
-  launch_cg_init<T>(st, h->sc, S.Ytol, S.ldy, S.r, S.n, S.k, S.tol, S.max_iter, part);
+  launch_cg_init<T>(st, h->sc, S.Ytol, S.ldy, S.r, S.n, S.k, S.tol, S.max_iter, part, hist,
+                    CG_HIST_CAP);
   if (S.apply)
     S.apply(st, S.r, S.z);
   else
@@ -322,6 +371,24 @@ void pcg_finish(krr_handle* h, int k, LoopOut* out) {
   }
   out->flags = h->sc_host->flags;
   out->iter = h->sc_host->iter;
+  // the condition estimate from the recorded alpha, beta
+  const int m = std::min(out->iter, h->sc_host->hist_cap);
+  for (int c = 0; c < KRR_MAX_RHS; ++c) out->kappa[c] = 0.0;
+  if (m >= 2 && h->sc_host->hist) {
+    std::vector<double> hh((size_t)m * 2 * KRR_MAX_RHS);
+    KRR_CUDA(cudaMemcpyAsync(hh.data(), h->sc_host->hist, hh.size() * sizeof(double),
+                             cudaMemcpyDeviceToHost, st));
+    KRR_CUDA(cudaStreamSynchronize(st));
+    for (int c = 0; c < k; ++c) {
+      const int mc = std::min(out->iters[c], m);
+      std::vector<double> a(mc), b(mc);
+      for (int j = 0; j < mc; ++j) {
+        a[j] = hh[((size_t)j * 2) * KRR_MAX_RHS + c];
+        b[j] = hh[((size_t)j * 2 + 1) * KRR_MAX_RHS + c];
+      }
+      out->kappa[c] = lanczos_kappa_est(a, b);
+    }
+  }
 }
 
 template <typename T>
@@ -522,6 +589,7 @@ krr_status solve_plain(krr_handle* h, const SolveArgs& a, int prec, krr_report* 
     ap = [&](cudaStream_t s2, const T* R, T* Zo) { apply_precond<T>(h, s2, R, k, k, Zo, k); };
   int restarts = 0;
   int total_iters[KRR_MAX_RHS] = {0};
+  double kmax[KRR_MAX_RHS] = {0};
   krr_status status = KRR_OK;
   LoopOut lo;
   int remaining = a.o.max_iter;
@@ -531,7 +599,11 @@ krr_status solve_plain(krr_handle* h, const SolveArgs& a, int prec, krr_report* 
     S.x = x; S.r = r; S.p = p; S.z = z; S.q = q;
     S.tol = a.o.tol; S.max_iter = remaining; S.matvec = mv; S.apply = ap; S.prec = prec;
     pcg_loop<T>(h, S, a.o.use_graph != 0, &lo, matvecs);
-    for (int c = 0; c < k; ++c) total_iters[c] += lo.iters[c];
+    for (int c = 0; c < k; ++c) {
+      total_iters[c] += lo.iters[c];
+      kmax[c] = std::max(kmax[c], lo.kappa[c]);
+      if (rep) rep->rel_res_rec[c] = lo.yy[c] > 0 ? std::sqrt(lo.rr[c] / lo.yy[c]) : 0.0;
+    }
     remaining -= lo.iter;
     if (lo.flags & FLAG_NAN) {
       status = KRR_ENAN;
@@ -572,7 +644,10 @@ krr_status solve_plain(krr_handle* h, const SolveArgs& a, int prec, krr_report* 
   }
   launch_convert<T, double>(st, x, n, k, k, a.C, a.ldc, one);
   if (rep) {
-    for (int c = 0; c < k; ++c) rep->iters[c] = total_iters[c];
+    for (int c = 0; c < k; ++c) {
+      rep->iters[c] = total_iters[c];
+      rep->kappa[c] = kmax[c];
+    }
     rep->outer_steps = restarts;
   }
   return status;
@@ -698,6 +773,7 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
   // direction (residual replacement) unless a step was taken back
   bool keep_ok = false;
   double norm_prev[KRR_MAX_RHS] = {0};
+  double kmax[KRR_MAX_RHS] = {0};
   for (;;) {
     double rr[KRR_MAX_RHS];
     host_colnorm2<double>(h, Rd, n, k, k, rr);
@@ -800,7 +876,14 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
       pcg_loop<double>(h, S, a.o.use_graph != 0, &lo, matvecs);
       if (!(lo.flags & FLAG_NAN)) launch_axpy_d<double>(st, S.x, n, k, k, Cd, k, inv);
     }
-    for (int c = 0; c < k; ++c) total_iters[c] += lo.iters[c];
+    for (int c = 0; c < k; ++c) {
+      total_iters[c] += lo.iters[c];
+      kmax[c] = std::max(kmax[c], lo.kappa[c]);
+      // the inner system is r / ||r||: its recursive residual in units of ||y||
+      if (rep)
+        rep->rel_res_rec[c] =
+            (lo.yy[c] > 0 ? std::sqrt(lo.rr[c] / lo.yy[c]) : 0.0) * rel_saved[c];
+    }
     remaining -= lo.iter;
     KRR_TRACE("mixed: inner solve %d iterations, flags %d", lo.iter, lo.flags);
     // a NaN in the inner solve leaves Cd unchanged; the next pass takes the
@@ -814,7 +897,10 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
     for (int c = 0; c < k; ++c) rep->rel_res[c] = rel[c];
   launch_convert<double, double>(st, Cd, n, k, k, a.C, a.ldc, one);
   if (rep) {
-    for (int c = 0; c < k; ++c) rep->iters[c] = total_iters[c];
+    for (int c = 0; c < k; ++c) {
+      rep->iters[c] = total_iters[c];
+      rep->kappa[c] = kmax[c];
+    }
     rep->outer_steps = outer;
   }
   return status;
@@ -1058,6 +1144,8 @@ struct BItem {
   int level = INNER_LOW;
   double rel_prev = 0.0;
   double rel_saved[KRR_MAX_RHS] = {0};
+  double kappa[KRR_MAX_RHS] = {0};   // largest condition estimate over its loops
+  double rrec[KRR_MAX_RHS] = {0};    // last loop's recursive residual (units of ||y||)
 };
 
 double max_rel(const BItem& it) {
@@ -1152,7 +1240,11 @@ void batched_plain(krr_handle* h, std::vector<BItem>& B, const krr_opts& o, int 
       pending[i] = false;
       LoopOut lo;
       pcg_finish(g, it.k, &lo);
-      for (int c = 0; c < it.k; ++c) it.iters[c] += lo.iters[c];
+      for (int c = 0; c < it.k; ++c) {
+        it.iters[c] += lo.iters[c];
+        it.kappa[c] = std::max(it.kappa[c], lo.kappa[c]);
+        it.rrec[c] = lo.yy[c] > 0 ? std::sqrt(lo.rr[c] / lo.yy[c]) : 0.0;
+      }
       it.remaining -= lo.iter;
       it.matvecs += lo.iter;
       if (lo.flags & FLAG_NAN) {
@@ -1317,7 +1409,11 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
       krr_handle* g = it.sub;
       LoopOut lo;
       pcg_finish(g, it.k, &lo);
-      for (int c = 0; c < it.k; ++c) it.iters[c] += lo.iters[c];
+      for (int c = 0; c < it.k; ++c) {
+        it.iters[c] += lo.iters[c];
+        it.kappa[c] = std::max(it.kappa[c], lo.kappa[c]);
+        it.rrec[c] = (lo.yy[c] > 0 ? std::sqrt(lo.rr[c] / lo.yy[c]) : 0.0) * it.rel_saved[c];
+      }
       it.remaining -= lo.iter;
       it.matvecs += lo.iter;
       const size_t nk = (size_t)it.n * it.k;
@@ -1666,6 +1762,8 @@ krr_status krr_pcg_solve_batched(krr_handle* h, const krr_problem* probs, int np
         for (int c = 0; c < it.k; ++c) {
           r.iters[c] = it.iters[c];
           r.rel_res[c] = it.rel[c];
+          r.kappa[c] = it.kappa[c];
+          r.rel_res_rec[c] = it.rrec[c];
         }
         r.outer_steps = it.outer;
         r.matvecs = it.matvecs;

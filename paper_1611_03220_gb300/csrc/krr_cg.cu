@@ -84,7 +84,8 @@ __device__ __forceinline__ bool bad(double x) { return isnan(x) || isinf(x); }
 template <typename T>
 __global__ void __launch_bounds__(CT)
 cg_init_kernel(CgScalars* sc, const double* __restrict__ Y, int ldy, const T* __restrict__ R,
-               int n, int k, double tol, int max_iter, double* part) {
+               int n, int k, double tol, int max_iter, double* part, double* hist,
+               int hist_cap) {
   double v[KRR_MAX_RHS], tot[KRR_MAX_RHS];
 #pragma unroll
   for (int c = 0; c < KRR_MAX_RHS; ++c) v[c] = 0.0;
@@ -102,6 +103,8 @@ cg_init_kernel(CgScalars* sc, const double* __restrict__ Y, int ldy, const T* __
   sc->iter = 0;
   sc->max_iter = max_iter;
   sc->flags = 0;
+  sc->hist = hist;
+  sc->hist_cap = hist ? hist_cap : 0;
   int any = 0;
   for (int c = 0; c < KRR_MAX_RHS; ++c) {
     if (c < k) {
@@ -267,6 +270,7 @@ cg_alpha_kernel(CgScalars* sc, const T* __restrict__ P, const T* __restrict__ Q,
       }
     }
     sc->alpha[c] = a;
+    if (sc->iter < sc->hist_cap) sc->hist[((size_t)sc->iter * 2) * KRR_MAX_RHS + c] = a;
   }
 }
 
@@ -335,6 +339,7 @@ cg_rz_kernel(CgScalars* sc, const T* __restrict__ R, const T* __restrict__ Z, in
       sc->rz[c] = tot[c];
     }
     sc->beta[c] = b;
+    if (sc->iter < sc->hist_cap) sc->hist[((size_t)sc->iter * 2 + 1) * KRR_MAX_RHS + c] = b;
   }
 }
 
@@ -490,9 +495,10 @@ size_t cg_part_elems(int n, int k) {
 
 template <typename T>
 void launch_cg_init(cudaStream_t st, CgScalars* sc, const double* Y, int ldy, const T* R, int n,
-                    int k, double tol, int max_iter, double* part) {
+                    int k, double tol, int max_iter, double* part, double* hist, int hist_cap) {
   (void)R;
-  cg_init_kernel<T><<<cg_blocks(n), CT, 0, st>>>(sc, Y, ldy, R, n, k, tol, max_iter, part);
+  cg_init_kernel<T><<<cg_blocks(n), CT, 0, st>>>(sc, Y, ldy, R, n, k, tol, max_iter, part, hist,
+                                                 hist_cap);
   KRR_CHECK_LAUNCH();
 }
 
@@ -602,7 +608,7 @@ void launch_colnorm2(cudaStream_t st, const T* a, int n, int k, int lda, double*
 
 #define KRR_CG_INST(T)                                                                        \
   template void launch_cg_init<T>(cudaStream_t, CgScalars*, const double*, int, const T*, int, \
-                                  int, double, int, double*);                                 \
+                                  int, double, int, double*, double*, int);                   \
   template void launch_cg_rz_first<T>(cudaStream_t, CgScalars*, const T*, const T*, T*, int,  \
                                       int, double*);                                          \
   template void launch_cg_restart<T>(cudaStream_t, CgScalars*, const T*, const T*, T*, int,   \

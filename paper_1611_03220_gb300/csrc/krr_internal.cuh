@@ -75,7 +75,12 @@ struct CgScalars {
   int k;
   int run;                     // 1 while the loop should execute another iteration
   unsigned int counter[8];     // last-block-done counters for reductions
+  double* hist;                // alpha, beta of the first hist_cap iterations
+  int hist_cap;                //   ([iter][2][KRR_MAX_RHS]; null: not recorded)
 };
+
+// Rows of the alpha/beta record kept for the condition estimate.
+constexpr int CG_HIST_CAP = 4096;
 
 enum : int { FLAG_BREAKDOWN = 1, FLAG_NAN = 2, FLAG_CAP = 4 };
 
@@ -157,7 +162,8 @@ struct ColScale {
 size_t cg_part_elems(int n, int k);
 template <typename T>
 void launch_cg_init(cudaStream_t st, CgScalars* sc, const double* Y, int ldy, const T* R, int n,
-                    int k, double tol, int max_iter, double* part);
+                    int k, double tol, int max_iter, double* part, double* hist = nullptr,
+                    int hist_cap = 0);
 template <typename T>
 void launch_cg_rz_first(cudaStream_t st, CgScalars* sc, const T* R, const T* Z, T* P, int n,
                         int k, double* part);
