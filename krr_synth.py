@@ -83,6 +83,20 @@ def rff_draw(seed: int, d: int, s: int, sigma: float) -> tuple[np.ndarray, np.nd
     return W, b
 
 
+def tensorsketch_draw(seed: int, d: int, q: int, s: int) -> tuple[np.ndarray, np.ndarray]:
+    """Draw the hash and sign tables of a degree-q TensorSketch (Section 2.2).
+
+    Returns ``h`` (q x d int32, entries uniform on [0, s)) and ``g`` (q x d int8,
+    entries uniform on {-1, +1}).  Fully random tables are k-wise independent
+    for every k, so they meet the 3-wise (hashes) and 4-wise (signs)
+    requirements.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h = rng.integers(0, s, size=(q, d)).astype(np.int32)
+    g = (2 * rng.integers(0, 2, size=(q, d)) - 1).astype(np.int8)
+    return h, g
+
+
 def _cfg1(n: int, s: int | None) -> Problem:
     rng = np.random.Generator(np.random.PCG64(1001))
     d = 8

@@ -28,6 +28,20 @@ Sketching and Preconditioning"):
                                  the features of Section 2.2,
                                  w = (Z^T Z + lambda I)^-1 Z^T y by Cholesky of
                                  the s x s Gram matrix, f(x) = phi(x)^T w.
+* ``poly_kernel``             -- k(x, z) = (gamma x^T z + c)^q, the second
+                                 kernel of the experiments (Section 6).
+* ``countsketch``             -- z_i = sum over j with h(j) = i of g(j) x_j
+                                 (Section 2.2).
+* ``tensorsketch_features``   -- phi(x) = S v_q(x) for the degree-q TensorSketch
+                                 of Section 2.2, by enumerating the d^q monomials
+                                 (readings: the composite hash is taken mod s,
+                                 printed "mod m", and the t-th sign factor reads
+                                 i_t, printed i_1 in the second factor); the
+                                 offset c enters as an extra coordinate sqrt(c)
+                                 and gamma as a factor sqrt(gamma) on x, so that
+                                 E phi(x)^T phi(z) = (gamma x^T z + c)^q.
+* ``krr_poly_pcg_solve``      -- Algorithm 1 for the polynomial kernel with the
+                                 TensorSketch preconditioner.
 * ``kernel_dlogsigma``        -- D o K, the derivative of K in log sigma.
 * ``hypergrad``               -- gradient of a held-out MSE with respect to
                                  log sigma and log lambda (not in the paper;
@@ -50,6 +64,7 @@ __all__ = [
     "rff_features", "gram", "precond_setup", "precond_apply", "pcg",
     "krr_pcg_solve", "predict", "kernel_matvec_blocked", "true_rel_residual",
     "lanczos_kappa", "hypergrad", "heldout_loss", "rfm_fit", "rfm_predict",
+    "poly_kernel", "countsketch", "tensorsketch_features", "krr_poly_pcg_solve",
 ]
 
 
@@ -326,6 +341,77 @@ def rfm_fit(X, W, b, lam: float, Y) -> np.ndarray:
 def rfm_predict(Xte, W, b, w) -> np.ndarray:
     """f(x) = phi(x)^T w with phi the random Fourier features of Section 2.2."""
     return rff_features(Xte, W, b) @ np.asarray(w, np.float64)
+
+
+# ------------------------------------ polynomial kernel and TensorSketch ---
+
+def poly_kernel(Xa, Xb, gamma: float, c: float, q: int) -> np.ndarray:
+    """K_ij = (gamma a_i^T b_j + c)^q (the polynomial kernel of Section 6)."""
+    G = np.asarray(Xa, np.float64) @ np.asarray(Xb, np.float64).T
+    return (gamma * G + c) ** q
+
+
+def countsketch(X, h, g, s: int) -> np.ndarray:
+    """CountSketch of each row of X (Section 2.2): z_i = sum_{j: h(j) = i} g(j) x_j."""
+    X = np.asarray(X, np.float64).reshape(-1, len(h))
+    Z = np.zeros((X.shape[0], s))
+    for j in range(len(h)):
+        Z[:, int(h[j])] += float(g[j]) * X[:, j]
+    return Z
+
+
+def _augment(X, gamma: float, c: float) -> np.ndarray:
+    """[sqrt(gamma) x, sqrt(c)]: its degree-q monomial products give (gamma x^T z + c)^q."""
+    X = np.asarray(X, np.float64)
+    return np.hstack([math.sqrt(gamma) * X, np.full((X.shape[0], 1), math.sqrt(c))])
+
+
+def tensorsketch_features(X, h, g, s: int, gamma: float = 1.0, c: float = 0.0) -> np.ndarray:
+    """phi(x) = S v_q(x~) with x~ = [sqrt(gamma) x, sqrt(c)] (Section 2.2).
+
+    h, g: q x d~ hash and sign tables (d~ = d + 1 when c > 0, else d).  Column
+    (i_1..i_q) of S is G e_H with H = (h_1(i_1) + ... + h_q(i_q)) mod s and
+    G = g_1(i_1) ... g_q(i_q); v_q(x) lists the products x_{i_1} ... x_{i_q}.
+    The d~^q monomials are enumerated one multi-index at a time.
+    """
+    Xa = _augment(X, gamma, c) if c > 0.0 else math.sqrt(gamma) * np.asarray(X, np.float64)
+    h = np.asarray(h)
+    g = np.asarray(g)
+    q, dd = h.shape
+    if Xa.shape[1] != dd:
+        raise ValueError("hash tables must cover every (augmented) coordinate")
+    Z = np.zeros((Xa.shape[0], s))
+    idx = [0] * q
+    for _ in range(dd ** q):
+        H = sum(int(h[t, idx[t]]) for t in range(q)) % s
+        G = 1.0
+        mono = np.ones(Xa.shape[0])
+        for t in range(q):
+            G *= float(g[t, idx[t]])
+            mono = mono * Xa[:, idx[t]]
+        Z[:, H] += G * mono
+        # next multi-index (i_1 fastest)
+        t = 0
+        while t < q:
+            idx[t] += 1
+            if idx[t] < dd:
+                break
+            idx[t] = 0
+            t += 1
+    return Z
+
+
+def krr_poly_pcg_solve(X, Y, gamma: float, c: float, q: int, lam: float, h, g, s: int,
+                       lam_p: float | None = None, tol: float = 1e-8,
+                       max_iter: int = 1000) -> dict:
+    """Algorithm 1 for the polynomial kernel: the TensorSketch features build the
+    preconditioner Z Z^T + lambda_p I (Woodbury form), PCG runs on K + lambda I."""
+    X = np.asarray(X, np.float64)
+    Z = tensorsketch_features(X, h, g, s, gamma, c)
+    P = precond_setup(Z, lam if lam_p is None else lam_p)
+    A = poly_kernel(X, X, gamma, c, q)
+    A[np.diag_indices_from(A)] += lam
+    return pcg(lambda V: A @ V, lambda R: precond_apply(P, R), Y, tol, max_iter)
 
 
 # ------------------------------------------------------------- gradient ---

@@ -289,6 +289,88 @@ def test_rfm_converges_to_kernel_ridge_regression():
     assert errs[2] < errs[1] < errs[0] and errs[2] < 0.1, errs
 
 
+def test_poly_kernel_bruteforce():
+    """(gamma x.z + c)^q against scalar loops."""
+    rng = _rng(21)
+    X = rng.standard_normal((5, 3))
+    Kp = O.poly_kernel(X, X[:4], 0.7, 1.3, 3)
+    for i in range(5):
+        for j in range(4):
+            dot = sum(X[i, t] * X[j, t] for t in range(3))
+            assert math.isclose(Kp[i, j], (0.7 * dot + 1.3) ** 3, rel_tol=1e-13, abs_tol=1e-13)
+
+
+def test_countsketch_is_a_sparse_matrix_product():
+    """CountSketch equals the s x d matrix with column j = g(j) e_{h(j)} (Section 2.2)."""
+    h, g = ks.tensorsketch_draw(3, 7, 1, 5)
+    X = _rng(22).standard_normal((4, 7))
+    Cm = np.zeros((5, 7))
+    for j in range(7):
+        Cm[h[0, j], j] = g[0, j]
+    np.testing.assert_allclose(O.countsketch(X, h[0], g[0], 5), X @ Cm.T, rtol=0, atol=1e-14)
+
+
+def test_tensorsketch_explicit_matrix_tiny():
+    """phi(x) = S v_q(x~) with S and v_q built as explicit arrays from the definition."""
+    import itertools
+    q, d, s, gam, c = 2, 3, 5, 0.5, 2.0
+    h, g = ks.tensorsketch_draw(4, d + 1, q, s)
+    X = _rng(23).standard_normal((3, d))
+    Xa = np.hstack([math.sqrt(gam) * X, np.full((3, 1), math.sqrt(c))])
+    cols = list(itertools.product(range(d + 1), repeat=q))
+    S = np.zeros((s, len(cols)))
+    V = np.zeros((3, len(cols)))
+    for m, ii in enumerate(cols):
+        S[sum(int(h[t, ii[t]]) for t in range(q)) % s, m] += np.prod([g[t, ii[t]] for t in range(q)])
+        V[:, m] = np.prod([Xa[:, ii[t]] for t in range(q)], axis=0)
+    np.testing.assert_allclose(O.tensorsketch_features(X, h, g, s, gam, c), V @ S.T,
+                               rtol=1e-12, atol=1e-12)
+
+
+def test_tensorsketch_equals_convolved_countsketches():
+    """Pagh's identity: the TensorSketch is the circular convolution of the q
+    CountSketches, computed here through the FFT (a different route)."""
+    q, d, s, gam, c = 3, 6, 32, 0.8, 0.5
+    h, g = ks.tensorsketch_draw(5, d + 1, q, s)
+    X = _rng(24).standard_normal((4, d))
+    Xa = np.hstack([math.sqrt(gam) * X, np.full((4, 1), math.sqrt(c))])
+    prod = np.ones((4, s), dtype=complex)
+    for t in range(q):
+        prod *= np.fft.fft(O.countsketch(Xa, h[t], g[t], s), axis=1)
+    ref = np.real(np.fft.ifft(prod, axis=1))
+    np.testing.assert_allclose(O.tensorsketch_features(X, h, g, s, gam, c), ref,
+                               rtol=1e-10, atol=1e-10)
+
+
+def test_tensorsketch_inner_products_are_unbiased():
+    """E phi(x).phi(z) = (gamma x.z + c)^q over the hash draws (Section 2.2)."""
+    q, d, s, gam, c = 2, 4, 16, 0.5, 1.0
+    rng = _rng(25)
+    x, z = rng.standard_normal((2, d))
+    exact = (gam * x @ z + c) ** q
+    vals = []
+    for seed in range(3000):
+        h, g = ks.tensorsketch_draw(10_000 + seed, d + 1, q, s)
+        F = O.tensorsketch_features(np.vstack([x, z]), h, g, s, gam, c)
+        vals.append(F[0] @ F[1])
+    vals = np.asarray(vals)
+    assert abs(vals.mean() - exact) <= 5.0 * vals.std() / math.sqrt(len(vals)), \
+        (vals.mean(), exact)
+
+
+def test_poly_pcg_matches_direct_solve():
+    """Algorithm 1 with the polynomial kernel and the TensorSketch preconditioner
+    reaches the direct solve of (K + lambda I) c = y."""
+    rng = _rng(26)
+    X = rng.standard_normal((150, 4)) / 2.0
+    Y = np.sin(X.sum(axis=1, keepdims=True))
+    h, g = ks.tensorsketch_draw(6, 5, 2, 64)
+    r = O.krr_poly_pcg_solve(X, Y, 0.5, 1.0, 2, 1e-2, h, g, 64, tol=1e-11, max_iter=500)
+    A = O.poly_kernel(X, X, 0.5, 1.0, 2) + 1e-2 * np.eye(150)
+    Cd = np.linalg.solve(A, Y)
+    np.testing.assert_allclose(r["x"], Cd, rtol=1e-7, atol=1e-9)
+
+
 def test_kernel_dlogsigma_central_differences():
     """D o K against Richardson-extrapolated central differences of K in log sigma."""
     rng = np.random.default_rng(31)
