@@ -261,9 +261,10 @@ krr_status krr_pcg_solve_batched(krr_handle* h, const krr_problem* probs, int np
  * (Z^T Y, then L^-1 and L^-T).  By the push-through identity its predictions
  * at the training points are those of kernel ridge regression with the
  * approximate kernel Z Z^T.  X: n x d (ldx) FP32; W: d x s, b: s FP32;
- * Y: n x k double (ldy); Wf: s x k double (ldw) out.  Host or device
- * pointers.  Replaces the handle's preconditioner factors.  Errors:
- * KRR_EINVAL (sizes, lambda <= 0), KRR_ECHOL (Gram not positive definite).
+ * Y: n x k double (ldy); Wf: s x k double (ldw) out; 0 < s <= n.  Host or
+ * device pointers.  Replaces the handle's preconditioner factors.  Errors:
+ * KRR_EINVAL (sizes, s > n, lambda <= 0), KRR_ECHOL (Gram not positive
+ * definite).
  */
 krr_status krr_rfm_fit(krr_handle* h, const float* X, int n, int d, int ldx,
                        const float* W, const float* b, int s, double lambda,

@@ -1822,6 +1822,7 @@ krr_status krr_rfm_fit(krr_handle* h, const float* X, int n, int d, int ldx, con
     KRR_REQUIRE(n > 0 && d > 0 && s > 0 && k >= 1 && k <= KRR_MAX_RHS, "rfm_fit: bad sizes");
     KRR_REQUIRE(ldx >= d && ldy >= k && ldw >= k, "rfm_fit: bad leading dims");
     KRR_REQUIRE(lambda > 0.0 && std::isfinite(lambda), "rfm_fit: lambda must be > 0");
+    KRR_REQUIRE(s <= n, "rfm_fit: need s <= n (the preconditioner set-up's Gram path)");
     cudaStream_t st = h->stream;
     const float* Xd = (const float*)stage_in(h, X, (size_t)n * ldx * sizeof(float), "X");
     const float* Wd = (const float*)stage_in(h, W, (size_t)d * s * sizeof(float), "W");

@@ -97,3 +97,8 @@ def test_rfm_rejects_bad_arguments(K, h):
         K.krr_rfm_fit(h, cuda(P.X), cuda(P.W), cuda(P.b), 0.0, cuda(P.Y), Wf)
     with pytest.raises(K.KrrError):
         K.krr_rfm_fit(h, cuda(P.X), cuda(P.W), cuda(P.b), -1.0, cuda(P.Y), Wf)
+    # more features than points: refused before any launch
+    Q = ks.make_config(1, n=100, s=128)
+    Wq = torch.empty((128, 1), dtype=torch.float64, device="cuda")
+    with pytest.raises(K.KrrError):
+        K.krr_rfm_fit(h, cuda(Q.X), cuda(Q.W), cuda(Q.b), 1.0, cuda(Q.Y), Wq)
