@@ -48,6 +48,7 @@ class krr_report(C.Structure):
                 ("rel_res_rec", C.c_double * KRR_MAX_RHS)]
 
     def as_dict(self) -> dict:
+        """The report's first k columns as plain Python values."""
         k = self.k
         return {"status": STATUS.get(self.status, self.status), "k": k,
                 "iters": list(self.iters[:k]), "rel_res": list(self.rel_res[:k]),
@@ -141,9 +142,11 @@ class Handle:
 
     @property
     def ptr(self):
+        """The ``krr_handle*`` to pass to the C functions."""
         return self._h
 
     def set_stream(self, stream=None):
+        """Bind the handle to ``stream`` (a torch stream; None: torch's current one)."""
         self._check(_lib.krr_set_stream(self._h, _stream_ptr(stream)))
 
     def set_autotune(self, on=True) -> int:
@@ -161,6 +164,7 @@ class Handle:
             raise KrrError(st, _lib.krr_last_error(self._h).decode())
 
     def close(self):
+        """Destroy the handle (synchronises its stream, frees its workspace)."""
         if self._h:
             _lib.krr_destroy(self._h)
             self._h = _vp()
@@ -179,6 +183,9 @@ class Handle:
 
 
 def default_opts(**kw) -> krr_opts:
+    """``krr_default_opts`` with the given fields overridden; ``precision`` and
+    ``inner_precision`` may be names ("fp64", "fp32", "mixed", "fp16", "bf16", ...),
+    ``apply_form`` "zl" or "u"."""
     o = krr_opts()
     _lib.krr_default_opts(C.byref(o))
     for k, v in kw.items():
@@ -225,6 +232,8 @@ def krr_kernel_matvec_fp64_noalloc(Xr, Xc, sigma: float, shift: float, V, Q, str
 
 
 def krr_precond_setup(h: Handle, Z, lambda_p: float, apply_form="zl", z_bf16: bool = False):
+    """Preconditioner set-up from the features Z (n x s float32): G = Z^T Z + lambda_p I,
+    its Cholesky factor and the factors of the apply form ("zl" or "u")."""
     n, s = Z.shape
     form = APPLY_FORM[apply_form] if isinstance(apply_form, str) else int(apply_form)
     h._check(_lib.krr_precond_setup(h.ptr, _ptr(Z), n, s, _ld(Z), float(lambda_p), form,
@@ -232,6 +241,7 @@ def krr_precond_setup(h: Handle, Z, lambda_p: float, apply_form="zl", z_bf16: bo
 
 
 def krr_precond_apply(h: Handle, R, Zout):
+    """Zout = (Z Z^T + lambda_p I)^-1 R by the Woodbury identity (R, Zout n x k float64)."""
     k = R.shape[1]
     h._check(_lib.krr_precond_apply(h.ptr, _ptr(R), k, _ld(R), _ptr(Zout), _ld(Zout)))
     return Zout
@@ -290,6 +300,7 @@ def krr_pcg_solve_batched(h: Handle, problems, opts: krr_opts | None = None,
 
 
 def krr_predict(h: Handle, Xtr, Xte, sigma: float, Cc, F, precision="fp64"):
+    """F = K(Xte, Xtr) Cc, the kernel ridge regression predictor at the rows of Xte."""
     n, d = Xtr.shape
     m = Xte.shape[0]
     k = Cc.shape[1]
