@@ -42,8 +42,9 @@ WORKLOAD = ("gaussian-mixture n=65536 d=64 (10 centres N(0,4I), unit spread), si
             "lambda=1e-4, s=2048 RFF, tol 1e-6, predict m=8192")
 M_TEST = 8192
 L2_FLUSH_BYTES = 512 << 20
-# DRAM bytes (read + write) of one tc_matvec_kernel<1> launch on FP16 points at n = 65536,
-# d = 64, from the ncu capture summarised in profiles/tc_matvec_kernel_n65536_d64.md
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one fused FP16 product
+# launch at n = 65536, d = 64, from an ncu capture of `bench.py --profile fp16`; ncu does
+# not run inside the bench, so the figure is carried here and applies to that size only.
 TC_DRAM_BYTES_N65536 = 8679168
 
 
@@ -57,6 +58,8 @@ def parse():
                     help="override n (smaller instance)")
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparator")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-c3", action="store_true",
+                    help="skip the d = 784, k = 10 product (workload 3's shape)")
     ap.add_argument("--profile", default=None,
                     choices=["step", "bf16", "fp16", "fp16sym", "hp", "fp32", "apply"],
                     help="short run for ncu: 'step' = one mixed and one FP32 solve of "
@@ -67,6 +70,8 @@ def parse():
                          "one JSON line of its results instead of the bench line; 6 is the "
                          "65,536-point workload with the random-features method and "
                          "Algorithm 1 at several preconditioner ridges lambda_p")
+    ap.add_argument("--oracle-config1", action="store_true",
+                    help="internal: time the oracle's Algorithm 1 on workload 1 and print it")
     ap.add_argument("--profile-iters", type=int, default=12)
     ap.add_argument("--profile-k", type=int, default=1,
                     help="right-hand sides of the --profile bf16/fp16/hp/fp32 products")
@@ -95,6 +100,18 @@ def bench_config(P, n: int, world: int) -> dict:
             "lambda": P.lam, "tol": P.tol, "m_predict": M_TEST,
             "l2": "flushed between steps (512 MiB write)",
             "parallelism": "replicas" if world > 1 else "single-gpu"}
+
+
+def tensor_peak_tflops() -> tuple[float, str]:
+    """Dense FP16/BF16 tensor peak for a kernel timed alone: the measured cuBLAS
+    BF16 burst figure when the measured-peaks file is present (FP16 runs at the
+    BF16 rate), else the fallback of 1,900 TFLOP/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = float(json.load(f)["bf16_tflops"])
+        return v, "of measured (cuBLAS BF16 burst; FP16 runs at the BF16 rate)"
+    except Exception:
+        return 1900.0, "of fallback (1.9 PFLOP/s BF16 burst)"
 
 
 def blas_threads() -> int:
@@ -163,57 +180,105 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------- oracle leg --
-def oracle_sample(P, rows: int, reps: int = 1) -> tuple[float, int]:
-    """Seconds for the FP64 oracle's kernel product on `rows` rows of the workload."""
+def oracle_product_seconds(P, rows: int) -> float:
+    """Seconds for one full FP64 oracle kernel product on this workload, timed on
+    `rows` rows (the blocked product is row-parallel, so time scales with rows)."""
     from oracle import krr_oracle as O
-    rng = np.random.default_rng(0)
-    V = rng.standard_normal((P.n, 1))
-    best = float("inf")
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        O.kernel_matvec_blocked(P.X[:rows], P.X, V, P.sigma)
-        best = min(best, time.perf_counter() - t0)
-    return best, blas_threads()
+    V = np.random.default_rng(0).standard_normal((P.n, 1))
+    t0 = time.perf_counter()
+    O.kernel_matvec_blocked(P.X[:rows], P.X, V, P.sigma)
+    return (time.perf_counter() - t0) * P.n / rows
 
 
-def cpu_baseline(P, matvecs: int, rows: int = 4096) -> dict:
-    t, cores = oracle_sample(P, rows)
-    per_mv = t * P.n / rows
-    est_ms = per_mv * matvecs * 1e3
+def oracle_alg1(P) -> dict:
+    """The oracle's Algorithm 1 (RFF features, Woodbury preconditioner, FP64 PCG)
+    end to end on P, timed, with its own iteration count and true residual."""
+    from oracle import krr_oracle as O
+    t0 = time.perf_counter()
+    out = O.krr_pcg_solve(P.X, P.Y, P.sigma, P.lam, P.W, P.b, tol=P.tol, max_iter=5000)
+    t = time.perf_counter() - t0
+    res = float(O.true_rel_residual(P.X, P.Y, out["x"], P.sigma, P.lam)[0])
+    return {"n": P.n, "s": P.s, "seconds": t, "iters": int(out["iters"][0]), "rel_res": res,
+            "status": out["status"]}
+
+
+def oracle_direct(P) -> dict:
+    from oracle import krr_oracle as O
+    t0 = time.perf_counter()
+    C = O.direct_solve(P.X, P.Y, P.sigma, P.lam)
+    t = time.perf_counter() - t0
+    return {"n": P.n, "seconds": t,
+            "rel_res": float(O.true_rel_residual(P.X, P.Y, C, P.sigma, P.lam)[0])}
+
+
+def oracle_one_core_config1() -> dict | None:
+    """Workload 1 (n = 2,000) through the oracle's Algorithm 1 on one core: a
+    child process with every BLAS/OpenMP pool limited to one thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        p = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-config1"],
+                           env=env, capture_output=True, text=True, timeout=600)
+        return json.loads(p.stdout.strip().splitlines()[-1])
+    except Exception as e:  # the baseline is reported, not required
+        return {"error": str(e)[:200]}
+
+
+def cpu_baseline(P) -> dict:
+    """The FP64 oracle timed on the host cores (measured parts and one labelled
+    extrapolation to the benched size)."""
+    cores = blas_threads()
+    cfg1 = oracle_alg1(ks.make_config(1))
+    cfg1_one = oracle_one_core_config1()
+    P8 = ks.make_config(2, n=8192)          # same recipe, same W and b
+    alg8 = oracle_alg1(P8)
+    direct4 = oracle_direct(ks.make_config(2, n=4096))
+    rows = min(512, P.n)
+    t_mv = oracle_product_seconds(P, rows)
+    est_ms = alg8["iters"] * t_mv * 1e3
     return {"value": est_ms, "unit": "ms", "cores": cores, "kind": "oracle",
-            "sample": (f"FP64 oracle kernel product on {rows} of {P.n} rows "
-                       f"({t:.2f} s), scaled to a full product ({per_mv:.1f} s) times the "
-                       f"{matvecs} kernel products of the GPU solve")}
-
-
-# Kernel products of one Algorithm 1 solve of the bench workload to 1e-6 as the GPU run
-# counts them (its report's matvecs: 2,953 PCG iterations + 4 refinement residuals).
-REF_MATVECS = 2957
+            "sample": (f"extrapolated: the oracle's own Algorithm 1 iteration count on the "
+                       f"8,192-point instance ({alg8['iters']}) x one full {P.n}-point FP64 "
+                       f"product ({t_mv:.1f} s, timed on {rows} rows); iterations grow with n, "
+                       f"so this underestimates the full solve"),
+            "measured": {"config1_all_cores": cfg1, "config1_one_core": cfg1_one,
+                         "alg1_n8192": alg8, "direct_n4096": direct4,
+                         "full_product_s": t_mv, "full_product_rows_timed": rows}}
 
 
 def run_reference(args, rank, world):
-    """The oracle, timed on the host cores (rank 0 only; other ranks exit at once)."""
+    """The oracle, timed on the host cores (rank 0 only; other ranks exit at once).
+
+    One step = the oracle's Algorithm 1 end to end on a 2,048-point instance of
+    the benched workload (same recipe, same W and b) plus one full-size FP64
+    kernel product timed on 256 rows; the step's value scales the full-size
+    product time by the sample solve's own iteration count."""
     if rank != 0:
         return
     n = args.n or ks.CONFIGS[2]
     P = ks.make_config(2, n=n, m=M_TEST)
-    rows = min(1024, n)
-    matvecs = REF_MATVECS
-    times = []
+    Ps = ks.make_config(2, n=min(2048, n))
+    vals, last = [], None
     for i in range(args.warmup + args.steps):
-        t, cores = oracle_sample(P, rows)
+        alg = oracle_alg1(Ps)
+        t_mv = oracle_product_seconds(P, min(256, n))
         if i >= args.warmup:
-            times.append(t * P.n / rows * matvecs * 1e3)
-    v = statistics.mean(times)
-    sample = (f"FP64 oracle kernel product on {rows} of {n} rows per step, scaled to "
-              f"{matvecs} full products")
+            vals.append(alg["iters"] * t_mv * 1e3)
+            last = (alg, t_mv)
+    v = statistics.mean(vals)
+    alg, t_mv = last
+    cores = blas_threads()
+    sample = (f"extrapolated per step: oracle Algorithm 1 on a {Ps.n}-point instance "
+              f"({alg['seconds']:.2f} s, {alg['iters']} iterations, residual "
+              f"{alg['rel_res']:.1e}) x one full {n}-point FP64 product ({t_mv:.1f} s, timed "
+              f"on 256 rows)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": bench_config(P, n, world),
         "cpu_baseline": {"value": v, "unit": "ms", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "measured": {"alg1_sample": alg,
+                                                        "full_product_s": t_mv}},
         "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
@@ -450,31 +515,63 @@ def run_ours(args, rank, world, local):
     d_pad = 64 * math.ceil(P.d / 64)
     n_pad = 256 * math.ceil(n / 256)
     alg_flops = 2.0 * pairs * (P.d + 1)
-    ex2_rate = C_ms = None
+    # exp-bound roofline: the best measured rate of base-2 exponentials with the
+    # MUFU ex2 and the FMA-pipe polynomial running side by side, over splits
     import ctypes
     r = ctypes.c_double()
     kms = ctypes.c_double()
-    if K._lib.krr_bench_ex2(h.ptr, 4096, ctypes.byref(r), ctypes.byref(kms)) == 0:
-        ex2_rate = r.value
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mix = {}
+    for f in (0, 2, 4, 6, 8, 10, 12, 16):
+        if K._lib.krr_bench_ex2_mix(h.ptr, 2048, f, ctypes.byref(r), ctypes.byref(kms)) == 0:
+            mix[f] = r.value
+    best_f = max(mix, key=mix.get)
+    peak = mix[best_f]
     clk_mhz = clk.get("sm_mhz") or 2070.0
-    lanes = None
-    if ex2_rate:
-        lanes = 2 ** round(math.log2(ex2_rate / (sms * clk_mhz * 1e6)))
-    peak = (lanes or 16) * sms * 2070e6
     achieved = pairs / t_mv
     # algorithmic bytes of one product: the FP16 points once, w, and the row sums
     alg_bytes = n_pad * d_pad * 2 + n * 4 + n * 4
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
                 "unit": "Gexp/s", "frac": achieved / peak,
+                "frac_of_mufu_only": achieved / mix[0],
                 "traffic": TC_DRAM_BYTES_N65536 if n == 65536 and P.d == 64 else None,
-                "traffic_unit": "DRAM bytes per launch (ncu)", "alg_bytes": alg_bytes,
+                "traffic_unit": "DRAM bytes per launch (ncu capture of bench.py --profile fp16)",
+                "alg_bytes": alg_bytes,
                 "kernel": "tc_matvec_kernel (+ w/reduce helpers)",
-                "peak_basis": (f"{lanes or 16} MUFU ex2 lanes/SM/clk x {sms} SMs x 2070 MHz "
-                               f"(lanes from the ex2 probe: {ex2_rate and ex2_rate / 1e9:.0f} "
-                               f"Gexp/s at {clk_mhz:.0f} MHz)")}
+                "peak_basis": (f"measured: best combined MUFU ex2 + FMA-pipe polynomial exp2 "
+                               f"rate over splits ({best_f} of 32 on the FMA pipe), "
+                               f"152 SMs, clocks median {clk_mhz:.0f} MHz in the timed region"),
+                "exp2_rates_by_fma_per_32": {str(k): v / 1e9 for k, v in mix.items()}}
     mv = {"ms": t_mv * 1e3, "pairs_per_s": achieved, "alg_tflops": alg_flops / t_mv / 1e12,
           "tensor_tflops": 2.0 * n_pad * n_pad * d_pad / t_mv / 1e12}
+
+    # ------------- the tensor-bound product: workload 3's shape (d = 784, k = 10)
+    c3 = None
+    if n == ks.CONFIGS[2] and not args.no_c3:
+        P3 = ks.make_config(3)
+        X3 = torch.from_numpy(P3.X).to(dev)
+        V3 = torch.randn((P3.n, P3.k), dtype=torch.float32, device=dev)
+        Q3 = torch.empty_like(V3)
+        for _ in range(3):
+            K.krr_kernel_matvec(h, X3, X3, P3.sigma, P3.lam, V3, Q3, "fp16")
+        c3_ms = []
+        for _ in range(5):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            K.krr_kernel_matvec(h, X3, X3, P3.sigma, P3.lam, V3, Q3, "fp16")
+            e1.record(st)
+            e1.synchronize()
+            c3_ms.append(e0.elapsed_time(e1))
+        t3 = statistics.median(c3_ms) * 1e-3
+        fl3 = 2.0 * P3.n * P3.n * (P3.d + P3.k)
+        tpk, tpk_basis = tensor_peak_tflops()
+        c3 = {"workload": f"n={P3.n} d={P3.d} k={P3.k} sigma={P3.sigma} (FP16 points)",
+              "ms": t3 * 1e3, "alg_tflops": fl3 / t3 / 1e12,
+              "roofline": {"bound": "tensor", "achieved": fl3 / t3 / 1e12, "peak": tpk,
+                           "unit": "TFLOP/s", "frac": fl3 / t3 / 1e12 / tpk,
+                           "peak_basis": tpk_basis,
+                           "flops": "2 n^2 (d + k) per product"}}
+        del X3, V3, Q3
 
     # ------------------------------------------------ FP32 comparator ------
     fp32 = None
@@ -532,8 +629,13 @@ def run_ours(args, rank, world, local):
     d2h = Ch.nbytes + Fh.nbytes
 
     cpu = None
+    rel_res_oracle = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(P, rep["matvecs"])
+        # the headline solution's true residual recomputed by the FP64 oracle
+        from oracle import krr_oracle as O
+        rel_res_oracle = float(O.true_rel_residual(P.X, P.Y, C.cpu().numpy(), P.sigma,
+                                                   P.lam)[0])
+        cpu = cpu_baseline(P)
 
     if rank == 0:
         out = {
@@ -545,9 +647,11 @@ def run_ours(args, rank, world, local):
             "solve": {"status": rep["status"], "iters": rep["iters"][0],
                       "kappa_estimate": rep["kappa"][0],
                       "outer_steps": rep["outer_steps"], "matvecs": rep["matvecs"],
-                      "rel_res_fp64": rep["rel_res"][0], "ms_setup": rep["ms_setup"],
+                      "rel_res_fp64": rep["rel_res"][0], "rel_res_oracle": rel_res_oracle,
+                      "ms_setup": rep["ms_setup"],
                       "ms_solve": rep["ms_solve"], "step_ms_all": times},
             "fp32": fp32, "plain_cg": plain_cg, "pcg_lambda_p_1": tuned, "kernel_matvec": mv, "roofline": roofline,
+            "kernel_matvec_c3": c3,
             "cpu_baseline": cpu,
             "e2e": {"value": statistics.mean(e2e_ms), "unit": "ms", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -564,6 +668,9 @@ def run_ours(args, rank, world, local):
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.oracle_config1:
+        print(json.dumps(oracle_alg1(ks.make_config(1))))
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

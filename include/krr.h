@@ -383,6 +383,18 @@ long long krr_launch_count(void);
  */
 krr_status krr_bench_ex2(krr_handle* h, int iters, double* ex2_per_s, double* ms);
 
+/*
+ * Combined throughput of the two base-2 exponentials the fused products use:
+ * every thread runs 32 independent chains for `iters` steps, `fma_per_32` of
+ * them through the FMA-pipe polynomial and the rest through the MUFU
+ * ex2.approx, so both pipes work at once.  fma_per_32 is one of 0, 2, 4, 6,
+ * 8, 10, 12, 16, 32 (else KRR_EINVAL).  Writes exponentials per second to
+ * *exp2_per_s and the kernel time to *ms (may be NULL).  The best rate over
+ * the splits is the exp-bound roofline of the fused product.
+ */
+krr_status krr_bench_ex2_mix(krr_handle* h, int iters, int fma_per_32, double* exp2_per_s,
+                             double* ms);
+
 #ifdef __cplusplus
 }
 #endif

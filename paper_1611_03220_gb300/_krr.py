@@ -93,6 +93,7 @@ _SIGS = {
                            C.POINTER(krr_report)]),
     "krr_launch_count": (C.c_longlong, []),
     "krr_bench_ex2": (_i, [_vp, _i, C.POINTER(_d), C.POINTER(_d)]),
+    "krr_bench_ex2_mix": (_i, [_vp, _i, _i, C.POINTER(_d), C.POINTER(_d)]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)

@@ -1983,3 +1983,16 @@ extern "C" krr_status krr_bench_ex2(krr_handle* h, int iters, double* ex2_per_s,
     return KRR_OK;
   });
 }
+
+extern "C" krr_status krr_bench_ex2_mix(krr_handle* h, int iters, int fma_per_32,
+                                        double* exp2_per_s, double* ms) {
+  return guard(h, [&]() -> krr_status {
+    KRR_REQUIRE(iters > 0 && exp2_per_s, "bench_ex2_mix: iters > 0 and an output pointer");
+    KRR_REQUIRE(fma_per_32 == 0 || fma_per_32 == 2 || fma_per_32 == 4 || fma_per_32 == 6 ||
+                    fma_per_32 == 8 || fma_per_32 == 10 || fma_per_32 == 12 ||
+                    fma_per_32 == 16 || fma_per_32 == 32,
+                "bench_ex2_mix: fma_per_32 must be one of 0 2 4 6 8 10 12 16 32");
+    *exp2_per_s = bench_ex2_mix(h->stream, iters, fma_per_32, ms);
+    return KRR_OK;
+  });
+}

@@ -33,6 +33,8 @@ void capture_begin();
 long long capture_end();           // launches seen since capture_begin
 void add_launches(long long n);
 double bench_ex2(cudaStream_t st, int iters, double* ms_out);
+// Exponentials per second with fma_per_32 of every 32 on the FMA pipe.
+double bench_ex2_mix(cudaStream_t st, int iters, int fma_per_32, double* ms_out);
 #define KRR_CHECK_LAUNCH()            \
   do {                                \
     KRR_CUDA(cudaGetLastError());     \

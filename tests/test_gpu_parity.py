@@ -219,14 +219,21 @@ def test_pcg_host_buffers(K, h):
     assert O.true_rel_residual(P.X, P.Y, C, P.sigma, P.lam)[0] <= 1e-8
 
 
-def test_predict_matches_oracle(K, h):
-    P = ks.make_config(5, n=700, m=333, s=64)
-    rng = np.random.default_rng(1)
-    Cc = rng.standard_normal((700, 1))
-    F = torch.empty((333, 1), dtype=torch.float64, device="cuda")
-    K.krr_predict(h, dev(P.X), dev(P.Xte), P.sigma, dev(Cc), F, "fp64")
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("hp", 2e-12), ("fp32", 5e-5)])
+@pytest.mark.parametrize("n,m,k", [(700, 333, 1), (1100, 517, 3)])
+def test_predict_matches_oracle(K, h, prec, tol, n, m, k):
+    """f = K(X_te, X) c (Section 1) in each precision the entry point takes.  The
+    FP32 path rounds c to FP32 and runs the FP32 SIMT product (norm expansion,
+    expf), so its bound is the FP32 product's, 5e-5 of sum_j |K_ij||c_j|."""
+    P = ks.make_config(5, n=n, m=m, s=64)
+    rng = np.random.default_rng(n + k)
+    Cc = rng.standard_normal((n, k)) * 30.0
+    F = torch.full((m, k), float("nan"), dtype=torch.float64, device="cuda")
+    K.krr_predict(h, dev(P.X), dev(P.Xte), P.sigma, dev(Cc), F, prec)
     ref = O.predict(P.X, P.Xte, Cc, P.sigma)
-    assert np.all(np.abs(F.cpu().numpy() - ref) <= 1e-12 * kabs_v(P.Xte, P.X, P.sigma, Cc))
+    err = np.abs(F.cpu().numpy() - ref)
+    assert np.all(err <= tol * kabs_v(P.Xte, P.X, P.sigma, Cc)), float(
+        np.max(err / kabs_v(P.Xte, P.X, P.sigma, Cc)))
 
 
 # ------------------------------------------------------------- failures ---

@@ -7,7 +7,9 @@ keeps its partial sums in a fixed device array shared by every call, so the
 test runs it twice in a row on different inputs -- the second call must not
 see anything of the first -- and checks each result against the regular
 handle-based FP64 entry point on the same inputs, with the FP64 product's
-tolerance (1e-12 of sum_j |K_ij| |V_j|).  This file is collected last.
+tolerance (1e-12 of sum_j |K_ij| |V_j|).  One case fills the scratch array
+exactly, which forces the product down to a single column split.  This file
+is collected last.
 """
 import math
 
@@ -27,7 +29,9 @@ def test_noalloc_product_matches_regular_entry_point_twice():
     from oracle import krr_oracle as O
 
     rng = np.random.default_rng(2024)
-    cases = [(1000, 777, 37, 3, 0.0), (640, 640, 64, 1, 0.125)]
+    # the last case fills the scratch exactly (nr * k = 2^20 doubles), so the
+    # column split is cut to one partial per row and RHS
+    cases = [(1000, 777, 37, 3, 0.0), (640, 640, 64, 1, 0.125), (65536, 512, 4, 16, 0.0)]
     with K.Handle() as h:
         for nr, nc, d, k, shift in cases:
             Xr = rng.standard_normal((nr, d)).astype(np.float32)
