@@ -308,7 +308,7 @@ def run_profile(args):
     elif args.profile == "apply":
         Z = torch.empty((n, P.s), dtype=torch.float32, device="cuda")
         K.krr_rff_features(h, X, W, b, Z)
-        K.krr_precond_setup(h, Z, P.lam, "zl", z_bf16=True)
+        K.krr_precond_setup(h, Z, P.lam, "zl", z_format="bf16")
         R = torch.randn((n, 1), dtype=torch.float64, device="cuda")
         Zo = torch.empty_like(R)
         for _ in range(3):

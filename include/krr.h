@@ -71,6 +71,16 @@ typedef enum {
   KRR_APPLY_U = 1      /* z = (r - U^T U r) / lambda_p, U = L^-1 Z^T        */
 } krr_apply_form;
 
+/* How the handle stores the features Z of the preconditioner. */
+typedef enum {
+  KRR_Z_FP32 = 0,      /* FP32 copy; Gram accumulated in FP64 on the SIMT pipes */
+  KRR_Z_BF16 = 1,      /* BF16 copy; Gram of the rounded values, FP64 sums     */
+  KRR_Z_FIXED = 2      /* 7-bit fixed point: Z ~= 2^e Zs, Zs = q / 128 with     */
+                       /* q = clamp(rint(z 2^(7-e)), -127, 127) and 2^e the    */
+                       /* smallest power of two >= max |z|; the Gram of Zs is  */
+                       /* formed exactly on the tensor cores (integer sums)    */
+} krr_z_format;
+
 #define KRR_MAX_RHS 16
 
 typedef struct {
@@ -83,7 +93,9 @@ typedef struct {
   int use_graph;       /* 1: PCG loop as a CUDA-graph while node             */
   double inner_tol;    /* KRR_MIXED: inner PCG relative tolerance (0.03)     */
   int max_outer;       /* KRR_MIXED: refinement step cap                     */
-  int z_bf16;          /* store Z in BF16 (-1 auto: BF16 for BF16/MIXED)     */
+  int z_format;        /* krr_z_format of the preconditioner's features;     */
+                       /* -1 auto: KRR_Z_FIXED for KRR_MIXED (features and   */
+                       /* Gram on the tensor cores), else KRR_Z_FP32         */
   int warm_start;      /* 1: C holds x0 on entry                             */
   int inner_precision; /* KRR_MIXED: product of the inner PCG, KRR_FP16 or   */
                        /* KRR_BF16 (0: the default, KRR_FP16)                */
@@ -159,6 +171,19 @@ krr_status krr_rff_features(krr_handle* h, const float* X, int n, int d, int ldx
                             float* Z, int ldz);
 
 /*
+ * The same features on the tensor cores in the fixed-point form of
+ * KRR_Z_FIXED (the mixed solves' preconditioner): Zs (n x s, ldz >= s, BF16
+ * bit patterns, device memory) with Z ~= 2^e Zs, Zs = q / 128,
+ * q = clamp(rint(z 2^(7-e)), -127, 127), 2^e the smallest power of two >=
+ * sqrt(2/s); e is written to *e_out.  X W runs on split BF16 operands
+ * (hi.hi + lo.hi + hi.lo), so the cosine's argument carries about 2^-16 of
+ * sum_t |x_t||w_t| of error besides FP32 rounding.  X, W, b in device memory.
+ */
+krr_status krr_rff_features_fixed(krr_handle* h, const float* X, int n, int d, int ldx,
+                                  const float* W, const float* b, int s, uint16_t* Zs, int ldz,
+                                  int* e_out);
+
+/*
  * Kernel-matrix product, the per-iteration cost the paper names dominant
  * (Section 3.1, "multiplying the kernel matrix by a vector"):
  *   Q[i, :] = sum_j k(xr_i, xc_j) V[j, :] + shift * V[i, :]
@@ -166,7 +191,8 @@ krr_status krr_rff_features(krr_handle* h, const float* X, int n, int d, int ldx
  * (ldq).  V and Q are double for KRR_FP64 and KRR_HP and float for KRR_FP32,
  * KRR_BF16, KRR_FP16, KRR_BF16X3 and KRR_BF16P.  `shift` (lambda of Eq. (1))
  * needs nr == nc and is added
- * only when it is nonzero; pass Xr == Xc for the training system.
+ * only when it is nonzero; pass Xr == Xc for the training system.  The
+ * tensor-core products take any row set (Xr != Xc) except KRR_BF16P.
  * 1 <= k <= KRR_MAX_RHS.
  */
 krr_status krr_kernel_matvec(krr_handle* h, const float* Xr, int nr, int ldxr,
@@ -180,13 +206,17 @@ krr_status krr_kernel_matvec(krr_handle* h, const float* Xr, int nr, int ldxr,
  *   G = Z^T Z + lambda_p I_s (FP64 accumulation), L L^T = G (FP64
  *   Cholesky, lower L), then either U = L^-1 Z^T (KRR_APPLY_U, stored FP32
  *   s x n) or L^-1 kept for triangular solves (KRR_APPLY_ZL).
- * Z: n x s (ldz) FP32; the handle keeps its own copy (BF16 when z_bf16 is
- * 1, in which case G is formed from the rounded values so that the stored
- * factors describe exactly the operator applied).  s <= n.
- * Returns KRR_ECHOL when a pivot of the Cholesky factorisation is <= 0.
+ * Z: n x s (ldz) FP32; the handle keeps its own copy in `z_format`
+ * (krr_z_format).  With KRR_Z_BF16 or KRR_Z_FIXED, G is formed from the
+ * stored (rounded) values, so the factors describe exactly the operator
+ * applied, (Zt Zt^T + lambda_p I)^-1 with Zt the stored features; with
+ * KRR_Z_FIXED that Gram is exact (integer sums on the tensor cores) and the
+ * call synchronises once to find max |Z|.  s <= n.
+ * Returns KRR_ECHOL when a pivot of the Cholesky factorisation is <= 0 or Z
+ * holds a NaN or Inf, KRR_ETIMEOUT when a tensor-core wait hit its limit.
  */
 krr_status krr_precond_setup(krr_handle* h, const float* Z, int n, int s, int ldz,
-                             double lambda_p, int apply_form, int z_bf16);
+                             double lambda_p, int apply_form, int z_format);
 
 /*
  * Apply the preconditioner inverse of the last krr_precond_setup
@@ -285,7 +315,14 @@ krr_status krr_rfm_predict(krr_handle* h, const float* Xte, int m, int d, int ld
  *   F = K(Xte, Xtr) C.  Xtr: n x d (ldxtr), Xte: m x d (ldxte) FP32,
  * C: n x k double (ldc), F: m x k double (ldf); host or device pointers
  * (F is written before the call returns when it is a host pointer).
- * precision: KRR_FP64, KRR_HP or KRR_FP32 (FP32 then widened).
+ * precision: KRR_FP64, KRR_HP, KRR_FP32 (FP32 then widened), or a
+ * tensor-core product on rounded points, KRR_FP16, KRR_BF16 or KRR_BF16X3
+ * (C rounded to FP32; the held-out points rounded with the training mean and
+ * scale; KRR_EUNSUPPORTED when a held-out point lies so far from the training
+ * mean that the factored exp2 would overflow).  The rounded-point products
+ * carry the point rounding's error (about 2^-12 relative of -log K for FP16,
+ * 2^-16 for BF16X3), amplified by sum_j |K_ij||c_j| / |f_i|: use them when c
+ * does not cancel heavily.
  */
 krr_status krr_predict(krr_handle* h, const float* Xtr, int n, int ldxtr,
                        const float* Xte, int m, int ldxte, int d, double sigma,
@@ -307,7 +344,12 @@ krr_status krr_predict(krr_handle* h, const float* Xtr, int n, int ldxtr,
  * Derivative product  Q = (D o K)(Xr, Xc) V  (the lambda I term has no
  * sigma dependence, so there is no shift).  Xr: nr x d (ldxr), Xc: nc x d
  * (ldxc) FP32; V: nc x k (ldv), Q: nr x k (ldq) double; device pointers.
- * precision: KRR_FP64 (distances summed from differences, FP64 exp).
+ * precision: KRR_FP64 (distances summed from differences, FP64 exp),
+ * KRR_HP (float-float SIMT), or the tensor-core product on rounded points
+ * (KRR_FP16, KRR_BF16, KRR_BF16X3): S = xh_i.xh_j on tcgen05 and, with
+ * log2 K_ij = S_ij - nh_i/2 - nh_j/2, the epilogue contracts exp2(S) S and
+ * exp2(S) so that D o K = -2 ln 2 (log2 K) o K is formed without K (V, Q
+ * rounded to FP32 on the way).
  * 1 <= k <= KRR_MAX_RHS.  Returns KRR_EINVAL for bad arguments.
  */
 krr_status krr_kernel_dsigma_matvec(krr_handle* h, const float* Xr, int nr, int ldxr,

@@ -36,7 +36,7 @@ class krr_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("lambda_p", C.c_double),
                 ("precond", C.c_int), ("precision", C.c_int), ("apply_form", C.c_int),
                 ("use_graph", C.c_int), ("inner_tol", C.c_double), ("max_outer", C.c_int),
-                ("z_bf16", C.c_int), ("warm_start", C.c_int), ("inner_precision", C.c_int),
+                ("z_format", C.c_int), ("warm_start", C.c_int), ("inner_precision", C.c_int),
                 ("keep_direction", C.c_int)]
 
 
@@ -74,6 +74,8 @@ _SIGS = {
     "krr_status_string": (C.c_char_p, [_i]),
     "krr_set_autotune": (_i, [_vp, _i, C.POINTER(_i)]),
     "krr_rff_features": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _i, _vp, _i]),
+    "krr_rff_features_fixed": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _i, _vp, _i,
+                                    C.POINTER(_i)]),
     "krr_kernel_matvec": (_i, [_vp, _vp, _i, _i, _vp, _i, _i, _i, _d, _d, _vp, _i, _i, _vp, _i, _i]),
     "krr_precond_setup": (_i, [_vp, _vp, _i, _i, _i, _d, _i, _i]),
     "krr_precond_apply": (_i, [_vp, _vp, _i, _i, _vp, _i]),
@@ -232,13 +234,29 @@ def krr_kernel_matvec_fp64_noalloc(Xr, Xc, sigma: float, shift: float, V, Q, str
                                                _ptr(Q), _ld(Q), _stream_ptr(stream))
 
 
-def krr_precond_setup(h: Handle, Z, lambda_p: float, apply_form="zl", z_bf16: bool = False):
+Z_FORMAT = {"fp32": 0, "bf16": 1, "fixed": 2}
+
+
+def krr_precond_setup(h: Handle, Z, lambda_p: float, apply_form="zl", z_format="fp32"):
     """Preconditioner set-up from the features Z (n x s float32): G = Z^T Z + lambda_p I,
-    its Cholesky factor and the factors of the apply form ("zl" or "u")."""
+    its Cholesky factor and the factors of the apply form ("zl" or "u"); the handle
+    stores Z as ``z_format`` ("fp32", "bf16" or "fixed": 7-bit fixed point with an
+    exact tensor-core Gram)."""
     n, s = Z.shape
     form = APPLY_FORM[apply_form] if isinstance(apply_form, str) else int(apply_form)
-    h._check(_lib.krr_precond_setup(h.ptr, _ptr(Z), n, s, _ld(Z), float(lambda_p), form,
-                                    1 if z_bf16 else 0))
+    zf = Z_FORMAT[z_format] if isinstance(z_format, str) else int(z_format)
+    h._check(_lib.krr_precond_setup(h.ptr, _ptr(Z), n, s, _ld(Z), float(lambda_p), form, zf))
+
+
+def krr_rff_features_fixed(h: Handle, X, W, b, Zs) -> int:
+    """Fixed-point random Fourier features on the tensor cores: Zs (n x s torch.bfloat16)
+    with Z ~= 2^e Zs; returns e."""
+    n, d = X.shape
+    s = W.shape[1]
+    e = C.c_int()
+    h._check(_lib.krr_rff_features_fixed(h.ptr, _ptr(X), n, d, _ld(X), _ptr(W), _ptr(b), s,
+                                         _ptr(Zs), _ld(Zs), C.byref(e)))
+    return e.value
 
 
 def krr_precond_apply(h: Handle, R, Zout):

@@ -473,22 +473,11 @@ void host_colnorm2(krr_handle* h, const T* a, int n, int k, int lda, double* out
   for (int c = 0; c < k; ++c) out[c] = h->hostd[c];
 }
 
-void precond_setup_impl(krr_handle* h, const float* Z, int n, int s, int ldz, double lambda_p,
-                        int form, int z_bf16) {
-  KRR_REQUIRE(Z && n > 0 && s > 0 && ldz >= s, "precond_setup: bad Z / sizes");
-  KRR_REQUIRE(s <= n, "precond_setup: need s <= n");
-  KRR_REQUIRE(lambda_p > 0.0 && std::isfinite(lambda_p), "precond_setup: lambda_p must be > 0");
-  KRR_REQUIRE(form == KRR_APPLY_ZL || form == KRR_APPLY_U, "precond_setup: bad apply form");
+// Cholesky of the Gram matrix already in pc.L, then the apply form's factors
+// (the rest of Algorithm 1's set-up); z_bf16: storage of pc.Z.
+void precond_factor(krr_handle* h, int n, int s, double lambda_p, int form, int z_bf16) {
   cudaStream_t st = h->stream;
   Precond& pc = h->pc;
-  pc.ready = false;
-  const size_t esz = z_bf16 ? 2 : 4;
-  ensure_buf(pc.Z, (size_t)n * s * esz);
-  launch_copy_z(st, Z, n, s, ldz, pc.Z.p, z_bf16);
-  ensure_buf(pc.L, (size_t)s * s * sizeof(double));
-  const int nch = gram_chunks(n, s);
-  double* part = wsT<double>(h, "gram_part", (size_t)nch * s * s);
-  launch_gram(st, pc.Z.p, z_bf16, n, s, lambda_p, (double*)pc.L.p, part, nch);
   launch_cholesky(st, (double*)pc.L.p, s, h->info);
   int info = 0;
   KRR_CUDA(cudaMemcpyAsync(&h->hostd[0], h->info, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -515,6 +504,83 @@ void precond_setup_impl(krr_handle* h, const float* Z, int n, int s, int ldz, do
   pc.z_bf16 = z_bf16;
   pc.lam_p = lambda_p;
   pc.ready = true;
+}
+
+// The exact tensor-core Gram of the fixed-point features in pc.Z (whose
+// transpose is in ZT), G' = Zs^T Zs + lambda_p 2^-2e I, and the factors.
+void precond_fixed_gram_factor(krr_handle* h, const __nv_bfloat16* ZT, int e, int n, int s,
+                               double lambda_p, int form, int* err) {
+  cudaStream_t st = h->stream;
+  Precond& pc = h->pc;
+  ensure_buf(pc.L, (size_t)s * s * sizeof(double));
+  int* part = wsT<int>(h, "tcs_part", gram_tc_part_elems(n, s));
+  launch_gram_tc(st, ZT, n, s, lambda_p * std::ldexp(1.0, -2 * e), part, (double*)pc.L.p, err);
+  precond_factor(h, n, s, lambda_p, form, 1);
+  int e_flag = 0;
+  KRR_CUDA(cudaMemcpyAsync(&e_flag, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  KRR_CUDA(cudaStreamSynchronize(st));
+  if (e_flag) {
+    pc.ready = false;
+    throw Error{KRR_ETIMEOUT, "tensor-core set-up: a pipeline wait hit its limit"};
+  }
+  pc.z_fixed_e = e;
+}
+
+void precond_setup_impl(krr_handle* h, const float* Z, int n, int s, int ldz, double lambda_p,
+                        int form, int z_format) {
+  KRR_REQUIRE(Z && n > 0 && s > 0 && ldz >= s, "precond_setup: bad Z / sizes");
+  KRR_REQUIRE(s <= n, "precond_setup: need s <= n");
+  KRR_REQUIRE(lambda_p > 0.0 && std::isfinite(lambda_p), "precond_setup: lambda_p must be > 0");
+  KRR_REQUIRE(form == KRR_APPLY_ZL || form == KRR_APPLY_U, "precond_setup: bad apply form");
+  KRR_REQUIRE(z_format >= KRR_Z_FP32 && z_format <= KRR_Z_FIXED, "precond_setup: bad Z format");
+  cudaStream_t st = h->stream;
+  Precond& pc = h->pc;
+  pc.ready = false;
+  pc.z_fixed_e = 0;
+  if (z_format == KRR_Z_FIXED) {
+    ensure_buf(pc.Z, (size_t)n * s * 2);
+    __nv_bfloat16* ZT = wsT<__nv_bfloat16>(
+        h, "tcs_zt", (size_t)setup_tc_s_pad(s) * setup_tc_n_pad(n));
+    int* scr = wsT<int>(h, "tcs_scr", 4);
+    KRR_CUDA(cudaMemsetAsync(scr, 0, 4 * sizeof(int), st));
+    const int e = launch_quantize_z(st, Z, n, s, ldz, (__nv_bfloat16*)pc.Z.p, ZT, scr);
+    precond_fixed_gram_factor(h, ZT, e, n, s, lambda_p, form, scr + 1);
+    return;
+  }
+  const int z_bf16 = z_format == KRR_Z_BF16 ? 1 : 0;
+  const size_t esz = z_bf16 ? 2 : 4;
+  ensure_buf(pc.Z, (size_t)n * s * esz);
+  launch_copy_z(st, Z, n, s, ldz, pc.Z.p, z_bf16);
+  ensure_buf(pc.L, (size_t)s * s * sizeof(double));
+  const int nch = gram_chunks(n, s);
+  double* part = wsT<double>(h, "gram_part", (size_t)nch * s * s);
+  launch_gram(st, pc.Z.p, z_bf16, n, s, lambda_p, (double*)pc.L.p, part, nch);
+  precond_factor(h, n, s, lambda_p, form, z_bf16);
+}
+
+// Features and preconditioner on the tensor cores in one go (the mixed
+// solves' set-up): fixed-point random Fourier features of X straight into
+// pc.Z (and their transpose), then the exact Gram and the factors.
+void precond_setup_rff_tc(krr_handle* h, const float* Xd, int n, int d, int ldx, const float* Wd,
+                          const float* bd, int s, double lambda_p, int form) {
+  KRR_REQUIRE(s <= n, "precond_setup: need s <= n");
+  KRR_REQUIRE(lambda_p > 0.0 && std::isfinite(lambda_p), "precond_setup: lambda_p must be > 0");
+  cudaStream_t st = h->stream;
+  Precond& pc = h->pc;
+  pc.ready = false;
+  pc.z_fixed_e = 0;
+  ensure_buf(pc.Z, (size_t)n * s * 2);
+  const int n_pad = setup_tc_n_pad(n), s_pad = setup_tc_s_pad(s), kp = setup_tc_kp(d);
+  __nv_bfloat16* ZT = wsT<__nv_bfloat16>(h, "tcs_zt", (size_t)s_pad * n_pad);
+  __nv_bfloat16* Xh = wsT<__nv_bfloat16>(h, "tcs_xh", (size_t)n_pad * kp);
+  __nv_bfloat16* Xl = wsT<__nv_bfloat16>(h, "tcs_xl", (size_t)n_pad * kp);
+  __nv_bfloat16* Wh = wsT<__nv_bfloat16>(h, "tcs_wh", (size_t)s_pad * kp);
+  __nv_bfloat16* Wl = wsT<__nv_bfloat16>(h, "tcs_wl", (size_t)s_pad * kp);
+  int* scr = wsT<int>(h, "tcs_scr", 4);
+  KRR_CUDA(cudaMemsetAsync(scr, 0, 4 * sizeof(int), st));
+  const int e = launch_rff_tc(st, Xd, n, d, ldx, Wd, bd, s, Xh, Xl, Wh, Wl,
+                              (__nv_bfloat16*)pc.Z.p, ZT, scr + 1);
+  precond_fixed_gram_factor(h, ZT, e, n, s, lambda_p, form, scr + 1);
 }
 
 // Nonzero if a streamed apply hit its bounded wait since the set-up.
@@ -933,11 +999,16 @@ void setup_impl(krr_handle* h, const float* Xd, int n, int d, int ldx, double si
                 double lambda, const float* Wd, const float* bd, int s, const krr_opts& o) {
   cudaStream_t st = h->stream;
   if (o.precond) {
-    float* Z = wsT<float>(h, "rff_Z", (size_t)n * s);
-    launch_rff(st, Xd, n, d, ldx, Wd, bd, s, Z, s);
-    int zb = o.z_bf16 < 0 ? (o.precision == KRR_MIXED ? 1 : 0) : (o.z_bf16 ? 1 : 0);
-    double lp = o.lambda_p > 0.0 ? o.lambda_p : lambda;
-    precond_setup_impl(h, Z, n, s, s, lp, o.apply_form, zb);
+    const int zf = o.z_format < 0 ? (o.precision == KRR_MIXED ? KRR_Z_FIXED : KRR_Z_FP32)
+                                : o.z_format;
+    const double lp = o.lambda_p > 0.0 ? o.lambda_p : lambda;
+    if (zf == KRR_Z_FIXED) {
+      precond_setup_rff_tc(h, Xd, n, d, ldx, Wd, bd, s, lp, o.apply_form);
+    } else {
+      float* Z = wsT<float>(h, "rff_Z", (size_t)n * s);
+      launch_rff(st, Xd, n, d, ldx, Wd, bd, s, Z, s);
+      precond_setup_impl(h, Z, n, s, s, lp, o.apply_form, zf);
+    }
   }
   if (o.precision == KRR_MIXED) {
     if (low_precision(o) == KRR_FP16)
@@ -983,6 +1054,18 @@ krr_status solve_impl(krr_handle* h, const float* Xd, int n, int d, int ldx, dou
 void dsigma_dispatch(krr_handle* h, cudaStream_t st, const float* Xr, int nr, int ldxr,
                      const float* Xc, int nc, int ldxc, int d, double sigma, const double* V,
                      int k, int ldv, double* Q, int ldq, int prec) {
+  if (prec == KRR_FP16 || prec == KRR_BF16 || prec == KRR_BF16X3) {
+    // tensor-core derivative product on rounded points: FP32 in and out
+    ColScale one;
+    for (int c = 0; c < KRR_MAX_RHS; ++c) one.v[c] = 1.0;
+    float* Vf = wsT<float>(h, "ds_vf", (size_t)nc * k);
+    float* Qf = wsT<float>(h, "ds_qf", (size_t)nr * k);
+    launch_convert<double, float>(st, V, nc, k, ldv, Vf, k, one);
+    tc_dsigma_matvec(h->tc, st, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, Vf, k, k, Qf, k,
+                     prec == KRR_BF16X3 ? 1 : 0, prec == KRR_FP16 ? 1 : 0);
+    launch_convert<float, double>(st, Qf, nr, k, k, Q, ldq, one);
+    return;
+  }
   if (prec == KRR_FP64) {
     double* part = wsT<double>(h, "mv_part64", mv_fp64_part_elems(nr, nc, k));
     launch_mv_fp64(st, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, 0.0, V, k, ldv, Q, ldq, part, 1);
@@ -1473,7 +1556,7 @@ void krr_default_opts(krr_opts* o) {
   o->use_graph = 1;
   o->inner_tol = 3e-2;
   o->max_outer = 30;
-  o->z_bf16 = -1;
+  o->z_format = -1;
   o->warm_start = 0;
   o->inner_precision = KRR_FP16;
   o->keep_direction = 0;
@@ -1566,6 +1649,36 @@ krr_status krr_rff_features(krr_handle* h, const float* X, int n, int d, int ldx
   });
 }
 
+krr_status krr_rff_features_fixed(krr_handle* h, const float* X, int n, int d, int ldx,
+                                  const float* W, const float* b, int s, uint16_t* Zs, int ldz,
+                                  int* e_out) {
+  return guard(h, [&]() -> krr_status {
+    KRR_REQUIRE(X && W && b && Zs && e_out, "rff_features_fixed: null pointer");
+    KRR_REQUIRE(n > 0 && d > 0 && s > 0, "rff_features_fixed: sizes must be positive");
+    KRR_REQUIRE(ldx >= d && ldz >= s, "rff_features_fixed: leading dimension too small");
+    cudaStream_t st = h->stream;
+    const int n_pad = setup_tc_n_pad(n), s_pad = setup_tc_s_pad(s), kp = setup_tc_kp(d);
+    __nv_bfloat16* ZT = wsT<__nv_bfloat16>(h, "tcs_zt", (size_t)s_pad * n_pad);
+    __nv_bfloat16* Xh = wsT<__nv_bfloat16>(h, "tcs_xh", (size_t)n_pad * kp);
+    __nv_bfloat16* Xl = wsT<__nv_bfloat16>(h, "tcs_xl", (size_t)n_pad * kp);
+    __nv_bfloat16* Wh = wsT<__nv_bfloat16>(h, "tcs_wh", (size_t)s_pad * kp);
+    __nv_bfloat16* Wl = wsT<__nv_bfloat16>(h, "tcs_wl", (size_t)s_pad * kp);
+    __nv_bfloat16* Zo = ldz == s ? reinterpret_cast<__nv_bfloat16*>(Zs)
+                                 : wsT<__nv_bfloat16>(h, "tcs_zout", (size_t)n * s);
+    int* scr = wsT<int>(h, "tcs_scr", 4);
+    KRR_CUDA(cudaMemsetAsync(scr, 0, 4 * sizeof(int), st));
+    *e_out = launch_rff_tc(st, X, n, d, ldx, W, b, s, Xh, Xl, Wh, Wl, Zo, ZT, scr + 1);
+    if (ldz != s)
+      KRR_CUDA(cudaMemcpy2DAsync(Zs, (size_t)ldz * 2, Zo, (size_t)s * 2, (size_t)s * 2, n,
+                                 cudaMemcpyDeviceToDevice, st));
+    int flag = 0;
+    KRR_CUDA(cudaMemcpyAsync(&flag, scr + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KRR_CUDA(cudaStreamSynchronize(st));
+    if (flag) throw Error{KRR_ETIMEOUT, "rff_features_fixed: a pipeline wait hit its limit"};
+    return KRR_OK;
+  });
+}
+
 krr_status krr_kernel_matvec(krr_handle* h, const float* Xr, int nr, int ldxr, const float* Xc,
                              int nc, int ldxc, int d, double sigma, double shift, const void* V,
                              int k, int ldv, void* Q, int ldq, int precision) {
@@ -1593,9 +1706,9 @@ krr_status krr_kernel_matvec(krr_handle* h, const float* Xr, int nr, int ldxr, c
 }
 
 krr_status krr_precond_setup(krr_handle* h, const float* Z, int n, int s, int ldz,
-                             double lambda_p, int apply_form, int z_bf16) {
+                             double lambda_p, int apply_form, int z_format) {
   return guard(h, [&]() -> krr_status {
-    precond_setup_impl(h, Z, n, s, ldz, lambda_p, apply_form, z_bf16 ? 1 : 0);
+    precond_setup_impl(h, Z, n, s, ldz, lambda_p, apply_form, z_format);
     return KRR_OK;
   });
 }
@@ -1785,7 +1898,8 @@ krr_status krr_predict(krr_handle* h, const float* Xtr, int n, int ldxtr, const 
     KRR_REQUIRE(n > 0 && m > 0 && d > 0 && k >= 1 && k <= KRR_MAX_RHS, "predict: bad sizes");
     KRR_REQUIRE(ldxtr >= d && ldxte >= d && ldc >= k && ldf >= k, "predict: bad leading dims");
     KRR_REQUIRE(sigma > 0.0 && std::isfinite(sigma), "predict: sigma must be > 0");
-    KRR_REQUIRE(precision == KRR_FP64 || precision == KRR_HP || precision == KRR_FP32,
+    KRR_REQUIRE(precision == KRR_FP64 || precision == KRR_HP || precision == KRR_FP32 ||
+                    precision == KRR_FP16 || precision == KRR_BF16 || precision == KRR_BF16X3,
                 "predict: bad precision");
     cudaStream_t st = h->stream;
     const float* Xtr_d = (const float*)stage_in(h, Xtr, (size_t)n * ldxtr * sizeof(float), "pXtr");
@@ -1793,15 +1907,18 @@ krr_status krr_predict(krr_handle* h, const float* Xtr, int n, int ldxtr, const 
     const double* C_d = (const double*)stage_in(h, C, (size_t)n * ldc * sizeof(double), "pC");
     const bool f_host = !on_device(F);
     double* F_d = f_host ? wsT<double>(h, "pF", (size_t)m * ldf) : F;
-    if (precision == KRR_FP32) {
+    if (precision != KRR_FP64 && precision != KRR_HP) {
+      // FP32 SIMT or a tensor-core product on rounded points: FP32 in and out
       ColScale one;
       for (int c = 0; c < KRR_MAX_RHS; ++c) one.v[c] = 1.0;
       float* Cf = wsT<float>(h, "pr_cf", (size_t)n * k);
       float* Ff = wsT<float>(h, "pr_ff", (size_t)m * k);
       launch_convert<double, float>(st, C_d, n, k, ldc, Cf, k, one);
       matvec_dispatch(h, st, Xte_d, m, ldxte, Xtr_d, n, ldxtr, d, sigma, 0.0, Cf, k, k, Ff, k,
-                      KRR_FP32);
+                      precision);
       launch_convert<float, double>(st, Ff, m, k, k, F_d, ldf, one);
+      if (precision != KRR_FP32 && tc_error(h->tc, st))
+        throw Error{KRR_ETIMEOUT, "tensor-core product: a pipeline wait hit its limit"};
     } else {
       matvec_dispatch(h, st, Xte_d, m, ldxte, Xtr_d, n, ldxtr, d, sigma, 0.0, C_d, k, ldc, F_d,
                       ldf, precision);
@@ -1890,10 +2007,15 @@ krr_status krr_kernel_dsigma_matvec(krr_handle* h, const float* Xr, int nr, int 
     KRR_REQUIRE(ldxr >= d && ldxc >= d && ldv >= k && ldq >= k,
                 "kernel_dsigma_matvec: leading dimension too small");
     KRR_REQUIRE(sigma > 0.0 && std::isfinite(sigma), "kernel_dsigma_matvec: sigma must be > 0");
-    KRR_REQUIRE(precision == KRR_FP64 || precision == KRR_HP,
-                "kernel_dsigma_matvec: precision must be KRR_FP64 or KRR_HP");
+    KRR_REQUIRE(precision == KRR_FP64 || precision == KRR_HP || precision == KRR_FP16 ||
+                    precision == KRR_BF16 || precision == KRR_BF16X3,
+                "kernel_dsigma_matvec: precision must be KRR_FP64, KRR_HP, KRR_FP16, KRR_BF16 "
+                "or KRR_BF16X3");
     dsigma_dispatch(h, h->stream, Xr, nr, ldxr, Xc, nc, ldxc, d, sigma, V, k, ldv, Q, ldq,
                     precision);
+    if ((precision == KRR_FP16 || precision == KRR_BF16 || precision == KRR_BF16X3) &&
+        tc_error(h->tc, h->stream))
+      throw Error{KRR_ETIMEOUT, "tensor-core product: a pipeline wait hit its limit"};
     return KRR_OK;
   });
 }

@@ -90,6 +90,7 @@ enum : int { FLAG_BREAKDOWN = 1, FLAG_NAN = 2, FLAG_CAP = 4 };
 struct Precond {
   bool ready = false;
   int n = 0, s = 0, form = KRR_APPLY_ZL, z_bf16 = 0;
+  int z_fixed_e = 0;  // fixed-point features: Z ~= 2^e Zs (0 otherwise)
   double lam_p = 0.0;
   DevBuf Z;      // n x s (ld = s), FP32 or BF16
   DevBuf L;      // s x s FP64 lower Cholesky factor of G
@@ -131,6 +132,28 @@ void launch_mv_fp32(cudaStream_t st, const float* Xr, int nr, int ldxr, const fl
                     int nc, int ldxc, int d, double sigma, double shift, const float* V,
                     int k, int ldv, float* Q, int ldq, float* nrm_r, float* nrm_c,
                     float* part);
+
+// Tensor-core set-up (krr_setup_tc.cu): fixed-point features zs = q / 128
+// (q = clamp(rint(z 2^(7-e)), +-127), z ~= 2^e zs) and their exact Gram.
+// Padded sizes: Z^T is setup_tc_s_pad(s) x setup_tc_n_pad(n) BF16; the split
+// operands are setup_tc_n_pad(n) (X) or setup_tc_s_pad(s) (W^T) x setup_tc_kp(d).
+int setup_tc_n_pad(int n);
+int setup_tc_s_pad(int s);
+int setup_tc_kp(int d);
+int fixed_point_exponent(double maxabs);
+size_t gram_tc_part_elems(int n, int s);
+// Features of X (n x d, ldx) for W (d x s), b (s): Z (n x s BF16) and Z^T;
+// returns e.
+int launch_rff_tc(cudaStream_t st, const float* X, int n, int d, int ldx, const float* W,
+                  const float* b, int s, __nv_bfloat16* Xh, __nv_bfloat16* Xl,
+                  __nv_bfloat16* Wh, __nv_bfloat16* Wl, __nv_bfloat16* Z, __nv_bfloat16* ZT,
+                  int* err);
+// Fixed-point copy of a caller's FP32 Z (synchronises once for max |Z|); returns e.
+int launch_quantize_z(cudaStream_t st, const float* Z, int n, int s, int ldz, __nv_bfloat16* Zs,
+                      __nv_bfloat16* ZT, int* scratch);
+// G = Zs^T Zs + shift I (s x s FP64, exact) from Z^T; part: gram_tc_part_elems ints.
+void launch_gram_tc(cudaStream_t st, const __nv_bfloat16* ZT, int n, int s, double shift,
+                    int* part, double* G, int* err);
 
 // Preconditioner (krr_precond.cu)
 void launch_copy_z(cudaStream_t st, const float* Z, int n, int s, int ldz, void* Zs, int bf16);

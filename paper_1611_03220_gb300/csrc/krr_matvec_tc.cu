@@ -98,11 +98,14 @@ struct TcParams {
   const float* w;   // n_ct*BN x KV
   float* part;      // nchunk x n_rpad x KV
   int* err;
+  int ds_k = 0;     // derivative mode: w columns c < ds_k take exp2(S) S, the rest exp2(S)
 };
 
 // EMU of every 32 exponentials run on the FMA pipe (a tuner dimension for
-// one right-hand side; Cfg<KV>::EMU otherwise).
-template <int KV, int EMU = Cfg<KV>::EMU>
+// one right-hand side; Cfg<KV>::EMU otherwise).  DS = 1 is the derivative
+// mode of the (D o K) product: the first p.ds_k weight columns are
+// contracted with exp2(S) S instead of exp2(S).
+template <int KV, int EMU = Cfg<KV>::EMU, int DS = 0>
 __global__ void __launch_bounds__(Cfg<KV>::THREADS, 1)
 tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
@@ -323,9 +326,11 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                              *reinterpret_cast<uint32_t(*)[16]>(&raw[cur ^ 1][16]));
           }
           // all exponentials of the chunk first (independent), then the contraction
+          float sv[DS ? 32 : 1];
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const float s = __uint_as_float(raw[cur][j]);
+            if (DS) sv[j] = s;
             raw[cur][j] = __float_as_uint((j % PER == PER - 1) ? ex2_fma(s) : ex2_mufu(s));
           }
           const float4* w4 = reinterpret_cast<const float4*>(wb + (grp * COLS + cc * 32) * KV);
@@ -354,7 +359,9 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
               for (int u = 0; u < 4; ++u) {
                 const int idx = j4 * 4 + u;  // = j * KV + c
                 const int j = idx / KV, c = idx % KV;
-                q[j % CH][c] = fmaf(__uint_as_float(raw[cur][j]), wq[u], q[j % CH][c]);
+                float ev = __uint_as_float(raw[cur][j]);
+                if (DS && c < p.ds_k) ev *= sv[j];
+                q[j % CH][c] = fmaf(ev, wq[u], q[j % CH][c]);
               }
             }
           }
@@ -837,6 +844,47 @@ __global__ void make_vt_kernel(const float* __restrict__ V, int n, int k, int ld
   }
 }
 
+// Weights of the derivative mode for RHS columns c0 .. c0 + kb - 1: columns
+// [0, kb) and [kb, 2 kb) hold ra_j v_j, [2 kb, 3 kb) hold (nh_j / 2) ra_j v_j.
+__global__ void make_w_ds_kernel(const float* __restrict__ V, int n, int kb, int c0, int ldv,
+                                 const float* __restrict__ ra, const float* __restrict__ nh,
+                                 int n_pad, int kv, float* __restrict__ w) {
+  const size_t total = (size_t)n_pad * kv;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / kv), c = (int)(e % kv);
+    float v = 0.f;
+    if (j < n && c < 3 * kb) {
+      const int cc = c % kb;
+      v = ra[j] * V[(size_t)j * ldv + c0 + cc];
+      if (c >= 2 * kb) v *= 0.5f * nh[j];
+    }
+    w[e] = v;
+  }
+}
+
+// (D o K) v = -2 ln 2 ra_i (sum_j E_ij S_ij w_j - (nh_i / 2) sum_j E_ij w_j
+//             - sum_j E_ij (nh_j / 2) w_j),  E = exp2(S), log2 K_ij = S_ij - nh_i/2 - nh_j/2
+__global__ void ds_reduce_kernel(const float* __restrict__ part, int nchunk, int n_rpad, int kv,
+                                 int kb, const float* __restrict__ ra,
+                                 const float* __restrict__ nh, int nr, int c0,
+                                 float* __restrict__ Q, int ldq) {
+  const size_t total = (size_t)nr * kb;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / kb), c = (int)(e % kb);
+    double a = 0.0, b = 0.0, cs = 0.0;
+    for (int ch = 0; ch < nchunk; ++ch) {
+      const float* pr = part + ((size_t)ch * n_rpad + i) * kv;
+      a += (double)pr[c];
+      b += (double)pr[kb + c];
+      cs += (double)pr[2 * kb + c];
+    }
+    const double r = -1.3862943611198906 * (double)ra[i] * (a - 0.5 * (double)nh[i] * b - cs);
+    Q[(size_t)i * ldq + c0 + c] = (float)r;
+  }
+}
+
 // Q[i, c] = ra_i * sum_ch part[ch, i, c] + shift * V[i, c]
 __global__ void tc_reduce_kernel(const float* __restrict__ part, int nchunk, int n_rpad, int kv,
                                  const float* __restrict__ ra, int nr, int k,
@@ -937,18 +985,28 @@ size_t smem_bytes(int a_res, int ns, int x3) {
          (size_t)NW * BN * KV * 4 + (size_t)(NG - 1) * BM * KV * 4 + 256;
 }
 
-template <int KV, int EMU = Cfg<KV>::EMU>
+template <int KV, int EMU = Cfg<KV>::EMU, int DS = 0>
 void launch_kernel(cudaStream_t st, const CUtensorMap& a, const CUtensorMap& b,
                    const CUtensorMap& a2, const CUtensorMap& b2, const TcParams& p, int grid) {
   static size_t attr = 0;
   const size_t sm = smem_bytes<KV>(p.a_res, p.ns, p.x3);
   if (attr < sm) {
-    KRR_CUDA(cudaFuncSetAttribute(tc_matvec_kernel<KV, EMU>,
+    KRR_CUDA(cudaFuncSetAttribute(tc_matvec_kernel<KV, EMU, DS>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr = sm;
   }
-  tc_matvec_kernel<KV, EMU><<<grid, Cfg<KV>::THREADS, sm, st>>>(a, b, a2, b2, p);
+  tc_matvec_kernel<KV, EMU, DS><<<grid, Cfg<KV>::THREADS, sm, st>>>(a, b, a2, b2, p);
   KRR_CHECK_LAUNCH();
+}
+
+// The derivative mode for weight blocks of kv = 4, 8, 12 or 16 columns.
+void dispatch_ds(int kv, cudaStream_t st, const TcOperand& op, const TcParams& p, int grid) {
+  switch (kv) {
+    case 4: launch_kernel<4, Cfg<4>::EMU, 1>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid); break;
+    case 8: launch_kernel<8, Cfg<8>::EMU, 1>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid); break;
+    case 12: launch_kernel<12, Cfg<12>::EMU, 1>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid); break;
+    default: launch_kernel<16, Cfg<16>::EMU, 1>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid); break;
+  }
 }
 
 // emu: FMA-pipe exponentials per 32 for one right-hand side (0, 2 or 4).
@@ -1098,6 +1156,10 @@ int default_ns(int a_res) { return a_res ? 4 : 3; }
 
 void tc_ensure(DevBuf& b, size_t bytes) { ensure(b, bytes); }
 
+void tc_make_map_bf16(CUtensorMap* m, const void* base, int rows, int row_elems, int box_rows) {
+  make_map(m, base, rows, row_elems, box_rows, false);
+}
+
 void tc_prepare(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int d, double sigma) {
   const double c = 1.4426950408889634 / (2.0 * sigma * sigma);  // log2(e) / (2 sigma^2)
   const double scale = std::sqrt(2.0 * c);
@@ -1153,6 +1215,28 @@ void tc_prepare_f16(TcState& t, cudaStream_t st, const float* X, int n, int ldx,
   t.half_ready = true;
 }
 
+void tc_prepare_rows(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr, int d,
+                     double sigma, int fmt) {
+  if (!t.ready || t.sigma != sigma || t.cols.d != d)
+    throw Error{KRR_EINVAL, "row operand prepared before the column operand"};
+  const double c = 1.4426950408889634 / (2.0 * sigma * sigma);
+  prep_operand(t.rows, st, Xr, nr, ldxr, d, (const double*)t.mu.p, std::sqrt(2.0 * c), fmt == 1,
+               fmt == 2);
+  // the factored exp2 needs xh_i.xh_j <= 120 as well: sqrt(nh_i nh_j) <= max(nh)
+  KRR_CUDA(cudaMemsetAsync(t.scal.p, 0, 16, st));
+  max_kernel<<<std::min(8 * sm_count(), (t.rows.n_pad + 255) / 256), 256, 0, st>>>(
+      (const float*)t.rows.nh.p, t.rows.n_pad, (float*)t.scal.p);
+  KRR_CHECK_LAUNCH();
+  float mx = 0.f;
+  KRR_CUDA(cudaMemcpyAsync(&mx, t.scal.p, sizeof(float), cudaMemcpyDeviceToHost, st));
+  KRR_CUDA(cudaStreamSynchronize(st));
+  if (!(mx <= 120.f))
+    throw Error{KRR_EUNSUPPORTED,
+                "tensor-core product: a row point is too far from the training mean for the "
+                "factored exp2 (||x - mean||^2 / (2 sigma^2) = " + std::to_string(mx) +
+                " in log2 units); use FP32, FP64 or HP"};
+}
+
 namespace {
 
 TcOperand& operand_of(TcState& t, int fmt) {
@@ -1194,6 +1278,110 @@ void run_fused(TcState& t, cudaStream_t st, TcOperand& op, const Plan& pl, int s
       (const float*)t.part.p, pl.nchunk, op.n_pad, pl.kv, (const float*)op.ra.p, nr, k, V, ldv,
       shift, Q, ldq);
   KRR_CHECK_LAUNCH();
+}
+
+// The fused product for a row set other than the columns (prediction, the
+// gradient's cross terms): row tiles from `rop` (prepared with the columns'
+// mean and scale, so xh_i.xh_j - nh_i/2 - nh_j/2 is still -c ||x_i - x_j||^2),
+// column tiles from `cop`; the kernel is the same.
+void run_fused_rows(TcState& t, cudaStream_t st, const TcOperand& rop, const TcOperand& cop,
+                    int split, int f16, const float* V, int k, int ldv, double shift, float* Q,
+                    int ldq) {
+  const int kv = kv_bucket(k);
+  const int n_rt = rop.n_pad / BM, n_ct = cop.n_pad / BN;
+  const int req = choose_nchunk(n_rt, n_ct, sm_count());
+  const int cpc = (n_ct + req - 1) / req;
+  const int nchunk = (n_ct + cpc - 1) / cpc;
+  ensure(t.w, (size_t)cop.n_pad * kv * 4);
+  ensure(t.part, (size_t)nchunk * rop.n_pad * kv * 4);
+  if (!t.err.p) {
+    ensure(t.err, 16);
+    KRR_CUDA(cudaMemsetAsync(t.err.p, 0, 16, st));
+  }
+  const int nkb = split ? 2 : cop.kp / BK;
+  const int a_res = (split || nkb == 1) ? 1 : 0;
+  make_w_kernel<<<std::min(8 * sm_count(), (int)(((size_t)cop.n_pad * kv + 255) / 256)), 256, 0,
+                  st>>>(V, cop.n, k, ldv, (const float*)cop.ra.p, cop.n_pad, kv, (float*)t.w.p);
+  KRR_CHECK_LAUNCH();
+  TcParams p;
+  p.n_rt = n_rt;
+  p.n_ct = n_ct;
+  p.nchunk = nchunk;
+  p.cpc = cpc;
+  p.nkb = nkb;
+  p.a_res = a_res;
+  p.ns = default_ns(a_res);
+  p.x3 = split;
+  p.idesc = f16 ? idesc_f16(BM, BN) : idesc_bf16(BM, BN);
+  p.n_rpad = rop.n_pad;
+  p.w = (const float*)t.w.p;
+  p.part = (float*)t.part.p;
+  p.err = (int*)t.err.p;
+  TcOperand mix;   // row maps of rop, column maps of cop
+  mix.map_a = rop.map_a;
+  mix.map_a2 = rop.map_a2;
+  mix.map_b = cop.map_b;
+  mix.map_b2 = cop.map_b2;
+  const int grid = std::min(n_rt * nchunk, sm_count());
+  dispatch(kv, st, mix, p, grid, 0);
+  const size_t total = (size_t)rop.n * k;
+  tc_reduce_kernel<<<std::min(8 * sm_count(), (int)((total + 255) / 256)), 256, 0, st>>>(
+      (const float*)t.part.p, nchunk, rop.n_pad, kv, (const float*)rop.ra.p, rop.n, k, V, ldv,
+      shift, Q, ldq);
+  KRR_CHECK_LAUNCH();
+}
+
+// Q = (D o K(Xr, Xc)) V, D_ij = ||x_i - x_j||^2 / sigma^2 = -2 ln 2 log2 K_ij
+// (the derivative of K in log sigma) on the rounded points of format fmt, in
+// blocks of up to five right-hand sides (three weight columns each).
+void run_dsigma(TcState& t, cudaStream_t st, const TcOperand& rop, const TcOperand& cop,
+                int split, int f16, const float* V, int k, int ldv, float* Q, int ldq) {
+  const int n_rt = rop.n_pad / BM, n_ct = cop.n_pad / BN;
+  const int req = choose_nchunk(n_rt, n_ct, sm_count());
+  const int cpc = (n_ct + req - 1) / req;
+  const int nchunk = (n_ct + cpc - 1) / cpc;
+  const int nkb = split ? 2 : cop.kp / BK;
+  const int a_res = (split || nkb == 1) ? 1 : 0;
+  TcOperand mix;
+  mix.map_a = rop.map_a;
+  mix.map_a2 = rop.map_a2;
+  mix.map_b = cop.map_b;
+  mix.map_b2 = cop.map_b2;
+  for (int c0 = 0; c0 < k; c0 += 5) {
+    const int kb = std::min(5, k - c0);
+    const int kv = kv_bucket(3 * kb);
+    ensure(t.w, (size_t)cop.n_pad * kv * 4);
+    ensure(t.part, (size_t)nchunk * rop.n_pad * kv * 4);
+    if (!t.err.p) {
+      ensure(t.err, 16);
+      KRR_CUDA(cudaMemsetAsync(t.err.p, 0, 16, st));
+    }
+    make_w_ds_kernel<<<std::min(8 * sm_count(), (int)(((size_t)cop.n_pad * kv + 255) / 256)),
+                       256, 0, st>>>(V, cop.n, kb, c0, ldv, (const float*)cop.ra.p,
+                                     (const float*)cop.nh.p, cop.n_pad, kv, (float*)t.w.p);
+    KRR_CHECK_LAUNCH();
+    TcParams p;
+    p.n_rt = n_rt;
+    p.n_ct = n_ct;
+    p.nchunk = nchunk;
+    p.cpc = cpc;
+    p.nkb = nkb;
+    p.a_res = a_res;
+    p.ns = default_ns(a_res);
+    p.x3 = split;
+    p.idesc = f16 ? idesc_f16(BM, BN) : idesc_bf16(BM, BN);
+    p.n_rpad = rop.n_pad;
+    p.w = (const float*)t.w.p;
+    p.part = (float*)t.part.p;
+    p.err = (int*)t.err.p;
+    p.ds_k = kb;
+    dispatch_ds(kv, st, mix, p, std::min(n_rt * nchunk, sm_count()));
+    const size_t total = (size_t)rop.n * kb;
+    ds_reduce_kernel<<<std::min(8 * sm_count(), (int)((total + 255) / 256)), 256, 0, st>>>(
+        (const float*)t.part.p, nchunk, rop.n_pad, kv, kb, (const float*)rop.ra.p,
+        (const float*)rop.nh.p, rop.n, c0, Q, ldq);
+    KRR_CHECK_LAUNCH();
+  }
 }
 
 // Time the candidate plans of one shape on the prepared operand (scratch
@@ -1358,7 +1546,8 @@ void tc_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr, c
                int nc, int ldxc, int d, double sigma, double shift, const float* V, int k,
                int ldv, float* Q, int ldq, int split, int gemm2, int f16) {
   const bool same = (Xr == Xc && nr == nc && ldxr == ldxc);
-  if (!same) throw Error{KRR_EUNSUPPORTED, "tensor-core product supports the training system (Xr == Xc)"};
+  if (!same && gemm2)
+    throw Error{KRR_EUNSUPPORTED, "two-GEMM product: the training system only (Xr == Xc)"};
   if (f16 && (split || gemm2))
     throw Error{KRR_EUNSUPPORTED, "FP16 points: plain product only (no split, no second GEMM)"};
   if (split)
@@ -1368,6 +1557,11 @@ void tc_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr, c
   else
     tc_prepare(t, st, Xc, nc, ldxc, d, sigma);
   const int fmt = split ? 1 : (f16 ? 2 : 0);
+  if (!same) {
+    tc_prepare_rows(t, st, Xr, nr, ldxr, d, sigma, fmt);
+    run_fused_rows(t, st, t.rows, operand_of(t, fmt), split, f16, V, k, ldv, shift, Q, ldq);
+    return;
+  }
   tc_reserve(t, st, k, gemm2, fmt);
   TcOperand& op = operand_of(t, fmt);
   const Plan pl = resolve_plan(t, st, op, k, gemm2, fmt);
@@ -1405,6 +1599,23 @@ void tc_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr, c
   run_fused(t, st, op, pl, split, f16, nr, V, k, ldv, shift, Q, ldq);
 }
 
+void tc_dsigma_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr,
+                      const float* Xc, int nc, int ldxc, int d, double sigma, const float* V,
+                      int k, int ldv, float* Q, int ldq, int split, int f16) {
+  if (f16 && split) throw Error{KRR_EUNSUPPORTED, "FP16 points: no split form"};
+  if (split)
+    tc_prepare_split(t, st, Xc, nc, ldxc, d, sigma);
+  else if (f16)
+    tc_prepare_f16(t, st, Xc, nc, ldxc, d, sigma);
+  else
+    tc_prepare(t, st, Xc, nc, ldxc, d, sigma);
+  const int fmt = split ? 1 : (f16 ? 2 : 0);
+  TcOperand& cop = operand_of(t, fmt);
+  const bool same = (Xr == Xc && nr == nc && ldxr == ldxc);
+  if (!same) tc_prepare_rows(t, st, Xr, nr, ldxr, d, sigma, fmt);
+  run_dsigma(t, st, same ? cop : t.rows, cop, split, f16, V, k, ldv, Q, ldq);
+}
+
 int tc_error(TcState& t, cudaStream_t st) {
   if (!t.err.p) return 0;
   int e = 0;
@@ -1418,7 +1629,7 @@ void tc_release(TcState& t) {
                     &t.w,       &t.part,    &t.err,     &t.vt,        &t.split.Xa,
                     &t.split.Xlo, &t.split.ra, &t.split.nh, &t.half.Xa,   &t.half.ra,
                     &t.half.nh, &t.tune_v,  &t.tune_q,  &t.sym_rowpart, &t.sym_colpart,
-                    &t.sym_items};
+                    &t.sym_items, &t.rows.Xa, &t.rows.Xlo, &t.rows.ra, &t.rows.nh};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   t = TcState();

@@ -35,6 +35,8 @@ struct TcState {
   double split_sigma = 0.0;
   bool split_ready = false;
   TcOperand half;       // FP16-rounded points (KRR_FP16)
+  TcOperand rows;       // a row set other than the columns (prediction), in the
+                        // format of the product that uses it
   double half_sigma = 0.0;
   bool half_ready = false;
   int autotune = 0;       // 1: time candidate tile plans per shape (process-wide
@@ -65,6 +67,9 @@ struct HpState {
 
 // Grow a device buffer to at least `bytes` (contents not kept).
 void tc_ensure(DevBuf& b, size_t bytes);
+// TMA map of a K-major BF16 matrix (rows x row_elems, row_elems a multiple of
+// 64), boxes of 64 elements x box_rows rows, 128-byte swizzle.
+void tc_make_map_bf16(CUtensorMap* m, const void* base, int rows, int row_elems, int box_rows);
 
 // Symmetric product (k = 1, d <= 64, no split): only tiles I <= J of 128 x 128,
 // each exponential serving K_ij and K_ji.  C: row blocks per work item,
@@ -89,10 +94,15 @@ void tc_prepare(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int
 // Also the split operands xh = bf16(u) + bf16(u - bf16(u)) (d <= 64).
 void tc_prepare_split(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int d,
                       double sigma);
+// A row set Xr other than the columns, with the columns' mean and scale, in
+// format fmt (0 BF16, 1 split, 2 FP16); the columns must be prepared.
+void tc_prepare_rows(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr, int d,
+                     double sigma, int fmt);
 // Also the FP16-rounded points (same range check as the BF16 set).
 void tc_prepare_f16(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int d,
                     double sigma);
-// Q = K(X, X) V + shift V through the tensor cores (Xr must equal Xc); with
+// Q = K(Xr, Xc) V + shift V through the tensor cores (Xr may differ from Xc
+// except with gemm2); with
 // `split` the dot products use split points (hi.hi + lo.hi + hi.lo); with
 // `f16` the points are rounded to FP16 instead of BF16; with `gemm2` the
 // contraction with V runs on the tensor cores on BF16-rounded kernel entries.
@@ -113,6 +123,11 @@ int tc_tuned_shapes();
 void tc_clear_error(TcState& t, cudaStream_t st);
 // Nonzero if any launch hit a bounded-wait limit since the state was created.
 int tc_error(TcState& t, cudaStream_t st);
+// Q = (D o K(Xr, Xc)) V with D_ij = ||x_i - x_j||^2 / sigma^2 (the derivative
+// of K in log sigma) on the rounded points (BF16, split or FP16), any row set.
+void tc_dsigma_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr,
+                      const float* Xc, int nc, int ldxc, int d, double sigma, const float* V,
+                      int k, int ldv, float* Q, int ldq, int split, int f16);
 void tc_release(TcState& t);
 
 }  // namespace krr

@@ -116,7 +116,7 @@ def test_precond_apply_matches_oracle(K, h, form):
     P = ks.make_config(1, n=300, s=70)
     Z = O.rff_features(P.X, P.W, P.b).astype(np.float32)
     lam_p = 1e-2
-    K.krr_precond_setup(h, dev(Z), lam_p, form, z_bf16=False)
+    K.krr_precond_setup(h, dev(Z), lam_p, form, z_format="fp32")
     rng = np.random.default_rng(3)
     R = rng.standard_normal((300, 3))
     out = torch.empty((300, 3), dtype=torch.float64, device="cuda")
@@ -136,7 +136,7 @@ def test_precond_bf16_storage_is_consistent(K, h):
     Z = O.rff_features(P.X, P.W, P.b).astype(np.float32)
     Zb = torch.from_numpy(Z).to(torch.bfloat16).to(torch.float64).numpy()
     lam_p = 1e-3
-    K.krr_precond_setup(h, dev(Z), lam_p, "zl", z_bf16=True)
+    K.krr_precond_setup(h, dev(Z), lam_p, "zl", z_format="bf16")
     rng = np.random.default_rng(4)
     V = rng.standard_normal((1000, 2))
     Mv = Zb @ (Zb.T @ V) + lam_p * V
