@@ -38,7 +38,8 @@ import math
 
 import numpy as np
 
-__all__ = ["Problem", "make_config", "make_uneven", "rff_draw", "CONFIGS"]
+__all__ = ["Problem", "make_config", "make_uneven", "rff_draw", "tensorsketch_draw",
+           "srht_draw", "gaussian_draw", "CONFIGS"]
 
 
 @dataclasses.dataclass
@@ -95,6 +96,23 @@ def tensorsketch_draw(seed: int, d: int, q: int, s: int) -> tuple[np.ndarray, np
     h = rng.integers(0, s, size=(q, d)).astype(np.int32)
     g = (2 * rng.integers(0, 2, size=(q, d)) - 1).astype(np.int8)
     return h, g
+
+
+def srht_draw(seed: int, m: int, s2: int) -> tuple[np.ndarray, np.ndarray]:
+    """Draw a subsampled randomized Hadamard transform of size s2 x m (Section 4):
+    the diagonal of random signs D (m int8 in {-1, +1}) and the sampled rows of
+    P (s2 distinct int32 indices, uniform without replacement, sorted)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    signs = (2 * rng.integers(0, 2, size=m) - 1).astype(np.int8)
+    rows = np.sort(rng.choice(m, size=s2, replace=False)).astype(np.int32)
+    return signs, rows
+
+
+def gaussian_draw(seed: int, s3: int, s2: int) -> np.ndarray:
+    """An s3 x s2 matrix of independent standard normal entries (the dense
+    projection of Algorithm 2), rounded to float32."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.standard_normal((s3, s2)).astype(np.float32)
 
 
 def _cfg1(n: int, s: int | None) -> Problem:

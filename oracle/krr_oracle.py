@@ -42,6 +42,17 @@ Sketching and Preconditioning"):
                                  E phi(x)^T phi(z) = (gamma x^T z + c)^q.
 * ``krr_poly_pcg_solve``      -- Algorithm 1 for the polynomial kernel with the
                                  TensorSketch preconditioner.
+* ``walsh_hadamard``, ``srht_apply``, ``gaussian_projection``,
+  ``multilevel_features``, ``krr_multilevel_pcg_solve``
+                              -- Algorithm 2 (Section 4): the SRHT
+                                 s2^-1/2 P H D of the features, then a dense
+                                 Gaussian projection (reading: the algorithm
+                                 omits the Cholesky step and writes Z for Z3).
+* ``eig_projector``, ``condition1_norm``, ``condition1_power``,
+  ``adaptive_sketch_size``
+                              -- Section 5 / Theorem 4: the projection P, the
+                                 first condition ||(I-P)K(I-P)|| <= 0.1 lambda
+                                 by power iteration, and doubling s.
 * ``kernel_dlogsigma``        -- D o K, the derivative of K in log sigma.
 * ``hypergrad``               -- gradient of a held-out MSE with respect to
                                  log sigma and log lambda (not in the paper;
@@ -412,6 +423,125 @@ def krr_poly_pcg_solve(X, Y, gamma: float, c: float, q: int, lam: float, h, g, s
     A = poly_kernel(X, X, gamma, c, q)
     A[np.diag_indices_from(A)] += lam
     return pcg(lambda V: A @ V, lambda R: precond_apply(P, R), Y, tol, max_iter)
+
+
+# ---------------------------------------- multiple-level sketching ---
+
+def walsh_hadamard(m: int) -> np.ndarray:
+    """H_m of Section 4 from its recursive definition: H_2 = [[1, 1], [1, -1]],
+    H_m = [[H_{m/2}, H_{m/2}], [H_{m/2}, -H_{m/2}]] (m a power of 2)."""
+    if m < 1 or m & (m - 1):
+        raise ValueError("m must be a power of 2")
+    H = np.ones((1, 1))
+    while H.shape[0] < m:
+        H = np.block([[H, H], [H, -H]])
+    return H
+
+
+def srht_apply(Z1, signs, rows) -> np.ndarray:
+    """Z2 = Z1 S2^T for the SRHT S2 = s2^-1/2 P H D of Section 4 (its definition):
+    D = diag(signs) (m random signs), H = H_m, P keeps rows `rows` of H D.  The
+    s1 columns of Z1 are padded with zeros to m = len(signs)."""
+    Z1 = np.asarray(Z1, np.float64)
+    m, s2 = len(signs), len(rows)
+    if Z1.shape[1] > m:
+        raise ValueError("m must be at least the number of columns of Z1")
+    Zp = np.zeros((Z1.shape[0], m))
+    Zp[:, :Z1.shape[1]] = Z1
+    D = np.asarray(signs, np.float64)
+    H = walsh_hadamard(m)
+    S2 = H[np.asarray(rows), :] * D[None, :] / math.sqrt(s2)
+    return Zp @ S2.T
+
+
+def gaussian_projection(Z2, G) -> np.ndarray:
+    """Z3 = s3^-1/2 Z2 S3^T with S3 = G, an s3 x s2 matrix of independent
+    standard normal entries (Algorithm 2)."""
+    G = np.asarray(G, np.float64)
+    return np.asarray(Z2, np.float64) @ G.T / math.sqrt(G.shape[0])
+
+
+def multilevel_features(Z1, signs, rows, G) -> np.ndarray:
+    """Z3 of Algorithm 2: the SRHT of the first-level features, then the dense
+    Gaussian projection."""
+    return gaussian_projection(srht_apply(Z1, signs, rows), G)
+
+
+def krr_multilevel_pcg_solve(X, Y, sigma: float, lam: float, W, b, signs, rows, G,
+                             lam_p: float | None = None, tol: float = 1e-6,
+                             max_iter: int = 1000) -> dict:
+    """Algorithm 2 for the Gaussian kernel: random Fourier features Z1 (s1 of
+    them), Z2 = Z1 S2^T (SRHT), Z3 = s3^-1/2 Z2 S3^T, then PCG on K + lambda I
+    with the preconditioner Z3 Z3^T + lambda_p I in the Woodbury form."""
+    X = np.asarray(X, np.float64)
+    Y = np.asarray(Y, np.float64).reshape(X.shape[0], -1)
+    Z3 = multilevel_features(rff_features(X, W, b), signs, rows, G)
+    P = precond_setup(Z3, lam if lam_p is None else lam_p)
+    A = kernel_matrix_system(X, sigma, lam)
+    out = pcg(lambda V: A @ V, lambda R: precond_apply(P, R), Y, tol, max_iter)
+    out["precond"] = P
+    return out
+
+
+# ---------------------------------------------- adaptive sketch size ---
+
+def eig_projector(Z, thresh: float) -> np.ndarray:
+    """P of Theorem 4: the orthogonal projection on the eigenvectors of Z Z^T
+    whose eigenvalues exceed `thresh` (from the SVD Z = U S V^T: the columns of U
+    with s_k^2 > thresh)."""
+    U, sv, _ = np.linalg.svd(np.asarray(Z, np.float64), full_matrices=False)
+    Uk = U[:, sv * sv > thresh]
+    return Uk @ Uk.T
+
+
+def condition1_norm(K, P) -> float:
+    """||(I - P) K (I - P)||_2 of Theorem 4's first condition, exactly (dense)."""
+    n = K.shape[0]
+    R = np.eye(n) - P
+    return float(np.max(np.abs(np.linalg.eigvalsh(R @ K @ R))))
+
+
+def condition1_power(matvec, P, x0, iters: int) -> float:
+    """Power iteration for ||(I - P) K (I - P)||_2 (Theorem 4: "testing condition 1
+    can be accomplished using simple power-iteration"), from the start vector
+    x0; `matvec` applies K.  Returns the last Rayleigh quotient."""
+    x = np.asarray(x0, np.float64).reshape(-1)
+    x = x / np.linalg.norm(x)
+    est = 0.0
+    for _ in range(iters):
+        y = x - P @ x
+        w = matvec(y)
+        w = w - P @ w
+        est = float(x @ w)
+        nw = np.linalg.norm(w)
+        if nw == 0.0:
+            return 0.0
+        x = w / nw
+    return est
+
+
+def adaptive_sketch_size(X, sigma: float, lam: float, W, b, s0: int, x0,
+                         iters: int = 30) -> dict:
+    """Section 5's adaptive choice of s with Theorem 4's first condition: from
+    s = s0, form the random Fourier features of the first s columns of (W, b),
+    test ||(I - P) K (I - P)|| <= 0.1 lambda (P: eigenvalues of Z Z^T above
+    0.05 lambda) by power iteration from x0, and double s until the test passes
+    or s reaches the number of columns of W (the second condition's test is
+    left out, as in the paper)."""
+    X = np.asarray(X, np.float64)
+    s_max = np.asarray(W).shape[1]
+    K = gaussian_kernel(X, X, sigma)
+    s = s0
+    history = []
+    while True:
+        Z = rff_features(X, np.asarray(W)[:, :s], np.asarray(b)[:s])
+        P = eig_projector(Z, 0.05 * lam)
+        est = condition1_power(lambda v: K @ v, P, x0, iters)
+        history.append((s, est))
+        if est <= 0.1 * lam or s >= s_max:
+            return {"s": s, "Z": Z, "estimate": est, "history": history,
+                    "passed": est <= 0.1 * lam}
+        s = min(2 * s, s_max)
 
 
 # ------------------------------------------------------------- gradient ---

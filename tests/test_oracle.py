@@ -449,3 +449,136 @@ def test_golden_six_point_problem_frozen():
     np.testing.assert_allclose(pre["U"], g["U"], rtol=1e-10, atol=1e-13)
     # the fixture's PCG and direct solutions agree (s=3 < n=6, tol 1e-12)
     np.testing.assert_allclose(g["c_pcg"], g["c_direct"], rtol=1e-9, atol=1e-10)
+
+
+# ------------------------------------------- multiple-level sketching ---
+
+@pytest.mark.parametrize("m", [1, 2, 4, 8, 32, 64])
+def test_walsh_hadamard_is_sylvesters_matrix(m):
+    """H_m from the recursion equals scipy's Sylvester Hadamard matrix and
+    H H^T = m I."""
+    import scipy.linalg as sla
+    H = O.walsh_hadamard(m)
+    assert np.array_equal(H, sla.hadamard(m))
+    np.testing.assert_array_equal(H @ H.T, m * np.eye(m))
+
+
+def test_walsh_hadamard_rejects_non_powers_of_two():
+    with pytest.raises(ValueError):
+        O.walsh_hadamard(12)
+
+
+def test_srht_without_subsampling_is_orthogonal():
+    """With every row kept (s2 = m), S2 = m^-1/2 H D is orthogonal, so
+    Z2 Z2^T = Z1 Z1^T exactly (up to rounding)."""
+    rng = np.random.default_rng(0)
+    Z1 = rng.standard_normal((20, 13))
+    signs, rows = ks.srht_draw(1, 16, 16)
+    Z2 = O.srht_apply(Z1, signs, rows)
+    np.testing.assert_allclose(Z2 @ Z2.T, Z1 @ Z1.T, rtol=1e-12, atol=1e-12)
+
+
+def test_srht_of_a_unit_vector():
+    """Closed form: for z1 = e_j, (S2 z1)_k = signs_j H[rows_k, j] / sqrt(s2); for
+    j = 0 (a column of ones in H) every entry is signs_0 / sqrt(s2)."""
+    signs, rows = ks.srht_draw(2, 32, 8)
+    Z1 = np.zeros((2, 32))
+    Z1[0, 0] = 1.0
+    Z1[1, 5] = 1.0
+    Z2 = O.srht_apply(Z1, signs, rows)
+    np.testing.assert_allclose(Z2[0], signs[0] / math.sqrt(8) * np.ones(8), rtol=1e-15)
+    bits = np.array([bin(int(r) & 5).count("1") for r in rows])
+    np.testing.assert_allclose(Z2[1], signs[5] * (-1.0) ** bits / math.sqrt(8), rtol=1e-15)
+
+
+def test_srht_is_unbiased():
+    """E S2^T S2 = I (signs and sampled rows random): the mean of Z2 Z2^T over
+    draws approaches Z1 Z1^T with error ~ draws^-1/2."""
+    rng = np.random.default_rng(3)
+    Z1 = rng.standard_normal((6, 50))
+    G1 = Z1 @ Z1.T
+    errs = []
+    for draws in (50, 800):
+        acc = np.zeros_like(G1)
+        for t in range(draws):
+            signs, rows = ks.srht_draw(1000 + t, 64, 16)
+            Z2 = O.srht_apply(Z1, signs, rows)
+            acc += Z2 @ Z2.T
+        errs.append(np.linalg.norm(acc / draws - G1) / np.linalg.norm(G1))
+    assert errs[1] < 0.5 * errs[0] and errs[1] < 0.05, errs
+
+
+def test_gaussian_projection_is_unbiased_and_exact_for_scaled_identity():
+    rng = np.random.default_rng(4)
+    Z2 = rng.standard_normal((5, 12))
+    # S3 = sqrt(s3) I gives Z3 = Z2
+    np.testing.assert_allclose(O.gaussian_projection(Z2, math.sqrt(12) * np.eye(12)), Z2,
+                               rtol=1e-14)
+    acc = np.zeros((5, 5))
+    draws = 400
+    for t in range(draws):
+        Z3 = O.gaussian_projection(Z2, ks.gaussian_draw(50 + t, 8, 12))
+        acc += Z3 @ Z3.T
+    G2 = Z2 @ Z2.T
+    assert np.linalg.norm(acc / draws - G2) / np.linalg.norm(G2) < 0.06
+
+
+def test_multilevel_pcg_matches_direct_solve():
+    """Algorithm 2 (RFF -> SRHT -> Gaussian projection -> Woodbury PCG) reaches the
+    direct solution of Eq. (1)."""
+    P = ks.make_config(1, n=400, s=128)
+    signs, rows = ks.srht_draw(7, 128, 64)
+    G = ks.gaussian_draw(8, 48, 64)
+    out = O.krr_multilevel_pcg_solve(P.X, P.Y, P.sigma, P.lam, P.W, P.b, signs, rows, G,
+                                     tol=1e-10, max_iter=2000)
+    assert out["status"] == "converged"
+    c = O.direct_solve(P.X, P.Y, P.sigma, P.lam)
+    kappa = np.linalg.cond(O.kernel_matrix_system(P.X, P.sigma, P.lam))
+    assert np.linalg.norm(out["x"] - c) <= kappa * 1e-10 * np.linalg.norm(c)
+
+
+# ---------------------------------------------- adaptive sketch size ---
+
+def test_eig_projector_properties():
+    rng = np.random.default_rng(5)
+    Z = rng.standard_normal((30, 8)) * np.linspace(0.01, 3.0, 8)
+    M = Z @ Z.T
+    ev = np.linalg.eigvalsh(M)
+    thresh = 0.5
+    P = O.eig_projector(Z, thresh)
+    np.testing.assert_allclose(P @ P, P, atol=1e-12)
+    np.testing.assert_allclose(P, P.T, atol=1e-14)
+    np.testing.assert_allclose(P @ M, M @ P, atol=1e-10)
+    assert round(np.trace(P)) == int(np.sum(ev > thresh))
+    assert np.allclose(O.eig_projector(Z, 1e9), 0.0)
+    Pr = O.eig_projector(Z, -1.0)   # the whole range of Z
+    np.testing.assert_allclose(Pr @ Z, Z, atol=1e-10)
+
+
+def test_condition1_power_iteration_converges_to_the_norm():
+    P = ks.make_config(1, n=200, s=16)
+    K = O.gaussian_kernel(P.X, P.X, P.sigma)
+    Z = O.rff_features(P.X, P.W, P.b)
+    Pp = O.eig_projector(Z, 0.05 * P.lam)
+    exact = O.condition1_norm(K, Pp)
+    x0 = np.random.default_rng(9).standard_normal(200)
+    est = O.condition1_power(lambda v: K @ v, Pp, x0, 300)
+    assert est == pytest.approx(exact, rel=1e-6)
+    # with P = I the condition holds trivially (zero)
+    assert O.condition1_norm(K, np.eye(200)) == pytest.approx(0.0, abs=1e-12)
+
+
+def test_adaptive_sketch_size_doubles_until_condition1_holds():
+    P = ks.make_config(1, n=300)
+    W, b = ks.rff_draw(77, P.d, 2048, P.sigma)
+    x0 = np.random.default_rng(1).standard_normal(300)
+    lam = 1e-1
+    out = O.adaptive_sketch_size(P.X, P.sigma, lam, W, b, 16, x0, iters=60)
+    ss = [s for s, _ in out["history"]]
+    assert ss[0] == 16 and all(b2 == 2 * a for a, b2 in zip(ss, ss[1:]))
+    assert out["passed"] and out["estimate"] <= 0.1 * lam
+    # every rejected s failed the test
+    assert all(est > 0.1 * lam for _, est in out["history"][:-1])
+    # capped at the columns available
+    capped = O.adaptive_sketch_size(P.X, P.sigma, 1e-9, W[:, :64], b[:64], 16, x0, iters=20)
+    assert capped["s"] == 64 and not capped["passed"]
