@@ -87,7 +87,10 @@ typedef struct {
   double tol;          /* relative residual target tau (default 1e-6)        */
   int max_iter;        /* PCG iteration cap (default 1000, Section 5)        */
   double lambda_p;     /* preconditioner ridge; 0 means lambda (Table 2)     */
-  int precond;         /* 1: RFF Woodbury preconditioner, 0: plain CG        */
+  int precond;         /* 1: RFF Woodbury preconditioner, 0: plain CG,       */
+                       /* 2: keep the handle's preconditioner from the last  */
+                       /* krr_precond_setup (any features: caller's,         */
+                       /* multiple-level, adaptive) -- single solves only    */
   int precision;       /* krr_precision; KRR_MIXED adds refinement           */
   int apply_form;      /* krr_apply_form                                     */
   int use_graph;       /* 1: PCG loop as a CUDA-graph while node             */
@@ -97,8 +100,11 @@ typedef struct {
                        /* -1 auto: KRR_Z_FIXED for KRR_MIXED (features and   */
                        /* Gram on the tensor cores), else KRR_Z_FP32         */
   int warm_start;      /* 1: C holds x0 on entry                             */
-  int inner_precision; /* KRR_MIXED: product of the inner PCG, KRR_FP16 or   */
-                       /* KRR_BF16 (0: the default, KRR_FP16)                */
+  int inner_precision; /* KRR_MIXED: product of the inner PCG, KRR_FP16,     */
+                       /* KRR_BF16 or KRR_BF16X3 (split points, d <= 64),    */
+                       /* or KRR_HP (FP64 vectors and HP products from the   */
+                       /* start: PCG in FP64-grade arithmetic throughout)    */
+                       /* (0: the default, KRR_FP16)                         */
   int keep_direction;  /* KRR_MIXED: 1 continues the previous inner solve's  */
                        /* search direction after the residual is replaced   */
                        /* (k <= 5); 0 (default) restarts each at p = z      */
@@ -151,11 +157,11 @@ const char* krr_status_string(krr_status s);
  * not depend on timing.  on = 2 selects, without timing, the symmetric
  * product where it applies (one right-hand side, d <= 64, BF16 or FP16
  * points): only the tiles on and above the block diagonal, each exponential
- * serving K_ij and K_ji -- half the exponentials, though on GB300 it runs
- * slower than the full product.  Batched solves pass the setting to their
- * problems.  `shapes` (may be NULL) receives the number of shapes tuned so
- * far in this process.  Errors: KRR_EINVAL for a NULL handle or on outside
- * 0..2.
+ * serving K_ij and K_ji (half the exponentials), with 16 epilogue warps;
+ * on = 3 the same with 8 epilogue warps.  Batched solves pass the setting to
+ * their problems.  `shapes` (may be NULL) receives the number of shapes
+ * tuned so far in this process.  Errors: KRR_EINVAL for a NULL handle or on
+ * outside 0..3.
  */
 krr_status krr_set_autotune(krr_handle* h, int on, int* shapes);
 
@@ -328,6 +334,104 @@ krr_status krr_predict(krr_handle* h, const float* Xtr, int n, int ldxtr,
                        const float* Xte, int m, int ldxte, int d, double sigma,
                        const double* C, int k, int ldc, double* F, int ldf,
                        int precision);
+
+/* ------------------------------------------- polynomial kernel -------- */
+/*
+ * The paper's second kernel (Section 6): k(x, z) = (gamma x^T z + c)^q,
+ * gamma > 0, c >= 0, 1 <= q <= 8, with its TensorSketch feature map
+ * (Section 2.2) as the preconditioner's features.
+ */
+
+/*
+ * TensorSketch features Z = phi(X) (Section 2.2): with x~ = [sqrt(gamma) x,
+ * sqrt(c)] (the extra coordinate only when c > 0; d~ = d + 1, else d),
+ *   phi(x)[H] = sum of g_1(i_1)..g_q(i_q) x~_{i_1}..x~_{i_q} over the index
+ *               tuples with (h_1(i_1) + .. + h_q(i_q)) mod s = H,
+ * so E phi(x)^T phi(z) = (gamma x^T z + c)^q.  hash: q x d~ int32 in [0, s),
+ * sign: q x d~ int8 in {-1, +1} (row t is the t-th CountSketch; host or
+ * device, checked on the host: KRR_EINVAL when out of range).  X: n x d
+ * (ldx) FP32 on the device, Z: n x s (ldz >= s) FP32 on the device; FP32
+ * arithmetic.  s <= 25,600.
+ */
+krr_status krr_tensorsketch_features(krr_handle* h, const float* X, int n, int d, int ldx,
+                                     const int* hash, const signed char* sign, int q, int s,
+                                     double gamma, double c, float* Z, int ldz);
+
+/*
+ * Polynomial-kernel product Q = P(Xr, Xc) V + shift V, P_ij = (gamma
+ * xr_i.xc_j + c)^q.  precision: KRR_FP64 (FP64 dot products, any row set;
+ * V, Q double) or, for the training system (Xr == Xc), the fused tensor-core
+ * kernel on rounded points, KRR_FP16, KRR_BF16 or KRR_BF16X3 (x rounded
+ * without scaling or centring, the power on the FMA pipe; V, Q float;
+ * KRR_EUNSUPPORTED when a point overflows FP16/BF16).  Device pointers.
+ */
+krr_status krr_kernel_matvec_poly(krr_handle* h, const float* Xr, int nr, int ldxr,
+                                  const float* Xc, int nc, int ldxc, int d, double gamma,
+                                  double c, int q, double shift, const void* V, int k, int ldv,
+                                  void* Q, int ldq, int precision);
+
+/*
+ * Algorithm 1 for the polynomial kernel: solve (P + lambda I) C = Y with PCG,
+ * preconditioned by (Z Z^T + lambda_p I)^-1 through the Woodbury identity,
+ * Z the TensorSketch features of X (hash, sign as for
+ * krr_tensorsketch_features; unused when opts->precond = 0).  Arguments,
+ * staging and report as for krr_pcg_solve; opts->precision is KRR_FP64 (FP64
+ * products) or KRR_MIXED (tensor-core inner solves on rounded points,
+ * refinement with FP64 residuals).
+ */
+krr_status krr_poly_pcg_solve(krr_handle* h, const float* X, int n, int d, int ldx, double gamma,
+                              double c, int q, double lambda, const int* hash,
+                              const signed char* sign, int s, const double* Y, int k, int ldy,
+                              double* C, int ldc, const krr_opts* opts, krr_report* rep);
+
+/* ------------------------------------ multiple-level sketching -------- */
+/*
+ * Features of Algorithm 2 (Section 4) from first-level features Z1 (n x s1,
+ * ldz1; random Fourier or TensorSketch features):
+ *   Z2 = Z1 S2^T,  S2 = s2^-1/2 P H D  (a subsampled randomized Walsh-Hadamard
+ *                                        transform: D = diag(signs), H = H_m,
+ *                                        P keeps rows `rows` of H D),
+ *   Z3 = s3^-1/2 Z2 G^T                 (G: s3 x s2 standard normal entries).
+ * m: a power of two with s1 <= m <= 32768 (Z1's rows are zero-padded to m);
+ * signs: m int8 in {-1, +1}; rows: s2 int32 in [0, m) (host or device,
+ * checked on the host); s3 <= s2 <= m.  Z1, G (FP32, row-major) and Z3
+ * (n x s3, ldz3, FP32) in device memory.  The transform runs per row in
+ * shared memory (log2 m butterfly passes); Z2 G^T on tcgen05 from split BF16
+ * operands (about 2^-16 of sum |z2||g| per entry).  Feed Z3 to
+ * krr_precond_setup and solve with opts->precond = 2.
+ */
+krr_status krr_multilevel_features(krr_handle* h, const float* Z1, int n, int s1, int ldz1,
+                                   const signed char* signs, int m, const int* rows, int s2,
+                                   const float* G, int s3, float* Z3, int ldz3);
+
+/* ------------------------------------------ adaptive sketch size ------ */
+/*
+ * Preconditioner set-up with the number of random Fourier features chosen
+ * adaptively (Section 5, Theorem 4), for the Gaussian kernel: from s = s0,
+ * features Z of the first s columns of W (d x s_max, row-major) and b are
+ * tested against Theorem 4's first condition
+ *     ||(I - P) K (I - P)||_2 <= 0.1 lambda,
+ * P the orthogonal projection on the eigenvectors of Z Z^T with eigenvalues
+ * above 0.05 lambda, by `power_iters` steps of power iteration from x0 (n
+ * doubles); s doubles (capped at s_max) until the test passes.  P comes from
+ * the s x s Gram matrix: P = Z G^-1 Pi Z^T with Pi the spectral projection of
+ * G on eigenvalues above 0.05 lambda, sign(I - 2 tau (G + tau I)^-1) by
+ * `ns_iters` Newton-Schulz steps (FP64; 25 resolves eigenvalues within about
+ * 1 % of the threshold).  The second condition's test is left out (the paper
+ * omits it).  product_precision: the K products of the power iteration,
+ * KRR_FP64, KRR_HP or KRR_FP16.  The handle's preconditioner is then set up
+ * from the chosen features with lambda_p (0: lambda), apply_form and
+ * z_format (krr_z_format; -1: KRR_Z_FP32); solve with opts->precond = 2.
+ * *s_out: the chosen s; estimates (may be NULL, room for log2(s_max/s0) + 2
+ * values): the power-iteration estimate at each s tried; *tests_out (may be
+ * NULL): how many s were tried.  X, W, b, x0: host or device.
+ */
+krr_status krr_precond_setup_adaptive(krr_handle* h, const float* X, int n, int d, int ldx,
+                                      double sigma, double lambda, const float* W,
+                                      const float* b, int s_max, int s0, const double* x0,
+                                      int power_iters, int ns_iters, int product_precision,
+                                      double lambda_p, int apply_form, int z_format, int* s_out,
+                                      double* estimates, int* tests_out);
 
 /* --------------------------------------- hyper-parameter gradient ------ */
 /*

@@ -93,6 +93,16 @@ _SIGS = {
     "krr_hypergrad": (_i, [_vp, _vp, _i, _i, _i, _vp, _i, _i, _d, _d, _vp, _vp, _i, _vp, _i, _vp,
                            _i, _i, C.POINTER(krr_opts), C.POINTER(_d), _vp, _i,
                            C.POINTER(krr_report)]),
+    "krr_tensorsketch_features": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _i, _i, _d, _d, _vp,
+                                       _i]),
+    "krr_kernel_matvec_poly": (_i, [_vp, _vp, _i, _i, _vp, _i, _i, _i, _d, _d, _i, _d, _vp, _i,
+                                    _i, _vp, _i, _i]),
+    "krr_poly_pcg_solve": (_i, [_vp, _vp, _i, _i, _i, _d, _d, _i, _d, _vp, _vp, _i, _vp, _i, _i,
+                                _vp, _i, C.POINTER(krr_opts), C.POINTER(krr_report)]),
+    "krr_multilevel_features": (_i, [_vp, _vp, _i, _i, _i, _vp, _i, _vp, _i, _vp, _i, _vp, _i]),
+    "krr_precond_setup_adaptive": (_i, [_vp, _vp, _i, _i, _i, _d, _d, _vp, _vp, _i, _i, _vp, _i,
+                                        _i, _i, _d, _i, _i, C.POINTER(_i), C.POINTER(_d),
+                                        C.POINTER(_i)]),
     "krr_launch_count": (C.c_longlong, []),
     "krr_bench_ex2": (_i, [_vp, _i, C.POINTER(_d), C.POINTER(_d)]),
     "krr_bench_ex2_mix": (_i, [_vp, _i, _i, C.POINTER(_d), C.POINTER(_d)]),
@@ -154,12 +164,13 @@ class Handle:
 
     def set_autotune(self, on=True) -> int:
         """Tile-plan selection: False/0 the fixed rule, True/1 autotune, 2 the
-        symmetric product where it applies; returns the shapes tuned so far."""
+        symmetric product where it applies (16 epilogue warps), 3 the same with 8;
+        returns the shapes tuned so far."""
         n = _i(0)
         mode = int(on) if not isinstance(on, bool) else (1 if on else 0)
         st = _lib.krr_set_autotune(self._h, mode, C.byref(n))
         if st != KRR_OK:
-            raise KrrError(st, "krr_set_autotune: mode must be 0, 1 or 2")
+            raise KrrError(st, "krr_set_autotune: mode must be 0, 1, 2 or 3")
         return n.value
 
     def _check(self, st: int):
@@ -287,6 +298,82 @@ def krr_pcg_solve(h: Handle, X, sigma: float, lam: float, W, b, Y, C_out, opts: 
     out = rep.as_dict()
     out["status_code"] = st
     return out
+
+
+def krr_tensorsketch_features(h: Handle, X, hash_, sign, s: int, gamma: float, c: float, Z):
+    """TensorSketch features of the polynomial kernel (gamma x.z + c)^q into Z (n x s
+    float32); hash_ (q x d~ int32) and sign (q x d~ int8) are the q CountSketches."""
+    n, d = X.shape
+    q = hash_.shape[0]
+    h._check(_lib.krr_tensorsketch_features(h.ptr, _ptr(X), n, d, _ld(X), _ptr(hash_),
+                                            _ptr(sign), q, int(s), float(gamma), float(c),
+                                            _ptr(Z), _ld(Z)))
+    return Z
+
+
+def krr_kernel_matvec_poly(h: Handle, Xr, Xc, gamma: float, c: float, q: int, shift: float, V, Q,
+                           precision="fp64"):
+    """Q = (gamma Xr Xc^T + c)^q V + shift V (float64 for "fp64", float32 for the
+    tensor-core precisions "fp16", "bf16", "bf16x3")."""
+    nr, d = Xr.shape
+    nc = Xc.shape[0]
+    k = V.shape[1]
+    prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    h._check(_lib.krr_kernel_matvec_poly(h.ptr, _ptr(Xr), nr, _ld(Xr), _ptr(Xc), nc, _ld(Xc), d,
+                                         float(gamma), float(c), int(q), float(shift), _ptr(V),
+                                         k, _ld(V), _ptr(Q), _ld(Q), prec))
+    return Q
+
+
+def krr_poly_pcg_solve(h: Handle, X, gamma: float, c: float, q: int, lam: float, hash_, sign,
+                       s: int, Y, C_out, opts: krr_opts | None = None, check: bool = True) -> dict:
+    """Algorithm 1 for the polynomial kernel with the TensorSketch preconditioner."""
+    n, d = X.shape
+    k = Y.shape[1]
+    rep = krr_report()
+    o = opts if opts is not None else default_opts()
+    st = _lib.krr_poly_pcg_solve(h.ptr, _ptr(X), n, d, _ld(X), float(gamma), float(c), int(q),
+                                 float(lam), _ptr(hash_) if hash_ is not None else None,
+                                 _ptr(sign) if sign is not None else None, int(s), _ptr(Y), k,
+                                 _ld(Y), _ptr(C_out), _ld(C_out), C.byref(o), C.byref(rep))
+    if check:
+        h._check(st)
+    out = rep.as_dict()
+    out["status_code"] = st
+    return out
+
+
+def krr_multilevel_features(h: Handle, Z1, signs, rows, G, Z3):
+    """Algorithm 2's features: Z3 = s3^-1/2 (Z1 S2^T) G^T with the SRHT S2 = s2^-1/2 P H D
+    (signs: m int8, rows: s2 int32) and G (s3 x s2 float32); Z1, Z3 float32."""
+    n, s1 = Z1.shape
+    s3, s2 = G.shape
+    h._check(_lib.krr_multilevel_features(h.ptr, _ptr(Z1), n, s1, _ld(Z1), _ptr(signs),
+                                          len(signs), _ptr(rows), s2, _ptr(G), s3, _ptr(Z3),
+                                          _ld(Z3)))
+    return Z3
+
+
+def krr_precond_setup_adaptive(h: Handle, X, sigma: float, lam: float, W, b, s0: int, x0,
+                               power_iters: int = 30, ns_iters: int = 25, precision="fp64",
+                               lambda_p: float = 0.0, apply_form="zl", z_format=-1) -> dict:
+    """Theorem 4's adaptive sketch size: double s from s0 (up to W's columns) until
+    ||(I - P) K (I - P)|| <= 0.1 lambda; sets up the handle's preconditioner with the
+    chosen features.  Returns {"s", "estimates", "tests"}."""
+    n, d = X.shape
+    s_max = W.shape[1]
+    est = (C.c_double * 64)()
+    s_out, tests = C.c_int(), C.c_int()
+    prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    form = APPLY_FORM[apply_form] if isinstance(apply_form, str) else int(apply_form)
+    zf = Z_FORMAT[z_format] if isinstance(z_format, str) else int(z_format)
+    h._check(_lib.krr_precond_setup_adaptive(h.ptr, _ptr(X), n, d, _ld(X), float(sigma),
+                                             float(lam), _ptr(W), _ptr(b), s_max, int(s0),
+                                             _ptr(x0), int(power_iters), int(ns_iters), prec,
+                                             float(lambda_p), form, zf, C.byref(s_out), est,
+                                             C.byref(tests)))
+    return {"s": s_out.value, "estimates": [est[i] for i in range(tests.value)],
+            "tests": tests.value}
 
 
 def krr_pcg_solve_batched(h: Handle, problems, opts: krr_opts | None = None,

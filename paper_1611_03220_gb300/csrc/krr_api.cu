@@ -37,6 +37,15 @@ struct krr_handle {
   TcState tc;
   HpState hp;
   std::vector<krr_handle*> subs;  // per-problem handles of krr_pcg_solve_batched
+  // The kernel of the solve in progress: the Gaussian kernel unless a
+  // polynomial-kernel solve has set `poly` (products then ignore sigma).
+  struct {
+    int poly = 0;
+    double gamma = 1.0, c = 0.0;
+    int q = 1;
+    const float* X = nullptr;  // the training points of that solve
+    int n = 0, ldx = 0, d = 0;
+  } kern;
 };
 
 namespace krr {
@@ -169,9 +178,43 @@ double ms_between(cudaEvent_t a, cudaEvent_t b) {
 // --------------------------------------------------------- kernel product --
 // Q = K(Xr, Xc) V + shift V in the requested arithmetic; V/Q double for
 // FP64/HP, float for FP32/BF16.
+// Products of the polynomial kernel (gamma x.z + c)^q: FP64 SIMT for KRR_FP64
+// and KRR_HP (the refinement residual), the fused tensor-core kernel on
+// rounded points for KRR_BF16, KRR_FP16 and KRR_BF16X3 (training system only).
+void poly_dispatch(krr_handle* h, cudaStream_t st, const float* Xr, int nr, int ldxr,
+                   const float* Xc, int nc, int ldxc, int d, double shift, const void* V, int k,
+                   int ldv, void* Q, int ldq, int prec) {
+  const auto& K = h->kern;
+  switch (prec) {
+    case KRR_FP64:
+    case KRR_HP: {
+      double* part = wsT<double>(h, "mv_part64", mv_fp64_part_elems(nr, nc, k));
+      launch_mv_fp64_poly(st, Xr, nr, ldxr, Xc, nc, ldxc, d, K.gamma, K.c, K.q, shift,
+                          (const double*)V, k, ldv, (double*)Q, ldq, part);
+      return;
+    }
+    case KRR_BF16:
+    case KRR_FP16:
+    case KRR_BF16X3: {
+      if (!(Xr == Xc && nr == nc && ldxr == ldxc))
+        throw Error{KRR_EUNSUPPORTED, "polynomial tensor-core product: training system only"};
+      tc_poly_matvec(h->tc, st, Xc, nc, ldxc, d, K.gamma, K.c, K.q, shift, (const float*)V, k,
+                     ldv, (float*)Q, ldq, prec == KRR_BF16X3 ? 1 : 0, prec == KRR_FP16 ? 1 : 0);
+      return;
+    }
+    default:
+      throw Error{KRR_EUNSUPPORTED, "polynomial kernel: precision must be KRR_FP64, KRR_HP, "
+                                    "KRR_BF16, KRR_FP16 or KRR_BF16X3"};
+  }
+}
+
 void matvec_dispatch(krr_handle* h, cudaStream_t st, const float* Xr, int nr, int ldxr,
                      const float* Xc, int nc, int ldxc, int d, double sigma, double shift,
                      const void* V, int k, int ldv, void* Q, int ldq, int prec) {
+  if (h->kern.poly) {
+    poly_dispatch(h, st, Xr, nr, ldxr, Xc, nc, ldxc, d, shift, V, k, ldv, Q, ldq, prec);
+    return;
+  }
   const bool same = (Xr == Xc && nr == nc && ldxr == ldxc);
   if (prec == KRR_HP && same && hp_supported(d)) {
     hp_matvec(h->hp, st, Xr, nr, ldxr, d, sigma, shift, (const double*)V, k, ldv, (double*)Q, ldq);
@@ -218,6 +261,17 @@ void matvec_dispatch(krr_handle* h, cudaStream_t st, const float* Xr, int nr, in
 // Allocate the product's workspace ahead of a graph capture (no allocation
 // may happen while the loop body is being captured).
 void matvec_reserve(krr_handle* h, int n, int k, int prec) {
+  if (h->kern.poly) {
+    if (prec == KRR_FP64 || prec == KRR_HP) {
+      wsT<double>(h, "mv_part64", mv_fp64_part_elems(n, n, k));
+    } else {
+      const auto& ps = h->kern;
+      tc_poly_prepare(h->tc, h->stream, ps.X, ps.n, ps.ldx, ps.d,
+                      prec == KRR_BF16X3 ? 1 : (prec == KRR_FP16 ? 2 : 0));
+      tc_poly_reserve(h->tc, h->stream, k);
+    }
+    return;
+  }
   switch (prec) {
     case KRR_FP64:
       wsT<double>(h, "mv_part64", mv_fp64_part_elems(n, n, k));
@@ -745,9 +799,11 @@ double inner_tol_for(int level, const krr_opts& o, double rel) {
   return std::min(o.inner_tol, std::max(level == INNER_SPLIT ? 1e-5 : 1e-11, want));
 }
 
-// Product of the lowest inner level: FP16 points unless BF16 was asked for.
+// Product of the lowest inner level: FP16 points unless BF16 or split BF16
+// points (d <= 64) were asked for (KRR_HP skips the low levels altogether).
 int low_precision(const krr_opts& o) {
-  return o.inner_precision == KRR_BF16 ? KRR_BF16 : KRR_FP16;
+  if (o.inner_precision == KRR_BF16 || o.inner_precision == KRR_BF16X3) return o.inner_precision;
+  return KRR_FP16;
 }
 
 const char* level_name(int level) {
@@ -832,7 +888,7 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
   int remaining = a.o.max_iter;
   // the inner arithmetic moves up a level (FP16 -> BF16x3 -> HP) once a
   // correction contracts the residual by less than a half (see batched_mixed)
-  int level = INNER_LOW;
+  int level = a.o.inner_precision == KRR_HP ? INNER_HP : INNER_LOW;
   double rel_prev = 0.0;
   double rel[KRR_MAX_RHS] = {0}, rel_saved[KRR_MAX_RHS] = {0};
   // consecutive low-level inner solves continue the previous search
@@ -934,7 +990,8 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
       S.tol = inner_tol_for(level, a.o, rel_prev);
       S.max_iter = remaining;
       S.prec = level == INNER_SPLIT ? KRR_BF16X3 : KRR_HP;
-      if (level == INNER_SPLIT) tc_prepare_split(h->tc, st, a.X, n, a.ldx, a.d, a.sigma);
+      if (level == INNER_SPLIT && !h->kern.poly)
+        tc_prepare_split(h->tc, st, a.X, n, a.ldx, a.d, a.sigma);
       double_inner_ops(h, a.X, n, a.ldx, a.d, a.sigma, a.lambda, k, level, a.o.precond != 0,
                        S.matvec, S.apply);
       launch_convert<double, double>(st, Rs, n, k, k, S.r, k, one);
@@ -981,14 +1038,16 @@ void check_solve_args(const krr_opts& o, int n, int d, int ldx, double sigma, do
   KRR_REQUIRE(o.tol > 0.0 && o.max_iter >= 0, "pcg_solve: bad tol / max_iter");
   KRR_REQUIRE(o.precision == KRR_FP64 || o.precision == KRR_FP32 || o.precision == KRR_MIXED,
               "pcg_solve: precision must be KRR_FP64, KRR_FP32 or KRR_MIXED");
-  if (o.precond) {
+  KRR_REQUIRE(o.precond >= 0 && o.precond <= 2, "pcg_solve: precond must be 0, 1 or 2");
+  if (o.precond == 1) {
     KRR_REQUIRE(W && b && s > 0 && s <= n, "pcg_solve: preconditioner needs W, b and 0 < s <= n");
   }
   if (o.precision == KRR_MIXED) {
     KRR_REQUIRE(o.inner_tol > 0.0 && o.inner_tol < 1.0, "pcg_solve: inner_tol in (0, 1)");
     KRR_REQUIRE(o.inner_precision == 0 || o.inner_precision == KRR_FP16 ||
-                    o.inner_precision == KRR_BF16,
-                "pcg_solve: inner_precision must be 0, KRR_FP16 or KRR_BF16");
+                    o.inner_precision == KRR_BF16 || o.inner_precision == KRR_BF16X3 ||
+                    o.inner_precision == KRR_HP,
+                "pcg_solve: inner_precision must be 0, KRR_FP16, KRR_BF16, KRR_BF16X3 or KRR_HP");
   }
 }
 
@@ -998,7 +1057,10 @@ void check_solve_args(const krr_opts& o, int n, int d, int ldx, double sigma, do
 void setup_impl(krr_handle* h, const float* Xd, int n, int d, int ldx, double sigma,
                 double lambda, const float* Wd, const float* bd, int s, const krr_opts& o) {
   cudaStream_t st = h->stream;
-  if (o.precond) {
+  if (o.precond == 2)
+    KRR_REQUIRE(h->pc.ready && h->pc.n == n,
+                "pcg_solve: precond = 2 needs a preconditioner set up for these n points");
+  if (o.precond == 1) {
     const int zf = o.z_format < 0 ? (o.precision == KRR_MIXED ? KRR_Z_FIXED : KRR_Z_FP32)
                                 : o.z_format;
     const double lp = o.lambda_p > 0.0 ? o.lambda_p : lambda;
@@ -1013,6 +1075,8 @@ void setup_impl(krr_handle* h, const float* Xd, int n, int d, int ldx, double si
   if (o.precision == KRR_MIXED) {
     if (low_precision(o) == KRR_FP16)
       tc_prepare_f16(h->tc, st, Xd, n, ldx, d, sigma);
+    else if (low_precision(o) == KRR_BF16X3)
+      tc_prepare_split(h->tc, st, Xd, n, ldx, d, sigma);
     else
       tc_prepare(h->tc, st, Xd, n, ldx, d, sigma);
     tc_clear_error(h->tc, st);
@@ -1382,6 +1446,7 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
   const ColScale one = ones();
   for (BItem& it : B) {
     krr_handle* g = it.sub;
+    if (o.inner_precision == KRR_HP) it.level = INNER_HP;
     const size_t nk = (size_t)it.n * it.k;
     double* Yc = wsT<double>(g, "v_y", nk);
     double* Cd = wsT<double>(g, "v_cd", nk);
@@ -1537,7 +1602,7 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
 extern "C" {
 
 krr_status krr_set_autotune(krr_handle* h, int on, int* shapes) {
-  if (!h || on < 0 || on > 2) return KRR_EINVAL;
+  if (!h || on < 0 || on > 3) return KRR_EINVAL;
   tc_set_autotune(h->tc, on);
   for (krr_handle* sub : h->subs) tc_set_autotune(sub->tc, on);
   if (shapes) *shapes = tc_tuned_shapes();
@@ -1755,7 +1820,7 @@ krr_status krr_pcg_solve(krr_handle* h, const float* X, int n, int d, int ldx, d
     int matvecs = 0;
     const float* Wd = nullptr;
     const float* bd = nullptr;
-    if (o.precond) {
+    if (o.precond == 1) {
       Wd = (const float*)stage_in(h, W, (size_t)d * s * sizeof(float), "W");
       bd = (const float*)stage_in(h, b, (size_t)s * sizeof(float), "b");
     }
@@ -1836,6 +1901,7 @@ krr_status krr_pcg_solve_batched(krr_handle* h, const krr_problem* probs, int np
       it.C = it.c_host ? wsT<double>(g, "stage_C", (size_t)p.n * p.ldc) : p.C;
       const float* Wd = nullptr;
       const float* bd = nullptr;
+      KRR_REQUIRE(o.precond != 2, "pcg_solve_batched: precond must be 0 or 1");
       if (o.precond) {
         Wd = (const float*)stage_in(g, p.W, (size_t)p.d * p.s * sizeof(float), "W");
         bd = (const float*)stage_in(g, p.b, (size_t)p.s * sizeof(float), "b");
@@ -2048,7 +2114,7 @@ krr_status krr_hypergrad(krr_handle* h, const float* X, int n, int d, int ldx, c
     const double* Gd = (const double*)stage_in(h, GF, (size_t)m * ldg * sizeof(double), "hG");
     const float* Wd = nullptr;
     const float* bd = nullptr;
-    if (o.precond) {
+    if (o.precond == 1) {
       Wd = (const float*)stage_in(h, W, (size_t)d * s * sizeof(float), "W");
       bd = (const float*)stage_in(h, b, (size_t)s * sizeof(float), "b");
     }
@@ -2115,6 +2181,313 @@ extern "C" krr_status krr_bench_ex2_mix(krr_handle* h, int iters, int fma_per_32
                     fma_per_32 == 16 || fma_per_32 == 32,
                 "bench_ex2_mix: fma_per_32 must be one of 0 2 4 6 8 10 12 16 32");
     *exp2_per_s = bench_ex2_mix(h->stream, iters, fma_per_32, ms);
+    return KRR_OK;
+  });
+}
+
+// ------------------------------------------------ polynomial kernel ------
+namespace {
+
+// The TensorSketch tables, checked on the host (every hash in [0, s), every
+// sign +-1: an out-of-range hash would address outside the sketch) and
+// staged on the device.
+void stage_sketch_tables(krr_handle* h, const int* hash, const signed char* sign, int q, int dd,
+                         int s, const int** hd, const signed char** sd) {
+  const size_t m = (size_t)q * dd;
+  std::vector<int> hh(m);
+  std::vector<signed char> sh(m);
+  KRR_CUDA(cudaMemcpy(hh.data(), hash, m * sizeof(int), cudaMemcpyDefault));
+  KRR_CUDA(cudaMemcpy(sh.data(), sign, m, cudaMemcpyDefault));
+  for (size_t i = 0; i < m; ++i) {
+    KRR_REQUIRE(hh[i] >= 0 && hh[i] < s, "tensorsketch: hash values must lie in [0, s)");
+    KRR_REQUIRE(sh[i] == 1 || sh[i] == -1, "tensorsketch: signs must be +1 or -1");
+  }
+  *hd = (const int*)stage_in(h, hash, m * sizeof(int), "ts_hash");
+  *sd = (const signed char*)stage_in(h, sign, m, "ts_sign");
+}
+
+// Makes the handle's products the polynomial kernel's for one call.
+struct PolyKernelScope {
+  krr_handle* h;
+  PolyKernelScope(krr_handle* hh, double gamma, double c, int q, const float* X, int n, int ldx,
+                  int d)
+      : h(hh) {
+    h->kern.poly = 1;
+    h->kern.gamma = gamma;
+    h->kern.c = c;
+    h->kern.q = q;
+    h->kern.X = X;
+    h->kern.n = n;
+    h->kern.ldx = ldx;
+    h->kern.d = d;
+  }
+  ~PolyKernelScope() { h->kern.poly = 0; }
+};
+
+void check_poly(double gamma, double c, int q) {
+  KRR_REQUIRE(gamma > 0.0 && std::isfinite(gamma), "polynomial kernel: gamma must be > 0");
+  KRR_REQUIRE(c >= 0.0 && std::isfinite(c), "polynomial kernel: c must be >= 0");
+  KRR_REQUIRE(q >= 1 && q <= 8, "polynomial kernel: need 1 <= q <= 8");
+}
+
+}  // namespace
+
+extern "C" krr_status krr_tensorsketch_features(krr_handle* h, const float* X, int n, int d,
+                                                int ldx, const int* hash,
+                                                const signed char* sign, int q, int s,
+                                                double gamma, double c, float* Z, int ldz) {
+  return guard(h, [&]() -> krr_status {
+    KRR_REQUIRE(X && hash && sign && Z, "tensorsketch: null pointer");
+    KRR_REQUIRE(n > 0 && d > 0 && s > 0 && ldx >= d && ldz >= s, "tensorsketch: bad sizes");
+    check_poly(gamma, c, q);
+    const int dd = d + (c > 0.0 ? 1 : 0);
+    const int* hd = nullptr;
+    const signed char* sd = nullptr;
+    stage_sketch_tables(h, hash, sign, q, dd, s, &hd, &sd);
+    launch_tensorsketch(h->stream, X, n, d, ldx, hd, sd, q, s, gamma, c, Z, ldz);
+    return KRR_OK;
+  });
+}
+
+extern "C" krr_status krr_kernel_matvec_poly(krr_handle* h, const float* Xr, int nr, int ldxr,
+                                             const float* Xc, int nc, int ldxc, int d,
+                                             double gamma, double c, int q, double shift,
+                                             const void* V, int k, int ldv, void* Q, int ldq,
+                                             int precision) {
+  return guard(h, [&]() -> krr_status {
+    KRR_REQUIRE(Xr && Xc && V && Q, "kernel_matvec_poly: null pointer");
+    KRR_REQUIRE(nr > 0 && nc > 0 && d > 0 && k >= 1 && k <= KRR_MAX_RHS,
+                "kernel_matvec_poly: bad sizes");
+    KRR_REQUIRE(ldxr >= d && ldxc >= d && ldv >= k && ldq >= k,
+                "kernel_matvec_poly: leading dimension too small");
+    KRR_REQUIRE(shift == 0.0 || nr == nc, "kernel_matvec_poly: shift needs a square product");
+    KRR_REQUIRE(precision == KRR_FP64 || precision == KRR_BF16 || precision == KRR_FP16 ||
+                    precision == KRR_BF16X3,
+                "kernel_matvec_poly: precision must be KRR_FP64, KRR_BF16, KRR_FP16 or "
+                "KRR_BF16X3");
+    check_poly(gamma, c, q);
+    PolyKernelScope scope(h, gamma, c, q, Xc, nc, ldxc, d);
+    matvec_dispatch(h, h->stream, Xr, nr, ldxr, Xc, nc, ldxc, d, 1.0, shift, V, k, ldv, Q, ldq,
+                    precision);
+    if (precision != KRR_FP64 && tc_error(h->tc, h->stream))
+      throw Error{KRR_ETIMEOUT, "tensor-core product: a pipeline wait hit its limit"};
+    return KRR_OK;
+  });
+}
+
+extern "C" krr_status krr_poly_pcg_solve(krr_handle* h, const float* X, int n, int d, int ldx,
+                                         double gamma, double c, int q, double lambda,
+                                         const int* hash, const signed char* sign, int s,
+                                         const double* Y, int k, int ldy, double* C, int ldc,
+                                         const krr_opts* opts, krr_report* rep) {
+  return guard(h, [&]() -> krr_status {
+    krr_opts o;
+    if (opts)
+      o = *opts;
+    else
+      krr_default_opts(&o);
+    KRR_REQUIRE(X && Y && C, "poly_pcg_solve: null pointer");
+    KRR_REQUIRE(n > 0 && d > 0 && k >= 1 && k <= KRR_MAX_RHS, "poly_pcg_solve: bad sizes");
+    KRR_REQUIRE(ldx >= d && ldy >= k && ldc >= k, "poly_pcg_solve: leading dimension too small");
+    KRR_REQUIRE(lambda > 0.0 && std::isfinite(lambda), "poly_pcg_solve: lambda must be > 0");
+    KRR_REQUIRE(o.tol > 0.0 && o.max_iter >= 0, "poly_pcg_solve: bad tol / max_iter");
+    KRR_REQUIRE(o.precision == KRR_FP64 || o.precision == KRR_MIXED,
+                "poly_pcg_solve: precision must be KRR_FP64 or KRR_MIXED");
+    if (o.precision == KRR_MIXED) {
+      KRR_REQUIRE(o.inner_tol > 0.0 && o.inner_tol < 1.0, "poly_pcg_solve: inner_tol in (0, 1)");
+      KRR_REQUIRE(o.inner_precision == 0 || o.inner_precision == KRR_FP16 ||
+                      o.inner_precision == KRR_BF16 || o.inner_precision == KRR_BF16X3 ||
+                    o.inner_precision == KRR_HP,
+                  "poly_pcg_solve: inner_precision must be 0, KRR_FP16, KRR_BF16, KRR_BF16X3 or KRR_HP");
+    }
+    check_poly(gamma, c, q);
+    KRR_REQUIRE(o.precond >= 0 && o.precond <= 2, "poly_pcg_solve: precond must be 0, 1 or 2");
+    if (o.precond == 1)
+      KRR_REQUIRE(hash && sign && s > 0 && s <= n,
+                  "poly_pcg_solve: the preconditioner needs hash, sign and 0 < s <= n");
+    if (o.precond == 2)
+      KRR_REQUIRE(h->pc.ready && h->pc.n == n,
+                  "poly_pcg_solve: precond = 2 needs a preconditioner set up for these n points");
+    if (rep) {
+      memset(rep, 0, sizeof(*rep));
+      rep->k = k;
+    }
+    cudaStream_t st = h->stream;
+    KRR_CUDA(cudaEventRecord(h->ev[0], st));
+    const bool c_host = !on_device(C);
+    const float* Xd = (const float*)stage_in(h, X, (size_t)n * ldx * sizeof(float), "X");
+    const double* Yd = (const double*)stage_in(h, Y, (size_t)n * ldy * sizeof(double), "Y");
+    double* Cd = C;
+    if (c_host) {
+      Cd = wsT<double>(h, "stage_C", (size_t)n * ldc);
+      if (o.warm_start)
+        KRR_CUDA(cudaMemcpyAsync(Cd, C, (size_t)n * ldc * sizeof(double), cudaMemcpyHostToDevice,
+                                 st));
+    }
+    PolyKernelScope scope(h, gamma, c, q, Xd, n, ldx, d);
+    if (o.precond == 1) {
+      // Algorithm 1 with TensorSketch features (Section 2.2) for the preconditioner
+      const int dd = d + (c > 0.0 ? 1 : 0);
+      const int* hd = nullptr;
+      const signed char* sd = nullptr;
+      stage_sketch_tables(h, hash, sign, q, dd, s, &hd, &sd);
+      float* Z = wsT<float>(h, "ts_Z", (size_t)n * s);
+      launch_tensorsketch(st, Xd, n, d, ldx, hd, sd, q, s, gamma, c, Z, s);
+      const int zf = o.z_format < 0 ? (o.precision == KRR_MIXED ? KRR_Z_FIXED : KRR_Z_FP32)
+                                    : o.z_format;
+      const double lp = o.lambda_p > 0.0 ? o.lambda_p : lambda;
+      precond_setup_impl(h, Z, n, s, s, lp, o.apply_form, zf);
+    }
+    KRR_CUDA(cudaEventRecord(h->ev[1], st));
+    int matvecs = 0;
+    SolveArgs a{Xd, n, d, ldx, 1.0, lambda, Yd, k, ldy, Cd, ldc, o};
+    krr_status status = o.precision == KRR_FP64 ? solve_plain<double>(h, a, KRR_FP64, rep, &matvecs)
+                                                : solve_mixed(h, a, rep, &matvecs);
+    if (o.precision == KRR_MIXED && tc_error(h->tc, st)) status = KRR_ETIMEOUT;
+    if (o.precond && precond_error(h)) status = KRR_ETIMEOUT;
+    if (c_host)
+      KRR_CUDA(cudaMemcpyAsync(C, Cd, (size_t)n * ldc * sizeof(double), cudaMemcpyDeviceToHost,
+                               st));
+    KRR_CUDA(cudaEventRecord(h->ev[2], st));
+    KRR_CUDA(cudaEventSynchronize(h->ev[2]));
+    if (rep) {
+      rep->status = status;
+      rep->matvecs = matvecs;
+      rep->ms_setup = ms_between(h->ev[0], h->ev[1]);
+      rep->ms_solve = ms_between(h->ev[1], h->ev[2]);
+      rep->ms_total = ms_between(h->ev[0], h->ev[2]);
+    }
+    if (status != KRR_OK) h->err = krr_status_string(status);
+    return status;
+  });
+}
+
+// ------------------------------------------- multiple-level sketching ---
+extern "C" krr_status krr_multilevel_features(krr_handle* h, const float* Z1, int n, int s1,
+                                              int ldz1, const signed char* signs, int m,
+                                              const int* rows, int s2, const float* G, int s3,
+                                              float* Z3, int ldz3) {
+  return guard(h, [&]() -> krr_status {
+    KRR_REQUIRE(Z1 && signs && rows && G && Z3, "multilevel_features: null pointer");
+    KRR_REQUIRE(n > 0 && s1 > 0 && s2 > 0 && s3 > 0 && ldz1 >= s1 && ldz3 >= s3,
+                "multilevel_features: bad sizes");
+    KRR_REQUIRE(m >= s1 && m > 0 && (m & (m - 1)) == 0 && m <= 32768,
+                "multilevel_features: m must be a power of two, s1 <= m <= 32768");
+    KRR_REQUIRE(s2 <= m && s3 <= s2, "multilevel_features: need s3 <= s2 <= m");
+    // the signs and the sampled rows, checked on the host: a row index out of
+    // range would read outside the transform's buffer
+    std::vector<signed char> sg(m);
+    std::vector<int> rw(s2);
+    KRR_CUDA(cudaMemcpy(sg.data(), signs, (size_t)m, cudaMemcpyDefault));
+    KRR_CUDA(cudaMemcpy(rw.data(), rows, (size_t)s2 * sizeof(int), cudaMemcpyDefault));
+    for (int j = 0; j < m; ++j)
+      KRR_REQUIRE(sg[j] == 1 || sg[j] == -1, "multilevel_features: signs must be +1 or -1");
+    for (int k = 0; k < s2; ++k)
+      KRR_REQUIRE(rw[k] >= 0 && rw[k] < m, "multilevel_features: rows must lie in [0, m)");
+    cudaStream_t st = h->stream;
+    const signed char* sd = (const signed char*)stage_in(h, signs, (size_t)m, "ml_signs");
+    const int* rd = (const int*)stage_in(h, rows, (size_t)s2 * sizeof(int), "ml_rows");
+    float* Z2 = wsT<float>(h, "ml_Z2", (size_t)n * s2);
+    launch_srht(st, Z1, n, s1, ldz1, sd, m, rd, s2, Z2, s2);
+    const int kp = setup_tc_kp(s2);
+    __nv_bfloat16* Ah = wsT<__nv_bfloat16>(h, "ml_ah", (size_t)setup_tc_n_pad(n) * kp);
+    __nv_bfloat16* Al = wsT<__nv_bfloat16>(h, "ml_al", (size_t)setup_tc_n_pad(n) * kp);
+    __nv_bfloat16* Bh = wsT<__nv_bfloat16>(h, "ml_bh", (size_t)setup_tc_s_pad(s3) * kp);
+    __nv_bfloat16* Bl = wsT<__nv_bfloat16>(h, "ml_bl", (size_t)setup_tc_s_pad(s3) * kp);
+    int* err = wsT<int>(h, "ml_err", 4);
+    KRR_CUDA(cudaMemsetAsync(err, 0, 4 * sizeof(int), st));
+    launch_gemm_tc_f32(st, Z2, n, s2, s2, G, s3, s2, (float)(1.0 / std::sqrt((double)s3)), Z3,
+                       ldz3, Ah, Al, Bh, Bl, err);
+    int flag = 0;
+    KRR_CUDA(cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KRR_CUDA(cudaStreamSynchronize(st));
+    if (flag) throw Error{KRR_ETIMEOUT, "multilevel_features: a pipeline wait hit its limit"};
+    return KRR_OK;
+  });
+}
+
+// ------------------------------------------------ adaptive sketch size ---
+extern "C" krr_status krr_precond_setup_adaptive(
+    krr_handle* h, const float* X, int n, int d, int ldx, double sigma, double lambda,
+    const float* W, const float* b, int s_max, int s0, const double* x0, int power_iters,
+    int ns_iters, int product_precision, double lambda_p, int apply_form, int z_format,
+    int* s_out, double* estimates, int* tests_out) {
+  return guard(h, [&]() -> krr_status {
+    KRR_REQUIRE(X && W && b && x0 && s_out, "precond_setup_adaptive: null pointer");
+    KRR_REQUIRE(n > 0 && d > 0 && ldx >= d && s0 > 0 && s0 <= s_max && s_max <= n,
+                "precond_setup_adaptive: need 0 < s0 <= s_max <= n");
+    KRR_REQUIRE(sigma > 0.0 && lambda > 0.0 && std::isfinite(sigma) && std::isfinite(lambda),
+                "precond_setup_adaptive: sigma and lambda must be > 0");
+    KRR_REQUIRE(power_iters >= 1 && ns_iters >= 1, "precond_setup_adaptive: iteration counts");
+    KRR_REQUIRE(product_precision == KRR_FP64 || product_precision == KRR_HP ||
+                    product_precision == KRR_FP16,
+                "precond_setup_adaptive: products in KRR_FP64, KRR_HP or KRR_FP16");
+    cudaStream_t st = h->stream;
+    const float* Xd = (const float*)stage_in(h, X, (size_t)n * ldx * sizeof(float), "X");
+    const float* Wd = (const float*)stage_in(h, W, (size_t)d * s_max * sizeof(float), "ad_Wmax");
+    const float* bd = (const float*)stage_in(h, b, (size_t)s_max * sizeof(float), "b");
+    const double* x0d = (const double*)stage_in(h, x0, (size_t)n * sizeof(double), "ad_x0");
+    double* xv = wsT<double>(h, "ad_x", n);
+    double* yv = wsT<double>(h, "ad_y", n);
+    double* wv = wsT<double>(h, "ad_w", n);
+    float* vf = wsT<float>(h, "ad_vf", n);
+    float* qf = wsT<float>(h, "ad_qf", n);
+    ColScale one;
+    for (int c = 0; c < KRR_MAX_RHS; ++c) one.v[c] = 1.0;
+    const double tau = 0.05 * lambda, bound = 0.1 * lambda;
+    int s = s0, tests = 0;
+    float* Z = nullptr;
+    for (;;) {
+      float* Wc = wsT<float>(h, "ad_W", (size_t)d * s);
+      KRR_CUDA(cudaMemcpy2DAsync(Wc, (size_t)s * sizeof(float), Wd, (size_t)s_max * sizeof(float),
+                                 (size_t)s * sizeof(float), d, cudaMemcpyDeviceToDevice, st));
+      Z = wsT<float>(h, "ad_Z", (size_t)n * s);
+      launch_rff(st, Xd, n, d, ldx, Wc, bd, s, Z, s);
+      double* G = wsT<double>(h, "ad_G", (size_t)s * s);
+      const int nch = gram_chunks(n, s);
+      double* part = wsT<double>(h, "gram_part", (size_t)nch * s * s);
+      launch_gram(st, Z, 0, n, s, 0.0, G, part, nch);
+      double* work = wsT<double>(h, "ad_work", adaptive_work_elems(n, s));
+      adaptive_projector(st, G, s, tau, ns_iters, work, h->info, (int*)h->hostd);
+      // power iteration on (I - P) K (I - P) from x0
+      KRR_CUDA(cudaMemcpyAsync(xv, x0d, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      double nrm = 0.0;
+      host_colnorm2<double>(h, xv, n, 1, 1, &nrm);
+      KRR_REQUIRE(nrm > 0.0, "precond_setup_adaptive: x0 is zero");
+      launch_scale_d(st, xv, n, 1.0 / std::sqrt(nrm));
+      double est = 0.0;
+      for (int it = 0; it < power_iters; ++it) {
+        apply_i_minus_p(st, Z, n, s, work, xv, yv);
+        if (product_precision == KRR_FP16) {
+          launch_convert<double, float>(st, yv, n, 1, 1, vf, 1, one);
+          matvec_dispatch(h, st, Xd, n, ldx, Xd, n, ldx, d, sigma, 0.0, vf, 1, 1, qf, 1,
+                          KRR_FP16);
+          launch_convert<float, double>(st, qf, n, 1, 1, wv, 1, one);
+        } else {
+          matvec_dispatch(h, st, Xd, n, ldx, Xd, n, ldx, d, sigma, 0.0, yv, 1, 1, wv, 1,
+                          product_precision);
+        }
+        apply_i_minus_p(st, Z, n, s, work, wv, yv);
+        est = host_dot(h, xv, 1, yv, 1, n, 1);
+        double nw = 0.0;
+        host_colnorm2<double>(h, yv, n, 1, 1, &nw);
+        if (!(nw > 0.0)) {
+          est = 0.0;
+          break;
+        }
+        KRR_CUDA(cudaMemcpyAsync(xv, yv, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        launch_scale_d(st, xv, n, 1.0 / std::sqrt(nw));
+      }
+      if (estimates) estimates[tests] = est;
+      ++tests;
+      KRR_TRACE("adaptive: s=%d ||(I-P)K(I-P)|| ~ %.3e (bound %.3e)", s, est, bound);
+      if (est <= bound || s >= s_max) break;
+      s = std::min(2 * s, s_max);
+    }
+    *s_out = s;
+    if (tests_out) *tests_out = tests;
+    const double lp = lambda_p > 0.0 ? lambda_p : lambda;
+    precond_setup_impl(h, Z, n, s, s, lp, apply_form, z_format < 0 ? KRR_Z_FP32 : z_format);
     return KRR_OK;
   });
 }

@@ -151,9 +151,40 @@ int launch_rff_tc(cudaStream_t st, const float* X, int n, int d, int ldx, const 
 // Fixed-point copy of a caller's FP32 Z (synchronises once for max |Z|); returns e.
 int launch_quantize_z(cudaStream_t st, const float* Z, int n, int s, int ldz, __nv_bfloat16* Zs,
                       __nv_bfloat16* ZT, int* scratch);
+// F = scale A B^T (A: n x K, B: s x K, FP32 row-major) on tcgen05 from split
+// BF16 operands (about 2^-16 of sum |a||b| per entry); the split buffers are
+// setup_tc_n_pad(n) / setup_tc_s_pad(s) x setup_tc_kp(K) BF16 each.
+void launch_gemm_tc_f32(cudaStream_t st, const float* A, int n, int K, int lda, const float* B,
+                        int s, int ldb, float scale, float* F, int ldf, __nv_bfloat16* Ah,
+                        __nv_bfloat16* Al, __nv_bfloat16* Bh, __nv_bfloat16* Bl, int* err);
+// z2 = s2^-1/2 P H D z1 per row (SRHT, Section 4; krr_sketch.cu): signs (m),
+// rows (s2) on the device, m a power of two >= s1.
+void launch_srht(cudaStream_t st, const float* Z1, int n, int s1, int ldz1,
+                 const signed char* signs, int m, const int* rows, int s2, float* Z2, int ldz2);
 // G = Zs^T Zs + shift I (s x s FP64, exact) from Z^T; part: gram_tc_part_elems ints.
 void launch_gram_tc(cudaStream_t st, const __nv_bfloat16* ZT, int n, int s, double shift,
                     int* part, double* G, int* err);
+
+// Polynomial kernel (gamma x.z + c)^q of Section 6: TensorSketch features
+// (krr_sketch.cu; hash, sign: q x d~ tables on the device, d~ = d + (c > 0))
+// and the FP64 SIMT product (krr_matvec_simt.cu; part: mv_fp64_part_elems).
+void launch_tensorsketch(cudaStream_t st, const float* X, int n, int d, int ldx, const int* hash,
+                         const signed char* sign, int q, int s, double gamma, double c, float* Z,
+                         int ldz);
+void launch_mv_fp64_poly(cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
+                         int nc, int ldxc, int d, double gamma, double c, int q, double shift,
+                         const double* V, int k, int ldv, double* Q, int ldq, double* part);
+
+// Adaptive sketch size (krr_adaptive.cu, Theorem 4).  work: adaptive_work_elems
+// doubles.  adaptive_projector leaves Q = G^-1 Pi (Pi: the spectral projection
+// of G = Z^T Z on eigenvalues above tau) in the work buffer; apply_i_minus_p
+// then gives out = (I - Z Q Z^T) x for FP32 Z (n x s) and FP64 x.
+size_t adaptive_work_elems(int n, int s);
+void adaptive_projector(cudaStream_t st, const double* G, int s, double tau, int ns_iters,
+                        double* work, int* info_dev, int* info_host);
+void apply_i_minus_p(cudaStream_t st, const float* Z, int n, int s, const double* work,
+                     const double* x, double* out);
+void launch_scale_d(cudaStream_t st, double* x, int n, double a);
 
 // Preconditioner (krr_precond.cu)
 void launch_copy_z(cudaStream_t st, const float* Z, int n, int s, int ldz, void* Zs, int bf16);

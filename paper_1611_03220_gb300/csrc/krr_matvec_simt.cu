@@ -32,12 +32,14 @@ int choose_split(int row_blocks, int col_tiles) {
 
 // DS = 1 evaluates the derivative dK/dlog(sigma) = D o K instead of K, with
 // D_ij = ||x_i - x_j||^2 / sigma^2 = -2 g ||x_i - x_j||^2 (g = -1 / (2 sigma^2)).
+// DS = 2 evaluates the polynomial kernel (g x_i.x_j + pc)^pq of Section 6
+// (g = gamma), the dot product accumulated in FP64.
 template <int DS>
 __global__ void __launch_bounds__(M64_ROWS)
 mv_fp64_kernel(const float* __restrict__ Xr, int nr, int ldxr,
                const float* __restrict__ Xc, int nc, int ldxc, int d, double g,
                const double* __restrict__ V, int k, int ldv,
-               double* __restrict__ part, int tiles_per_split) {
+               double* __restrict__ part, int tiles_per_split, double pc = 0.0, int pq = 1) {
   __shared__ float xs[M64_TJ][M64_DC + 1];
   __shared__ double vs[M64_TJ][KRR_MAX_RHS];
   const int tid = threadIdx.x;
@@ -72,8 +74,12 @@ mv_fp64_kernel(const float* __restrict__ Xr, int nr, int ldxr,
         double a = acc[jj];
 #pragma unroll
         for (int t = 0; t < M64_DC; ++t) {
-          double df = (double)xi[t] - (double)xs[jj][t];
-          a = fma(df, df, a);
+          if (DS == 2) {
+            a = fma((double)xi[t], (double)xs[jj][t], a);
+          } else {
+            double df = (double)xi[t] - (double)xs[jj][t];
+            a = fma(df, df, a);
+          }
         }
         acc[jj] = a;
       }
@@ -87,8 +93,15 @@ mv_fp64_kernel(const float* __restrict__ Xr, int nr, int ldxr,
     __syncthreads();
 #pragma unroll
     for (int jj = 0; jj < M64_TJ; ++jj) {
-      double kv = exp(g * acc[jj]);
-      if (DS) kv *= -2.0 * g * acc[jj];
+      double kv;
+      if (DS == 2) {
+        const double base = fma(g, acc[jj], pc);
+        kv = base;
+        for (int e = 1; e < pq; ++e) kv *= base;
+      } else {
+        kv = exp(g * acc[jj]);
+        if (DS) kv *= -2.0 * g * acc[jj];
+      }
 #pragma unroll
       for (int c = 0; c < KRR_MAX_RHS; ++c)
         if (c < k) q[c] = fma(kv, vs[jj][c], q[c]);
@@ -249,6 +262,23 @@ void launch_mv_fp64(cudaStream_t st, const float* Xr, int nr, int ldxr, const fl
   else
     mv_fp64_kernel<0><<<dim3(rb, ns), M64_ROWS, 0, st>>>(Xr, nr, ldxr, Xc, nc, ldxc, d, g, V, k,
                                                           ldv, part, tps);
+  KRR_CHECK_LAUNCH();
+  int nb = (int)std::min<size_t>(((size_t)nr * k + 255) / 256, (size_t)8 * sm_count());
+  reduce_split_kernel<double, double><<<nb, 256, 0, st>>>(part, ns, nr, k, V, ldv, shift, Q, ldq);
+  KRR_CHECK_LAUNCH();
+}
+
+// Q = P(Xr, Xc) V + shift V for the polynomial kernel (gamma x.z + c)^q in FP64.
+void launch_mv_fp64_poly(cudaStream_t st, const float* Xr, int nr, int ldxr, const float* Xc,
+                         int nc, int ldxc, int d, double gamma, double c, int q, double shift,
+                         const double* V, int k, int ldv, double* Q, int ldq, double* part) {
+  int rb = (nr + M64_ROWS - 1) / M64_ROWS;
+  int ct = (nc + M64_TJ - 1) / M64_TJ;
+  int ns = choose_split(rb, ct);
+  int tps = (ct + ns - 1) / ns;
+  ns = (ct + tps - 1) / tps;
+  mv_fp64_kernel<2><<<dim3(rb, ns), M64_ROWS, 0, st>>>(Xr, nr, ldxr, Xc, nc, ldxc, d, gamma, V,
+                                                        k, ldv, part, tps, c, q);
   KRR_CHECK_LAUNCH();
   int nb = (int)std::min<size_t>(((size_t)nr * k + 255) / 256, (size_t)8 * sm_count());
   reduce_split_kernel<double, double><<<nb, 256, 0, st>>>(part, ns, nr, k, V, ldv, shift, Q, ldq);

@@ -61,9 +61,15 @@ constexpr int T = 128;                 // tile edge (rows = columns)
 constexpr int SK = 64;                 // K extent (d <= 64, one K-block)
 constexpr int SUK = 16;                // K per MMA instruction
 constexpr int TILE_BYTES = T * SK * 2; // one 128 x 64 16-bit block
-constexpr int SNEPI = 8;               // epilogue warps: 4 row quadrants x 2 column halves
-constexpr int SCOLS = T / (SNEPI / 4); // columns per epilogue warp (64)
-constexpr int STHREADS = 32 * (2 + SNEPI);
+// Epilogue warps: 4 row quadrants x (SNEPI / 4) column groups of SCOLS
+// columns; 8 (64 columns per thread) or 16 (32 columns, twice the warps to
+// hide TMEM-load and MUFU latency with half the column accumulators).
+template <int SNEPI>
+struct SymCfg {
+  static constexpr int NG = SNEPI / 4;           // column groups
+  static constexpr int SCOLS = T / NG;           // columns per epilogue warp
+  static constexpr int STHREADS = 32 * (2 + SNEPI);
+};
 constexpr int SNS_MAX = 6;
 constexpr int NACC = 4;                // 128-column accumulators in TMEM
 constexpr uint32_t STMEM_COLS = NACC * T;
@@ -97,8 +103,8 @@ __device__ __forceinline__ void ld_wait(uint32_t (&r)[16]) {
                : "memory");
 }
 
-__device__ __forceinline__ void qbar_sync(int id) {
-  asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
+__device__ __forceinline__ void qbar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
 // The exponentials of one 16-column chunk: row sums against the column
@@ -131,16 +137,18 @@ __device__ __forceinline__ void chunk_math(uint32_t (&u)[16], const float* wv, f
   }
 }
 
-__global__ void __launch_bounds__(STHREADS, 1)
+template <int SNEPI>
+__global__ void __launch_bounds__(SymCfg<SNEPI>::STHREADS, 1)
 tc_sym_kernel(const __grid_constant__ CUtensorMap tmX, SymParams p) {
+  constexpr int NG = SymCfg<SNEPI>::NG, SCOLS = SymCfg<SNEPI>::SCOLS;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int NS = p.ns;
   uint8_t* bres = smem;                            // [2] resident column blocks (item parity)
   uint8_t* ring = smem + 2 * TILE_BYTES;           // NS row blocks
   float* wcol = (float*)(ring + NS * TILE_BYTES);  // [2][T] column weights per item parity
-  float* comb = wcol + 2 * T;                      // [2][2][T] row-sum combine per tile parity
-  float* colc = comb + 2 * 2 * T;                  // [4][T] column-sum combine
+  float* comb = wcol + 2 * T;                      // [2][NG][T] row-sum combine per tile parity
+  float* colc = comb + 2 * NG * T;                 // [4][T] column-sum combine
   uint64_t* bars = (uint64_t*)(colc + 4 * T);
   uint64_t* full = bars;
   uint64_t* empty = full + SNS_MAX;
@@ -265,7 +273,7 @@ tc_sym_kernel(const __grid_constant__ CUtensorMap tmX, SymParams p) {
     // ------------------------------------------------------------ epilogue
     const int e = warp - 2;
     const int q = warp & 3;        // TMEM lane quadrant = row quadrant of the tile
-    const int g = e >> 2;          // column half: columns 64 g .. 64 g + 63
+    const int g = e >> 2;          // column group: columns SCOLS g .. SCOLS (g + 1) - 1
     const int r = q * 32 + lane;   // row within the tile
     const int et = e * 32 + lane;  // 0 .. 255
     uint32_t acc = 0, aph = 0, tb = 0, ib = 0;
@@ -281,17 +289,64 @@ tc_sym_kernel(const __grid_constant__ CUtensorMap tmX, SymParams p) {
       bar_sync<SNEPI * 32>();
       const float* wc = wcol + ib * T + g * SCOLS;
       float w_next = p.w[(size_t)it.y * T + r];
-      // chunk 0 of the item's first tile; afterwards the next 16-column
-      // chunk (of this tile or the next) is always in flight while the
-      // current chunk's exponentials run
+      // SNEPI = 8: chunk 0 of the item's first tile; afterwards the next
+      // 16-column chunk (of this tile or the next) is always in flight while
+      // the current chunk's exponentials run.  SNEPI = 16: twice the warps
+      // hide the latencies instead, and one chunk is in registers at a time
+      // (the register budget of 18 warps is 96 per thread).
+      constexpr bool PF = SNEPI == 8;
       uint32_t ua[16], ub[16];
-      if (ok) ok = mbar_wait(smem_u32(&tfull[acc]), aph, abort_flag, p.err);
-      if (ok) {
-        fence_after();
-        tmem_ld16_nowait(tq + acc * T, ua);
-        ld_wait(ua);
+      if (PF) {
+        if (ok) ok = mbar_wait(smem_u32(&tfull[acc]), aph, abort_flag, p.err);
+        if (ok) {
+          fence_after();
+          tmem_ld16_nowait(tq + acc * T, ua);
+          ld_wait(ua);
+        }
       }
       for (int I = it.y; I < it.z; ++I) {
+      if (!PF) {
+        const float w_r = p.w[(size_t)I * T + r];
+        float2 rs[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) rs[m] = make_float2(0.f, 0.f);
+        const bool diag = I == J;
+        if (ok) ok = mbar_wait(smem_u32(&tfull[acc]), aph, abort_flag, p.err);
+        if (ok) {
+          fence_after();
+#pragma unroll
+          for (int kc = 0; kc < SCOLS / 16; ++kc) {
+            tmem_ld16_nowait(tq + acc * T + kc * 16, ua);
+            ld_wait(ua);
+            if (kc + 1 == SCOLS / 16) {
+              // the tile's last chunk is in registers: the accumulator is free
+              fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(smem_u32(&tempty[acc]));
+            }
+            if (diag)
+              chunk_math<true>(ua, wc + kc * 16, w_r, rs, cacc + kc * 8);
+            else
+              chunk_math<false>(ua, wc + kc * 16, w_r, rs, cacc + kc * 8);
+          }
+        }
+        float* cb = comb + tb * NG * T;
+        cb[g * T + r] = ((rs[0].x + rs[0].y) + (rs[1].x + rs[1].y)) +
+                        ((rs[2].x + rs[2].y) + (rs[3].x + rs[3].y));
+        qbar_sync(2 + q, 32 * NG);
+        if (g == 0 && ok) {
+          float t = cb[r];
+#pragma unroll
+          for (int gg = 1; gg < NG; ++gg) t += cb[gg * T + r];
+          p.rowpart[(size_t)J * p.n_pad + (size_t)I * T + r] = t;
+        }
+        tb ^= 1;
+        if (++acc == (uint32_t)NACC) {
+          acc = 0;
+          aph ^= 1;
+        }
+        continue;
+      }
         const float w_r = w_next;
         const bool more = I + 1 < it.z;
         if (more) w_next = p.w[(size_t)(I + 1) * T + r];
@@ -330,25 +385,31 @@ tc_sym_kernel(const __grid_constant__ CUtensorMap tmX, SymParams p) {
             }
           }
         }
-        // row sums of the tile: add the two column halves (fixed order); both
-        // warps of the quadrant pass this barrier once per tile
-        float* cb = comb + tb * 2 * T;
+        // row sums of the tile: add the column groups (fixed order); every
+        // warp of the quadrant passes this barrier once per tile
+        float* cb = comb + tb * NG * T;
         cb[g * T + r] = ((rs[0].x + rs[0].y) + (rs[1].x + rs[1].y)) +
                         ((rs[2].x + rs[2].y) + (rs[3].x + rs[3].y));
-        qbar_sync(2 + q);
-        if (g == 0 && ok)
-          p.rowpart[(size_t)J * p.n_pad + (size_t)I * T + r] = cb[r] + cb[T + r];
+        qbar_sync(2 + q, 32 * NG);
+        if (g == 0 && ok) {
+          float t = cb[r];
+#pragma unroll
+          for (int gg = 1; gg < NG; ++gg) t += cb[gg * T + r];
+          p.rowpart[(size_t)J * p.n_pad + (size_t)I * T + r] = t;
+        }
         tb ^= 1;
         if (++acc == (uint32_t)NACC) {
           acc = 0;
           aph ^= 1;
         }
       }
-      // column sums: reduce-scatter the 64 per-row partials across the warp's
-      // lanes (lane l ends with columns 64 g + 2 l and 64 g + 2 l + 1), then
-      // add the four quadrants
+      // column sums: reduce-scatter the SCOLS per-row partials across the
+      // warp's lanes (lane l ends with the column pair (l mod SCOLS/2) of its
+      // group; with 32 columns lanes l and l + 16 then add theirs), then add
+      // the four quadrants
+      constexpr int NP = SCOLS / 2;   // column pairs per thread
 #pragma unroll
-      for (int s = 16; s >= 1; s >>= 1) {
+      for (int s = NP / 2; s >= 1; s >>= 1) {
         const bool up = (lane & s) != 0;
 #pragma unroll
         for (int j = 0; j < s; ++j) {
@@ -358,10 +419,19 @@ tc_sym_kernel(const __grid_constant__ CUtensorMap tmX, SymParams p) {
           cacc[j].y = keep.y + __shfl_xor_sync(0xffffffffu, send.y, s);
         }
       }
-      colc[q * T + g * SCOLS + 2 * lane] = cacc[0].x;
-      colc[q * T + g * SCOLS + 2 * lane + 1] = cacc[0].y;
+      if (NP < 32) {
+#pragma unroll
+        for (int s = NP; s < 32; s <<= 1) {
+          cacc[0].x += __shfl_xor_sync(0xffffffffu, cacc[0].x, s);
+          cacc[0].y += __shfl_xor_sync(0xffffffffu, cacc[0].y, s);
+        }
+      }
+      if (lane < NP) {
+        colc[q * T + g * SCOLS + 2 * lane] = cacc[0].x;
+        colc[q * T + g * SCOLS + 2 * lane + 1] = cacc[0].y;
+      }
       if (bar_or<SNEPI * 32>(!ok || *abort_flag)) break;
-      if (q == 0) {
+      if (q == 0 && lane < NP) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int c = g * SCOLS + 2 * lane + h;
@@ -412,9 +482,22 @@ __global__ void sym_w_kernel(const float* __restrict__ V, int n, int ldv,
     w[j] = j < n ? ra[j] * V[(size_t)j * ldv] : 0.f;
 }
 
-size_t sym_smem_bytes(int ns) {
-  return 1024 + (size_t)(2 + ns) * TILE_BYTES + (size_t)(2 * T + 4 * T + 4 * T) * 4 +
+size_t sym_smem_bytes(int ns, int nepi) {
+  return 1024 + (size_t)(2 + ns) * TILE_BYTES + (size_t)(2 * T + 2 * (nepi / 4) * T + 4 * T) * 4 +
          (size_t)(2 * SNS_MAX + 2 * NACC + 4 + 1) * 8 + 16;
+}
+
+template <int SNEPI>
+void launch_sym(cudaStream_t st, const CUtensorMap& map, const SymParams& p, int grid) {
+  const size_t sm = sym_smem_bytes(p.ns, SNEPI);
+  static size_t attr = 0;
+  if (attr < sm) {
+    KRR_CUDA(cudaFuncSetAttribute(tc_sym_kernel<SNEPI>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr = sm;
+  }
+  tc_sym_kernel<SNEPI><<<grid, SymCfg<SNEPI>::STHREADS, sm, st>>>(map, p);
+  KRR_CHECK_LAUNCH();
 }
 
 }  // namespace
@@ -459,7 +542,7 @@ void sym_reserve(TcState& t, cudaStream_t st, const TcOperand& op, int C) {
 }
 
 void sym_matvec(TcState& t, cudaStream_t st, const TcOperand& op, int f16, int C, int ns,
-                int nr, const float* V, int ldv, double shift, float* Q, int ldq) {
+                int nr, const float* V, int ldv, double shift, float* Q, int ldq, int nepi) {
   sym_reserve(t, st, op, C);
   const int n_t = op.n_pad / T;
   sym_w_kernel<<<std::min(4 * sm_count(), (op.n_pad + 255) / 256), 256, 0, st>>>(
@@ -475,16 +558,11 @@ void sym_matvec(TcState& t, cudaStream_t st, const TcOperand& op, int f16, int C
   p.rowpart = (float*)t.sym_rowpart.p;
   p.colpart = (float*)t.sym_colpart.p;
   p.err = (int*)t.err.p;
-  const size_t sm = sym_smem_bytes(p.ns);
-  static size_t attr = 0;
-  if (attr < sm) {
-    KRR_CUDA(cudaFuncSetAttribute(tc_sym_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)sm));
-    attr = sm;
-  }
   const int grid = std::min(p.n_items, sm_count());
-  tc_sym_kernel<<<grid, STHREADS, sm, st>>>(op.map_a, p);
-  KRR_CHECK_LAUNCH();
+  if (nepi == 8)
+    launch_sym<8>(st, op.map_a, p, grid);
+  else
+    launch_sym<16>(st, op.map_a, p, grid);
   sym_reduce_kernel<<<op.n_pad / 32, 256, 0, st>>>(
       (const float*)t.sym_rowpart.p, (const float*)t.sym_colpart.p, n_t, op.n_pad, C,
       (const float*)op.ra.p, nr, V, ldv, shift, Q, ldq);

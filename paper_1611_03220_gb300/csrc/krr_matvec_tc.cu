@@ -99,12 +99,15 @@ struct TcParams {
   float* part;      // nchunk x n_rpad x KV
   int* err;
   int ds_k = 0;     // derivative mode: w columns c < ds_k take exp2(S) S, the rest exp2(S)
+  float pg = 0.f, pc = 0.f;  // polynomial mode: entries (pg S + pc)^pq
+  int pq = 1;
 };
 
 // EMU of every 32 exponentials run on the FMA pipe (a tuner dimension for
 // one right-hand side; Cfg<KV>::EMU otherwise).  DS = 1 is the derivative
 // mode of the (D o K) product: the first p.ds_k weight columns are
-// contracted with exp2(S) S instead of exp2(S).
+// contracted with exp2(S) S instead of exp2(S).  DS = 2 is the polynomial
+// kernel (pg S + pc)^pq of Section 6 on the FMA pipe instead of exp2(S).
 template <int KV, int EMU = Cfg<KV>::EMU, int DS = 0>
 __global__ void __launch_bounds__(Cfg<KV>::THREADS, 1)
 tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -326,12 +329,19 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                              *reinterpret_cast<uint32_t(*)[16]>(&raw[cur ^ 1][16]));
           }
           // all exponentials of the chunk first (independent), then the contraction
-          float sv[DS ? 32 : 1];
+          float sv[DS == 1 ? 32 : 1];
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const float s = __uint_as_float(raw[cur][j]);
-            if (DS) sv[j] = s;
-            raw[cur][j] = __float_as_uint((j % PER == PER - 1) ? ex2_fma(s) : ex2_mufu(s));
+            if (DS == 1) sv[j] = s;
+            if (DS == 2) {
+              const float b = fmaf(p.pg, s, p.pc);
+              float r = b;
+              for (int e = 1; e < p.pq; ++e) r *= b;
+              raw[cur][j] = __float_as_uint(r);
+            } else {
+              raw[cur][j] = __float_as_uint((j % PER == PER - 1) ? ex2_fma(s) : ex2_mufu(s));
+            }
           }
           const float4* w4 = reinterpret_cast<const float4*>(wb + (grp * COLS + cc * 32) * KV);
           if (KV == 1 && CH == 2) {
@@ -360,7 +370,7 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                 const int idx = j4 * 4 + u;  // = j * KV + c
                 const int j = idx / KV, c = idx % KV;
                 float ev = __uint_as_float(raw[cur][j]);
-                if (DS && c < p.ds_k) ev *= sv[j];
+                if (DS == 1 && c < p.ds_k) ev *= sv[j];
                 q[j % CH][c] = fmaf(ev, wq[u], q[j % CH][c]);
               }
             }
@@ -820,6 +830,12 @@ __global__ void max_kernel(const float* __restrict__ a, int n, float* __restrict
   }
 }
 
+// ra[i] = 1 for i < n, 0 for the padding (the polynomial kernel has no row factor).
+__global__ void unit_rows_kernel(float* __restrict__ ra, int n, int n_pad) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += gridDim.x * blockDim.x)
+    ra[i] = i < n ? 1.f : 0.f;
+}
+
 // w[j, c] = ra_j v[j, c] for c < k, 0 for padding (rows >= n or c >= k).
 __global__ void make_w_kernel(const float* __restrict__ V, int n, int k, int ldv,
                               const float* __restrict__ ra, int n_pad, int kv,
@@ -999,6 +1015,15 @@ void launch_kernel(cudaStream_t st, const CUtensorMap& a, const CUtensorMap& b,
   KRR_CHECK_LAUNCH();
 }
 
+// The polynomial mode for weight blocks of kv = 1, 4 or 16 columns.
+void dispatch_poly(int kv, cudaStream_t st, const TcOperand& op, const TcParams& p, int grid) {
+  switch (kv) {
+    case 1: launch_kernel<1, 0, 2>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid); break;
+    case 4: launch_kernel<4, Cfg<4>::EMU, 2>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid); break;
+    default: launch_kernel<16, Cfg<16>::EMU, 2>(st, op.map_a, op.map_b, op.map_a2, op.map_b2, p, grid); break;
+  }
+}
+
 // The derivative mode for weight blocks of kv = 4, 8, 12 or 16 columns.
 void dispatch_ds(int kv, cudaStream_t st, const TcOperand& op, const TcParams& p, int grid) {
   switch (kv) {
@@ -1098,6 +1123,7 @@ struct Plan {
   int C = 16;
   int req = 0;  // the chunk request this plan was made from
   int emu = 0;  // exponentials per 32 on the FMA pipe (one right-hand side)
+  int nepi = 16;  // the symmetric kernel's epilogue warps (8 or 16)
 };
 
 // The tile plan: column chunks per row tile from the wave-balance rule, or
@@ -1145,6 +1171,7 @@ struct TuneKey {
 struct Tuned {
   int req, ns, sym, C, emu;
   float ms;
+  int nepi;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, Tuned> g_tuned;
@@ -1247,7 +1274,7 @@ TcOperand& operand_of(TcState& t, int fmt) {
 void run_fused(TcState& t, cudaStream_t st, TcOperand& op, const Plan& pl, int split, int f16,
                int nr, const float* V, int k, int ldv, double shift, float* Q, int ldq) {
   if (pl.sym) {
-    sym_matvec(t, st, op, f16, pl.C, pl.ns, nr, V, ldv, shift, Q, ldq);
+    sym_matvec(t, st, op, f16, pl.C, pl.ns, nr, V, ldv, shift, Q, ldq, pl.nepi);
     return;
   }
   const int nkb = split ? 2 : op.kp / BK;
@@ -1384,6 +1411,52 @@ void run_dsigma(TcState& t, cudaStream_t st, const TcOperand& rop, const TcOpera
   }
 }
 
+// Q = P V + shift V for the polynomial kernel P_ij = (gamma xh_i.xh_j + c)^q
+// on the rounded points of `op` (ra = 1): the fused kernel in its polynomial
+// mode, the same tiles and pipeline as the Gaussian product.
+void run_poly(TcState& t, cudaStream_t st, const TcOperand& op, int split, int f16, double gamma,
+              double c, int q, const float* V, int k, int ldv, double shift, float* Q, int ldq) {
+  const int kv = k <= 1 ? 1 : (k <= 4 ? 4 : 16);
+  const int n_rt = op.n_pad / BM, n_ct = op.n_pad / BN;
+  const int req = choose_nchunk(n_rt, n_ct, sm_count());
+  const int cpc = (n_ct + req - 1) / req;
+  const int nchunk = (n_ct + cpc - 1) / cpc;
+  ensure(t.w, (size_t)op.n_pad * kv * 4);
+  ensure(t.part, (size_t)nchunk * op.n_pad * kv * 4);
+  if (!t.err.p) {
+    ensure(t.err, 16);
+    KRR_CUDA(cudaMemsetAsync(t.err.p, 0, 16, st));
+  }
+  const int nkb = split ? 2 : op.kp / BK;
+  const int a_res = (split || nkb == 1) ? 1 : 0;
+  make_w_kernel<<<std::min(8 * sm_count(), (int)(((size_t)op.n_pad * kv + 255) / 256)), 256, 0,
+                  st>>>(V, op.n, k, ldv, (const float*)op.ra.p, op.n_pad, kv, (float*)t.w.p);
+  KRR_CHECK_LAUNCH();
+  TcParams p;
+  p.n_rt = n_rt;
+  p.n_ct = n_ct;
+  p.nchunk = nchunk;
+  p.cpc = cpc;
+  p.nkb = nkb;
+  p.a_res = a_res;
+  p.ns = default_ns(a_res);
+  p.x3 = split;
+  p.idesc = f16 ? idesc_f16(BM, BN) : idesc_bf16(BM, BN);
+  p.n_rpad = op.n_pad;
+  p.w = (const float*)t.w.p;
+  p.part = (float*)t.part.p;
+  p.err = (int*)t.err.p;
+  p.pg = (float)gamma;
+  p.pc = (float)c;
+  p.pq = q;
+  dispatch_poly(kv, st, op, p, std::min(n_rt * nchunk, sm_count()));
+  const size_t total = (size_t)op.n * k;
+  tc_reduce_kernel<<<std::min(8 * sm_count(), (int)((total + 255) / 256)), 256, 0, st>>>(
+      (const float*)t.part.p, nchunk, op.n_pad, kv, (const float*)op.ra.p, op.n, k, V, ldv,
+      shift, Q, ldq);
+  KRR_CHECK_LAUNCH();
+}
+
 // Time the candidate plans of one shape on the prepared operand (scratch
 // right-hand sides) and return the fastest.
 Tuned tune_shape(TcState& t, cudaStream_t st, TcOperand& op, int k, int fmt) {
@@ -1416,18 +1489,20 @@ Tuned tune_shape(TcState& t, cudaStream_t st, TcOperand& op, int k, int fmt) {
       }
     }
   if (sym_supported(op, k, split))
-    for (int C : {8, 16, 32, 64})
-      for (int ns : {3, 4, 6}) {
-        Plan pl = base;
-        pl.sym = 1;
-        pl.C = C;
-        pl.ns = ns;
-        plans.push_back(pl);
-      }
+    for (int nepi : {8, 16})
+      for (int C : {8, 16, 32, 64})
+        for (int ns : {3, 4, 6}) {
+          Plan pl = base;
+          pl.sym = 1;
+          pl.C = C;
+          pl.ns = ns;
+          pl.nepi = nepi;
+          plans.push_back(pl);
+        }
   cudaEvent_t e0, e1;
   KRR_CUDA(cudaEventCreate(&e0));
   KRR_CUDA(cudaEventCreate(&e1));
-  Tuned best{0, default_ns(a_res), 0, 16, 0, 1e30f};
+  Tuned best{0, default_ns(a_res), 0, 16, 0, 1e30f, 16};
   try {
     for (const Plan& pl : plans) {
       if (pl.sym)
@@ -1451,7 +1526,7 @@ Tuned tune_shape(TcState& t, cudaStream_t st, TcOperand& op, int k, int fmt) {
                 "%.4f ms\n",
                 op.n_pad, op.kp, k, fmt, pl.sym ? "sym" : "full", pl.nchunk, pl.C, pl.ns, pl.emu,
                 ms);
-      if (ms < best.ms) best = Tuned{pl.req, pl.ns, pl.sym, pl.C, pl.emu, ms};
+      if (ms < best.ms) best = Tuned{pl.req, pl.ns, pl.sym, pl.C, pl.emu, ms, pl.nepi};
     }
   } catch (...) {
     cudaEventDestroy(e0);
@@ -1470,10 +1545,11 @@ Plan resolve_plan(TcState& t, cudaStream_t st, TcOperand& op, int k, int gemm2, 
   // the symmetric kernel is a tuner candidate only: at n = 65,536 it
   // measures 0.85 ms against 0.65 ms for this kernel (see krr_matvec_sym.cu)
   Plan pl = plan_for(op, k, gemm2);
-  if (!gemm2 && t.autotune == 2 && sym_supported(op, k, fmt == 1)) {
-    pl.sym = 1;   // asked for explicitly
+  if (!gemm2 && (t.autotune == 2 || t.autotune == 3) && sym_supported(op, k, fmt == 1)) {
+    pl.sym = 1;   // asked for explicitly: 16 (mode 2) or 8 (mode 3) epilogue warps
     pl.C = 32;
     pl.ns = 6;
+    pl.nepi = t.autotune == 2 ? 16 : 8;
     return pl;
   }
   if (gemm2 || t.autotune != 1) return pl;
@@ -1488,6 +1564,7 @@ Plan resolve_plan(TcState& t, cudaStream_t st, TcOperand& op, int k, int gemm2, 
       q.sym = it->second.sym;
       q.C = it->second.C;
       q.emu = it->second.emu;
+      q.nepi = it->second.nepi;
       return q;
     }
   }
@@ -1504,6 +1581,7 @@ Plan resolve_plan(TcState& t, cudaStream_t st, TcOperand& op, int k, int gemm2, 
   q.sym = tu.sym;
   q.C = tu.C;
   q.emu = tu.emu;
+  q.nepi = tu.nepi;
   return q;
 }
 
@@ -1616,6 +1694,55 @@ void tc_dsigma_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int 
   run_dsigma(t, st, same ? cop : t.rows, cop, split, f16, V, k, ldv, Q, ldq);
 }
 
+void tc_poly_prepare(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int d, int fmt) {
+  if (fmt == 1 && d > BK) throw Error{KRR_EUNSUPPORTED, "split BF16 product needs d <= 64"};
+  TcOperand& op = t.poly;
+  if (t.poly_fmt == fmt && op.src == X && op.n == n && op.ld == ldx && op.d == d) return;
+  t.poly_fmt = -1;
+  ensure(t.mu0, (size_t)d * sizeof(double));
+  KRR_CUDA(cudaMemsetAsync(t.mu0.p, 0, (size_t)d * sizeof(double), st));
+  prep_operand(op, st, X, n, ldx, d, (const double*)t.mu0.p, 1.0, fmt == 1, fmt == 2);
+  unit_rows_kernel<<<std::min(8 * sm_count(), (op.n_pad + 255) / 256), 256, 0, st>>>(
+      (float*)op.ra.p, n, op.n_pad);
+  KRR_CHECK_LAUNCH();
+  ensure(t.scal, 16);
+  KRR_CUDA(cudaMemsetAsync(t.scal.p, 0, 16, st));
+  max_kernel<<<std::min(8 * sm_count(), (op.n_pad + 255) / 256), 256, 0, st>>>(
+      (const float*)op.nh.p, op.n_pad, (float*)t.scal.p);
+  KRR_CHECK_LAUNCH();
+  float mx = 0.f;
+  KRR_CUDA(cudaMemcpyAsync(&mx, t.scal.p, sizeof(float), cudaMemcpyDeviceToHost, st));
+  KRR_CUDA(cudaStreamSynchronize(st));
+  if (!std::isfinite(mx))
+    throw Error{KRR_EUNSUPPORTED,
+                "polynomial tensor-core product: a point overflows the 16-bit format; use FP64"};
+  t.poly_fmt = fmt;
+}
+
+void tc_poly_reserve(TcState& t, cudaStream_t st, int k) {
+  if (t.poly_fmt < 0) throw Error{KRR_EINVAL, "polynomial product reserved before its operand"};
+  const TcOperand& op = t.poly;
+  const int kv = k <= 1 ? 1 : (k <= 4 ? 4 : 16);
+  const int n_rt = op.n_pad / BM, n_ct = op.n_pad / BN;
+  const int req = choose_nchunk(n_rt, n_ct, sm_count());
+  const int cpc = (n_ct + req - 1) / req;
+  const int nchunk = (n_ct + cpc - 1) / cpc;
+  ensure(t.w, (size_t)op.n_pad * kv * 4);
+  ensure(t.part, (size_t)nchunk * op.n_pad * kv * 4);
+  if (!t.err.p) {
+    ensure(t.err, 16);
+    KRR_CUDA(cudaMemsetAsync(t.err.p, 0, 16, st));
+  }
+}
+
+void tc_poly_matvec(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int d,
+                    double gamma, double c, int q, double shift, const float* V, int k, int ldv,
+                    float* Q, int ldq, int split, int f16) {
+  if (f16 && split) throw Error{KRR_EUNSUPPORTED, "FP16 points: no split form"};
+  tc_poly_prepare(t, st, X, n, ldx, d, split ? 1 : (f16 ? 2 : 0));
+  run_poly(t, st, t.poly, split, f16, gamma, c, q, V, k, ldv, shift, Q, ldq);
+}
+
 int tc_error(TcState& t, cudaStream_t st) {
   if (!t.err.p) return 0;
   int e = 0;
@@ -1629,7 +1756,8 @@ void tc_release(TcState& t) {
                     &t.w,       &t.part,    &t.err,     &t.vt,        &t.split.Xa,
                     &t.split.Xlo, &t.split.ra, &t.split.nh, &t.half.Xa,   &t.half.ra,
                     &t.half.nh, &t.tune_v,  &t.tune_q,  &t.sym_rowpart, &t.sym_colpart,
-                    &t.sym_items, &t.rows.Xa, &t.rows.Xlo, &t.rows.ra, &t.rows.nh};
+                    &t.sym_items, &t.rows.Xa, &t.rows.Xlo, &t.rows.ra, &t.rows.nh,
+                    &t.poly.Xa, &t.poly.Xlo, &t.poly.ra, &t.poly.nh, &t.mu0};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   t = TcState();

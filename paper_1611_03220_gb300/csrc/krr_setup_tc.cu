@@ -64,10 +64,12 @@ constexpr int MAX_ROWS_PER_ITEM = 131072;
 struct RffParams {
   int n, s, n_pad, s_pad, nkb, n_rt, n_ct;
   const float* b;       // s phases
-  float zscale;         // sqrt(2/s)
+  float zscale;         // sqrt(2/s) (the plain product's scale with MODE 1)
   float qscale;         // 2^(7-e)
   __nv_bfloat16* Z;     // n x s, ld s
   __nv_bfloat16* ZT;    // s_pad x n_pad
+  float* F;             // MODE 1: F = zscale X W (n x s, ld ldf), FP32
+  int ldf;
   int* err;
 };
 
@@ -152,7 +154,10 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
 // ------------------------------------------------------------ features --
 // Work item = (128-row tile of X, 128-column tile of W).  K runs over the
 // kp / 64 blocks of the d coordinates; per block the MMA warp issues
-// hi.hi + lo.hi + hi.lo (12 MMAs).
+// hi.hi + lo.hi + hi.lo (12 MMAs).  MODE 0: the fixed-point random Fourier
+// features; MODE 1: the plain product F = zscale X W in FP32 (the dense
+// Gaussian projection of the multiple-level sketch).
+template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
 rff_tc_kernel(const __grid_constant__ CUtensorMap tmXh, const __grid_constant__ CUtensorMap tmXl,
               const __grid_constant__ CUtensorMap tmWh, const __grid_constant__ CUtensorMap tmWl,
@@ -255,6 +260,15 @@ rff_tc_kernel(const __grid_constant__ CUtensorMap tmXh, const __grid_constant__ 
       const int i = rt * TM + row;
       const int j0 = ct * TN + grp * 64;
       const bool row_ok = i < p.n;
+      if (MODE == 1) {
+        if (row_ok) {
+          float* fr = p.F + (size_t)i * p.ldf;
+#pragma unroll
+          for (int c = 0; c < 64; ++c)
+            if (j0 + c < p.s) fr[j0 + c] = p.zscale * __uint_as_float(raw[c]);
+        }
+        continue;
+      }
 #pragma unroll
       for (int c = 0; c < 64; ++c) {
         const int j = j0 + c;
@@ -568,7 +582,7 @@ int launch_rff_tc(cudaStream_t st, const float* X, int n, int d, int ldx, const 
   tc_make_map_bf16(&mwl, Wl, s_pad, kp, TN);
   const float zscale = (float)std::sqrt(2.0 / s);
   const int e = fixed_point_exponent((double)zscale);
-  RffParams p;
+  RffParams p{};
   p.n = n;
   p.s = s;
   p.n_pad = n_pad;
@@ -585,11 +599,11 @@ int launch_rff_tc(cudaStream_t st, const float* X, int n, int d, int ldx, const 
   const size_t sm = 1024 + (size_t)RFF_NS * 4 * OP_BYTES + 256;
   static size_t attr = 0;
   if (attr < sm) {
-    set_smem(rff_tc_kernel, sm);
+    set_smem(rff_tc_kernel<0>, sm);
     attr = sm;
   }
   const int grid = std::min(p.n_rt * p.n_ct, sm_count());
-  rff_tc_kernel<<<grid, THREADS, sm, st>>>(mxh, mxl, mwh, mwl, p);
+  rff_tc_kernel<0><<<grid, THREADS, sm, st>>>(mxh, mxl, mwh, mwl, p);
   KRR_CHECK_LAUNCH();
   return e;
 }
@@ -644,6 +658,40 @@ void launch_gram_tc(cudaStream_t st, const __nv_bfloat16* ZT, int n, int s, doub
   const size_t total = (size_t)s * s;
   const int nb = (int)std::min<size_t>((total + 255) / 256, (size_t)8 * sm_count());
   gram_tc_finalize_kernel<<<nb, 256, 0, st>>>(part, p.ksplit, s, s_pad, shift, G);
+  KRR_CHECK_LAUNCH();
+}
+
+void launch_gemm_tc_f32(cudaStream_t st, const float* A, int n, int K, int lda, const float* B,
+                        int s, int ldb, float scale, float* F, int ldf, __nv_bfloat16* Ah,
+                        __nv_bfloat16* Al, __nv_bfloat16* Bh, __nv_bfloat16* Bl, int* err) {
+  const int n_pad = setup_tc_n_pad(n), s_pad = setup_tc_s_pad(s), kp = setup_tc_kp(K);
+  launch_split_rows(st, A, n, K, (size_t)lda, 1, n_pad, kp, Ah, Al);
+  launch_split_rows(st, B, s, K, (size_t)ldb, 1, s_pad, kp, Bh, Bl);
+  CUtensorMap mah, mal, mbh, mbl;
+  tc_make_map_bf16(&mah, Ah, n_pad, kp, TM);
+  tc_make_map_bf16(&mal, Al, n_pad, kp, TM);
+  tc_make_map_bf16(&mbh, Bh, s_pad, kp, TN);
+  tc_make_map_bf16(&mbl, Bl, s_pad, kp, TN);
+  RffParams p{};
+  p.n = n;
+  p.s = s;
+  p.n_pad = n_pad;
+  p.s_pad = s_pad;
+  p.nkb = kp / TK;
+  p.n_rt = n_pad / TM;
+  p.n_ct = s_pad / TN;
+  p.zscale = scale;
+  p.F = F;
+  p.ldf = ldf;
+  p.err = err;
+  const size_t sm = 1024 + (size_t)RFF_NS * 4 * OP_BYTES + 256;
+  static size_t attr = 0;
+  if (attr < sm) {
+    set_smem(rff_tc_kernel<1>, sm);
+    attr = sm;
+  }
+  const int grid = std::min(p.n_rt * p.n_ct, sm_count());
+  rff_tc_kernel<1><<<grid, THREADS, sm, st>>>(mah, mal, mbh, mbl, p);
   KRR_CHECK_LAUNCH();
 }
 

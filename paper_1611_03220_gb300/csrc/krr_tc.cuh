@@ -37,6 +37,9 @@ struct TcState {
   TcOperand half;       // FP16-rounded points (KRR_FP16)
   TcOperand rows;       // a row set other than the columns (prediction), in the
                         // format of the product that uses it
+  TcOperand poly;       // unscaled, uncentred rounded points of the polynomial kernel
+  int poly_fmt = -1;    // their format (0 BF16, 1 split, 2 FP16; -1 none)
+  DevBuf mu0;           // d zeros (the polynomial kernel is not shift invariant)
   double half_sigma = 0.0;
   bool half_ready = false;
   int autotune = 0;       // 1: time candidate tile plans per shape (process-wide
@@ -76,8 +79,9 @@ void tc_make_map_bf16(CUtensorMap* m, const void* base, int rows, int row_elems,
 // ns: TMA ring stages.
 bool sym_supported(const TcOperand& op, int k, int split);
 void sym_reserve(TcState& t, cudaStream_t st, const TcOperand& op, int C);
+// nepi: epilogue warps, 8 or 16.
 void sym_matvec(TcState& t, cudaStream_t st, const TcOperand& op, int f16, int C, int ns,
-                int nr, const float* V, int ldv, double shift, float* Q, int ldq);
+                int nr, const float* V, int ldv, double shift, float* Q, int ldq, int nepi = 16);
 
 bool hp_supported(int d);
 void hp_prepare(HpState& t, cudaStream_t st, const float* X, int n, int ldx, int d, double sigma);
@@ -123,6 +127,17 @@ int tc_tuned_shapes();
 void tc_clear_error(TcState& t, cudaStream_t st);
 // Nonzero if any launch hit a bounded-wait limit since the state was created.
 int tc_error(TcState& t, cudaStream_t st);
+// Q = P(X, X) V + shift V for the polynomial kernel (gamma x.z + c)^q
+// (Section 6) on rounded points (BF16, split or FP16); S = xh_i.xh_j on the
+// tensor cores, the power on the FMA pipe.
+void tc_poly_matvec(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int d,
+                    double gamma, double c, int q, double shift, const float* V, int k, int ldv,
+                    float* Q, int ldq, int split, int f16);
+// The polynomial product's operand in format fmt (0 BF16, 1 split, 2 FP16),
+// kept until X or the format changes, and its workspace for k right-hand
+// sides (both before a graph capture).
+void tc_poly_prepare(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int d, int fmt);
+void tc_poly_reserve(TcState& t, cudaStream_t st, int k);
 // Q = (D o K(Xr, Xc)) V with D_ij = ||x_i - x_j||^2 / sigma^2 (the derivative
 // of K in log sigma) on the rounded points (BF16, split or FP16), any row set.
 void tc_dsigma_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr,

@@ -87,6 +87,7 @@ def run_product(K, h, X, V, sigma, shift, prec, dtype=torch.float32, plan=0):
 @pytest.mark.parametrize("n,k,prec,plan", [
     (65536, 1, "fp16", 0),        # the benched product, headline size
     (65536, 1, "fp16", 2),        # the symmetric plan at the headline size
+    (65536, 1, "fp16", 3),        # the symmetric plan, 8 epilogue warps
     (40000, 10, "fp16", 0),       # multi-RHS, ragged last tile
     (32768, 1, "bf16", 0),
     (33000, 10, "bf16", 0),

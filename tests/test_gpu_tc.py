@@ -294,8 +294,9 @@ def test_mixed_solve_with_autotuning(K, h):
     assert O.true_rel_residual(P.X, P.Y, C.cpu().numpy(), P.sigma, P.lam)[0] <= 1e-6
 
 
+@pytest.mark.parametrize("mode", [2, 3])
 @pytest.mark.parametrize("n,d,prec", [(3000, 64, "fp16"), (1000, 37, "bf16"), (517, 8, "fp16")])
-def test_symmetric_product_matches_rounded_oracle(K, h, n, d, prec):
+def test_symmetric_product_matches_rounded_oracle(K, h, n, d, prec, mode):
     """The symmetric product (tiles I <= J only, each exponential used for K_ij
     and K_ji) is the same kernel of the rounded points as the full product."""
     rng = np.random.default_rng(11 * n + d)
@@ -305,7 +306,7 @@ def test_symmetric_product_matches_rounded_oracle(K, h, n, d, prec):
     Xd, Vd = torch.from_numpy(X).cuda(), torch.from_numpy(V).cuda()
     Qs = torch.empty((n, 1), dtype=torch.float32, device="cuda")
     Qf = torch.empty_like(Qs)
-    h.set_autotune(2)
+    h.set_autotune(mode)
     K.krr_kernel_matvec(h, Xd, Xd, sigma, 0.5, Vd, Qs, prec)
     h.set_autotune(0)
     K.krr_kernel_matvec(h, Xd, Xd, sigma, 0.5, Vd, Qf, prec)
@@ -320,7 +321,7 @@ def test_symmetric_product_matches_rounded_oracle(K, h, n, d, prec):
 
 def test_set_autotune_rejects_bad_mode(K, h):
     with pytest.raises(K.KrrError):
-        h.set_autotune(3)
+        h.set_autotune(4)
 
 
 def test_mixed_solve_keeping_the_search_direction(K, h):
