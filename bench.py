@@ -45,7 +45,7 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one fused FP16 product
 # launch at n = 65536, d = 64, from an ncu capture of `bench.py --profile fp16`; ncu does
 # not run inside the bench, so the figure is carried here and applies to that size only.
-TC_DRAM_BYTES_N65536 = 8679168
+TC_DRAM_BYTES_N65536 = 8679424
 
 
 def parse():
@@ -404,7 +404,13 @@ def run_workload(args):
                     "converged": sum(r["status_code"] == K.KRR_OK for r in reps),
                     "max_iters": max(r["iters"][0] for r in reps),
                     "max_rel_res": max(r["rel_res"][0] for r in reps),
-                    "sum_n2": float(sum(P.n ** 2 for P in probs))})
+                    "sum_n2": float(sum(P.n ** 2 for P in probs)),
+                    "not_converged": [
+                        {"problem": i, "n": P.n, "d": P.d, "lam": P.lam, "s": P.s,
+                         "status": r["status"], "iters": r["iters"][0],
+                         "outer_steps": r["outer_steps"], "rel_res": r["rel_res"][0]}
+                        for i, (P, r) in enumerate(zip(probs, reps))
+                        if r["status_code"] != K.KRR_OK]})
     else:
         P = ks.make_config(args.workload)
         Cc = torch.zeros((P.n, P.k), dtype=torch.float64, device="cuda")

@@ -105,9 +105,19 @@ typedef struct {
                        /* or KRR_HP (FP64 vectors and HP products from the   */
                        /* start: PCG in FP64-grade arithmetic throughout)    */
                        /* (0: the default, KRR_FP16)                         */
+  int batch_product;   /* krr_pcg_solve_batched, KRR_MIXED: 1 (default) runs  */
+                       /* the FP16-point products of all problems (k = 1,    */
+                       /* d <= 128) as one persistent launch per iteration;  */
+                       /* 0: each problem launches its own                   */
   int keep_direction;  /* KRR_MIXED: 1 continues the previous inner solve's  */
                        /* search direction after the residual is replaced   */
                        /* (k <= 5); 0 (default) restarts each at p = z      */
+  int fuse_step;       /* KRR_MIXED, single solves: 1 (default) runs an FP32  */
+                       /* inner PCG iteration as 8 launches, the CG vector   */
+                       /* updates fused into the passes that read the same   */
+                       /* vectors (the product's chunk sums, the apply's two */
+                       /* streamed passes over Z); 0: separate CG kernels    */
+                       /* (13 launches). Same arithmetic either way.         */
 } krr_opts;
 
 typedef struct {
@@ -178,15 +188,15 @@ krr_status krr_rff_features(krr_handle* h, const float* X, int n, int d, int ldx
 
 /*
  * The same features on the tensor cores in the fixed-point form of
- * KRR_Z_FIXED (the mixed solves' preconditioner): Zs (n x s, ldz >= s, BF16
- * bit patterns, device memory) with Z ~= 2^e Zs, Zs = q / 128,
- * q = clamp(rint(z 2^(7-e)), -127, 127), 2^e the smallest power of two >=
- * sqrt(2/s); e is written to *e_out.  X W runs on split BF16 operands
- * (hi.hi + lo.hi + hi.lo), so the cosine's argument carries about 2^-16 of
- * sum_t |x_t||w_t| of error besides FP32 rounding.  X, W, b in device memory.
+ * KRR_Z_FIXED (the mixed solves' preconditioner): Zq (n x s, ldz >= s, int8,
+ * device memory) holds q = clamp(rint(z 2^(7-e)), -127, 127), so
+ * Z ~= 2^(e-7) q, with 2^e the smallest power of two >= sqrt(2/s); e is
+ * written to *e_out.  X W runs on split BF16 operands (hi.hi + lo.hi +
+ * hi.lo), so the cosine's argument carries about 2^-16 of sum_t |x_t||w_t| of
+ * error besides FP32 rounding.  X, W, b in device memory.
  */
 krr_status krr_rff_features_fixed(krr_handle* h, const float* X, int n, int d, int ldx,
-                                  const float* W, const float* b, int s, uint16_t* Zs, int ldz,
+                                  const float* W, const float* b, int s, signed char* Zq, int ldz,
                                   int* e_out);
 
 /*
@@ -213,7 +223,8 @@ krr_status krr_kernel_matvec(krr_handle* h, const float* Xr, int nr, int ldxr,
  *   Cholesky, lower L), then either U = L^-1 Z^T (KRR_APPLY_U, stored FP32
  *   s x n) or L^-1 kept for triangular solves (KRR_APPLY_ZL).
  * Z: n x s (ldz) FP32; the handle keeps its own copy in `z_format`
- * (krr_z_format).  With KRR_Z_BF16 or KRR_Z_FIXED, G is formed from the
+ * (krr_z_format; KRR_Z_FIXED stores the 8-bit q, one byte per feature, which
+ * halves the apply's bytes against BF16).  With KRR_Z_BF16 or KRR_Z_FIXED, G is formed from the
  * stored (rounded) values, so the factors describe exactly the operator
  * applied, (Zt Zt^T + lambda_p I)^-1 with Zt the stored features; with
  * KRR_Z_FIXED that Gram is exact (integer sums on the tensor cores) and the
@@ -334,6 +345,31 @@ krr_status krr_predict(krr_handle* h, const float* Xtr, int n, int ldxtr,
                        const float* Xte, int m, int ldxte, int d, double sigma,
                        const double* C, int k, int ldc, double* F, int ldf,
                        int precision);
+
+/* --------------------------------------------- batched products ------- */
+/* One problem of krr_kernel_matvec_batched. */
+typedef struct {
+  const float* X;      /* n x d training points (ldx), device              */
+  int n, d, ldx;       /* d <= 128                                          */
+  double sigma;        /* Gaussian kernel bandwidth                         */
+  double shift;        /* lambda: Q = K V + shift V                          */
+  const float* V;      /* n x 1 right-hand side, device                     */
+  float* Q;            /* n x 1 product, device                             */
+} krr_matvec_problem;
+
+/*
+ * The kernel products of up to 64 independent problems (the uneven batch of
+ * independent KRR problems) in one persistent tensor-core launch: every
+ * problem's (128-row tile, column chunk) items in one work list, largest
+ * first, dealt to one CTA per SM.  The arithmetic is KRR_FP16's (the
+ * Gaussian kernel of the FP16-rounded, centred, scaled points), one
+ * right-hand side per problem.  Besides the kernel, one launch forms every
+ * problem's weights and one adds the partial sums.  The paper has no
+ * counterpart; krr_pcg_solve_batched uses the same launch for its inner
+ * solves (opts->batch_product).
+ */
+krr_status krr_kernel_matvec_batched(krr_handle* h, const krr_matvec_problem* probs,
+                                     int count);
 
 /* ------------------------------------------- polynomial kernel -------- */
 /*

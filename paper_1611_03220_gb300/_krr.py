@@ -37,7 +37,8 @@ class krr_opts(C.Structure):
                 ("precond", C.c_int), ("precision", C.c_int), ("apply_form", C.c_int),
                 ("use_graph", C.c_int), ("inner_tol", C.c_double), ("max_outer", C.c_int),
                 ("z_format", C.c_int), ("warm_start", C.c_int), ("inner_precision", C.c_int),
-                ("keep_direction", C.c_int)]
+                ("batch_product", C.c_int), ("keep_direction", C.c_int),
+                ("fuse_step", C.c_int)]
 
 
 class krr_report(C.Structure):
@@ -62,6 +63,12 @@ class krr_problem(C.Structure):
                 ("sigma", C.c_double), ("lam", C.c_double), ("W", C.c_void_p),
                 ("b", C.c_void_p), ("s", C.c_int), ("Y", C.c_void_p), ("k", C.c_int),
                 ("ldy", C.c_int), ("C", C.c_void_p), ("ldc", C.c_int)]
+
+
+class krr_matvec_problem(C.Structure):
+    _fields_ = [("X", C.c_void_p), ("n", C.c_int), ("d", C.c_int), ("ldx", C.c_int),
+                ("sigma", C.c_double), ("shift", C.c_double), ("V", C.c_void_p),
+                ("Q", C.c_void_p)]
 
 
 _vp, _i, _d = C.c_void_p, C.c_int, C.c_double
@@ -103,6 +110,7 @@ _SIGS = {
     "krr_precond_setup_adaptive": (_i, [_vp, _vp, _i, _i, _i, _d, _d, _vp, _vp, _i, _i, _vp, _i,
                                         _i, _i, _d, _i, _i, C.POINTER(_i), C.POINTER(_d),
                                         C.POINTER(_i)]),
+    "krr_kernel_matvec_batched": (_i, [_vp, C.POINTER(krr_matvec_problem), _i]),
     "krr_launch_count": (C.c_longlong, []),
     "krr_bench_ex2": (_i, [_vp, _i, C.POINTER(_d), C.POINTER(_d)]),
     "krr_bench_ex2_mix": (_i, [_vp, _i, _i, C.POINTER(_d), C.POINTER(_d)]),
@@ -259,14 +267,14 @@ def krr_precond_setup(h: Handle, Z, lambda_p: float, apply_form="zl", z_format="
     h._check(_lib.krr_precond_setup(h.ptr, _ptr(Z), n, s, _ld(Z), float(lambda_p), form, zf))
 
 
-def krr_rff_features_fixed(h: Handle, X, W, b, Zs) -> int:
-    """Fixed-point random Fourier features on the tensor cores: Zs (n x s torch.bfloat16)
-    with Z ~= 2^e Zs; returns e."""
+def krr_rff_features_fixed(h: Handle, X, W, b, Zq) -> int:
+    """Fixed-point random Fourier features on the tensor cores: Zq (n x s torch.int8)
+    holds q with Z ~= 2^(e-7) q; returns e."""
     n, d = X.shape
     s = W.shape[1]
     e = C.c_int()
     h._check(_lib.krr_rff_features_fixed(h.ptr, _ptr(X), n, d, _ld(X), _ptr(W), _ptr(b), s,
-                                         _ptr(Zs), _ld(Zs), C.byref(e)))
+                                         _ptr(Zq), _ld(Zq), C.byref(e)))
     return e.value
 
 
@@ -374,6 +382,19 @@ def krr_precond_setup_adaptive(h: Handle, X, sigma: float, lam: float, W, b, s0:
                                              C.byref(tests)))
     return {"s": s_out.value, "estimates": [est[i] for i in range(tests.value)],
             "tests": tests.value}
+
+
+def krr_kernel_matvec_batched(h: Handle, problems):
+    """Kernel products of independent problems in one persistent launch:
+    ``problems`` is a sequence of ``(X, sigma, shift, V, Q)`` with device tensors
+    (X n x d float32, V and Q n x 1 float32); Q_p = K_p V_p + shift_p V_p on
+    FP16 points."""
+    arr = (krr_matvec_problem * len(problems))()
+    for i, (X, sigma, shift, V, Q) in enumerate(problems):
+        n, d = X.shape
+        arr[i] = krr_matvec_problem(_ptr(X), n, d, _ld(X), float(sigma), float(shift), _ptr(V),
+                                    _ptr(Q))
+    h._check(_lib.krr_kernel_matvec_batched(h.ptr, arr, len(problems)))
 
 
 def krr_pcg_solve_batched(h: Handle, problems, opts: krr_opts | None = None,

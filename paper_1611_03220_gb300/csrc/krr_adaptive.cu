@@ -25,49 +25,6 @@
 namespace krr {
 namespace {
 
-constexpr int GB = 64;   // output tile of the s x s products
-constexpr int GK = 16;
-
-// C = alpha op(A) op(B) + beta C for s x s row-major FP64 matrices (ld s);
-// op(A) = A^T when ta.  C must not alias A or B.
-__global__ void __launch_bounds__(256)
-gemm_d_kernel(const double* __restrict__ A, const double* __restrict__ B, double* __restrict__ C,
-              int s, int ta, int tb, double alpha, double beta) {
-  __shared__ double As[GK][GB + 1];
-  __shared__ double Bs[GK][GB + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int i0 = blockIdx.y * GB, j0 = blockIdx.x * GB;
-  double acc[4][4] = {};
-  for (int k0 = 0; k0 < s; k0 += GK) {
-    for (int e = threadIdx.x; e < GK * GB; e += 256) {
-      const int t = e / GB, r = e % GB;
-      const int i = i0 + r, k = k0 + t, j = j0 + r;
-      As[t][r] = (i < s && k < s) ? (ta ? A[(size_t)k * s + i] : A[(size_t)i * s + k]) : 0.0;
-      Bs[t][r] = (j < s && k < s) ? (tb ? B[(size_t)j * s + k] : B[(size_t)k * s + j]) : 0.0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < GK; ++t)
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = fma(As[t][ty + 16 * r], Bs[t][tx + 16 * c], acc[r][c]);
-    __syncthreads();
-  }
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int i = i0 + ty + 16 * r;
-    if (i >= s) continue;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int j = j0 + tx + 16 * c;
-      if (j >= s) continue;
-      const size_t e = (size_t)i * s + j;
-      C[e] = alpha * acc[r][c] + (beta != 0.0 ? beta * C[e] : 0.0);
-    }
-  }
-}
-
 // out = a A + b I (s x s); A may alias out.
 __global__ void axpi_kernel(const double* A, int s, double a, double b, double* out) {
   const size_t total = (size_t)s * s;
@@ -125,9 +82,7 @@ __global__ void scale_kernel(double* x, int n, double a) {
 
 void gemm_d(cudaStream_t st, const double* A, const double* B, double* C, int s, int ta, int tb,
             double alpha, double beta) {
-  dim3 grid((s + GB - 1) / GB, (s + GB - 1) / GB);
-  gemm_d_kernel<<<grid, 256, 0, st>>>(A, B, C, s, ta, tb, alpha, beta);
-  KRR_CHECK_LAUNCH();
+  launch_gemm_d(st, s, s, s, alpha, A, s, ta, B, s, tb, beta, C, s);
 }
 
 void axpi(cudaStream_t st, const double* A, int s, double a, double b, double* out) {
@@ -140,7 +95,7 @@ void axpi(cudaStream_t st, const double* A, int s, double a, double b, double* o
 
 size_t adaptive_work_elems(int n, int s) {
   const int nb = std::max(1, std::min(8 * sm_count(), (n + 63) / 64));
-  return (size_t)5 * s * s + (size_t)nb * s + 2 * (size_t)s;
+  return (size_t)5 * s * s + (size_t)nb * s + 2 * (size_t)s + tri_inverse_scratch_elems(s);
 }
 
 void adaptive_projector(cudaStream_t st, const double* G, int s, double tau, int ns_iters,
@@ -151,6 +106,7 @@ void adaptive_projector(cudaStream_t st, const double* G, int s, double tau, int
   double* C = B + ss;
   double* D = C + ss;
   double* Q = D + ss;
+  double* tri = work + 5 * ss;   // scratch of the triangular inverse
   auto chol_inv = [&](double shift) {
     // C = (G + shift I)^-1 = L^-T L^-1
     axpi(st, G, s, 1.0, shift, A);
@@ -160,7 +116,7 @@ void adaptive_projector(cudaStream_t st, const double* G, int s, double tau, int
     if (*info_host != 0)
       throw Error{KRR_ECHOL, "adaptive sketch: G + shift I is not positive definite"};
     KRR_CUDA(cudaMemsetAsync(B, 0, ss * sizeof(double), st));
-    launch_tri_inverse(st, A, s, B);
+    launch_tri_inverse(st, A, s, B, tri);
     gemm_d(st, B, B, C, s, 1, 0, 1.0, 0.0);
   };
   // B0 = I - 2 tau (G + tau I)^-1, then its sign by Newton-Schulz
@@ -188,7 +144,7 @@ void apply_i_minus_p(cudaStream_t st, const float* Z, int n, int s, const double
                      const double* x, double* out) {
   const size_t ss = (size_t)s * s;
   const double* Q = work + 4 * ss;
-  double* part = const_cast<double*>(work) + 5 * ss;
+  double* part = const_cast<double*>(work) + 5 * ss + tri_inverse_scratch_elems(s);
   const int nb = std::max(1, std::min(8 * sm_count(), (n + 63) / 64));
   double* u = part + (size_t)nb * s;
   double* v = u + s;

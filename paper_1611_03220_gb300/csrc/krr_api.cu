@@ -16,6 +16,7 @@
 #include <functional>
 #include <map>
 #include <mutex>
+#include <type_traits>
 
 #include "krr_internal.cuh"
 #include "krr_tc.cuh"
@@ -36,6 +37,9 @@ struct krr_handle {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   TcState tc;
   HpState hp;
+  BatchState batch;               // the batched product of krr_pcg_solve_batched
+  std::vector<TcState> batch_tc;  // operands of krr_kernel_matvec_batched
+  DevBuf batch_ones;              // run flags (all 1) of krr_kernel_matvec_batched
   std::vector<krr_handle*> subs;  // per-problem handles of krr_pcg_solve_batched
   // The kernel of the solve in progress: the Gaussian kernel unless a
   // polynomial-kernel solve has set `poly` (products then ignore sigma).
@@ -374,6 +378,16 @@ struct PcgSpec {
   // smaller than these) instead of starting from p = z
   bool restart = false;
   ColScale rscale{};
+  // the product q = A p is enqueued elsewhere (a batched product shared by
+  // several solves) before this loop body runs
+  bool skip_matvec = false;
+  // fused body (FP32 vectors, the tensor-core product of the training points,
+  // the streamed ZL apply): 8 launches an iteration instead of 13
+  bool fused = false;
+  TcLoop tl{};
+  int tc_split = 0, tc_f16 = 0;
+  double shift = 0.0;
+  T* rn = nullptr;   // the updated residual between the apply's two passes
 };
 
 // Everything before the first iteration: ||y||, z0 = M^-1 r0, p0 = z0.
@@ -393,6 +407,44 @@ void pcg_begin(krr_handle* h, const PcgSpec<T>& S) {
     launch_cg_restart<T>(st, h->sc, S.r, S.z, S.p, S.n, S.k, S.rscale, part);
   else
     launch_cg_rz_first<T>(st, h->sc, S.r, S.z, S.p, S.n, S.k, part);
+  if constexpr (std::is_same<T, float>::value) {
+    // the fused body starts with the product: its weights from p0
+    if (S.fused)
+      launch_cg_update_pw<T>(st, h->sc, S.p, S.z, S.n, S.k, 0, S.tl.ra, S.tl.n_pad, S.tl.kv,
+                             S.tl.w);
+  }
+}
+
+// The fused iteration (same arithmetic as pcg_body, in 8 launches):
+//   product kernel (weights from the previous iteration) -> chunk sums with
+//   p.q and alpha -> Z^T pass with the x, r update and ||r||^2 -> slab sums
+//   -> L^-1 -> L^-T -> Z w pass with r.z, beta and the loop test -> p and
+//   the next weights.
+template <typename T>
+void pcg_body_fused(krr_handle* h, const PcgSpec<T>& S, cudaStream_t s2, unsigned long long cond) {
+  if constexpr (std::is_same<T, float>::value) {
+    double* part = wsT<double>(h, "cg_part", cg_part_elems(S.n, S.k));
+    const Precond& pc = h->pc;
+    tc_loop_product(h->tc, s2, S.k, S.tc_split, S.tc_f16);
+    launch_cg_reduce_alpha<T>(s2, h->sc, S.tl.part, S.tl.nchunk, S.tl.n_pad, S.tl.kv, S.tl.ra,
+                              S.shift, S.p, S.q, S.n, S.k, part);
+    CgStepArgs<T> f;
+    f.sc = h->sc;
+    f.X = S.x;
+    f.P = S.p;
+    f.Q = S.q;
+    f.Rn = S.rn;
+    f.cpart = part;
+    f.cond = cond;
+    double* t1 = wsT<double>(h, "ap_t1", (size_t)pc.s * S.k);
+    double* t2 = wsT<double>(h, "ap_t2", (size_t)pc.s * S.k);
+    double* apart = wsT<double>(h, "ap_part", apply_part_elems(pc.n, pc.s, S.k));
+    launch_apply_cg<T>(s2, pc, S.r, S.k, S.z, t1, t2, apart, f);
+    launch_cg_update_pw<T>(s2, h->sc, S.p, S.z, S.n, S.k, 1, S.tl.ra, S.tl.n_pad, S.tl.kv,
+                           S.tl.w);
+  } else {
+    throw Error{KRR_EINVAL, "fused PCG body: FP32 vectors only"};
+  }
 }
 
 // One PCG iteration of Algorithm 1: q = A p, alpha, x and r updates,
@@ -400,8 +452,12 @@ void pcg_begin(krr_handle* h, const PcgSpec<T>& S) {
 // Enqueues only (no allocation), so it can be captured into a graph.
 template <typename T>
 void pcg_body(krr_handle* h, const PcgSpec<T>& S, cudaStream_t s2, unsigned long long cond) {
+  if (S.fused && !S.skip_matvec) {
+    pcg_body_fused<T>(h, S, s2, cond);
+    return;
+  }
   double* part = wsT<double>(h, "cg_part", cg_part_elems(S.n, S.k));
-  S.matvec(s2, S.p, S.q);
+  if (!S.skip_matvec) S.matvec(s2, S.p, S.q);
   launch_cg_alpha<T>(s2, h->sc, S.p, S.q, S.n, S.k, part);
   launch_cg_update_xr<T>(s2, h->sc, S.x, S.r, S.p, S.q, S.n, S.k, part);
   if (S.apply)
@@ -541,7 +597,8 @@ void precond_factor(krr_handle* h, int n, int s, double lambda_p, int form, int 
     throw Error{KRR_ECHOL, "Z^T Z + lambda_p I is not positive definite (pivot " +
                                std::to_string(info - 1) + ")"};
   ensure_buf(pc.Linv, (size_t)s * s * sizeof(double));
-  launch_tri_inverse(st, (const double*)pc.L.p, s, (double*)pc.Linv.p);
+  launch_tri_inverse(st, (const double*)pc.L.p, s, (double*)pc.Linv.p,
+                     wsT<double>(h, "tri_scratch", tri_inverse_scratch_elems(s)));
   if (form == KRR_APPLY_ZL) {
     ensure_buf(pc.LinvT, (size_t)s * s * sizeof(double));
     launch_transpose_d(st, (const double*)pc.Linv.p, s, (double*)pc.LinvT.p);
@@ -569,7 +626,7 @@ void precond_fixed_gram_factor(krr_handle* h, const __nv_bfloat16* ZT, int e, in
   ensure_buf(pc.L, (size_t)s * s * sizeof(double));
   int* part = wsT<int>(h, "tcs_part", gram_tc_part_elems(n, s));
   launch_gram_tc(st, ZT, n, s, lambda_p * std::ldexp(1.0, -2 * e), part, (double*)pc.L.p, err);
-  precond_factor(h, n, s, lambda_p, form, 1);
+  precond_factor(h, n, s, lambda_p, form, 2);
   int e_flag = 0;
   KRR_CUDA(cudaMemcpyAsync(&e_flag, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   KRR_CUDA(cudaStreamSynchronize(st));
@@ -592,12 +649,12 @@ void precond_setup_impl(krr_handle* h, const float* Z, int n, int s, int ldz, do
   pc.ready = false;
   pc.z_fixed_e = 0;
   if (z_format == KRR_Z_FIXED) {
-    ensure_buf(pc.Z, (size_t)n * s * 2);
+    ensure_buf(pc.Z, (size_t)n * s);
     __nv_bfloat16* ZT = wsT<__nv_bfloat16>(
         h, "tcs_zt", (size_t)setup_tc_s_pad(s) * setup_tc_n_pad(n));
     int* scr = wsT<int>(h, "tcs_scr", 4);
     KRR_CUDA(cudaMemsetAsync(scr, 0, 4 * sizeof(int), st));
-    const int e = launch_quantize_z(st, Z, n, s, ldz, (__nv_bfloat16*)pc.Z.p, ZT, scr);
+    const int e = launch_quantize_z(st, Z, n, s, ldz, (signed char*)pc.Z.p, ZT, scr);
     precond_fixed_gram_factor(h, ZT, e, n, s, lambda_p, form, scr + 1);
     return;
   }
@@ -623,7 +680,7 @@ void precond_setup_rff_tc(krr_handle* h, const float* Xd, int n, int d, int ldx,
   Precond& pc = h->pc;
   pc.ready = false;
   pc.z_fixed_e = 0;
-  ensure_buf(pc.Z, (size_t)n * s * 2);
+  ensure_buf(pc.Z, (size_t)n * s);
   const int n_pad = setup_tc_n_pad(n), s_pad = setup_tc_s_pad(s), kp = setup_tc_kp(d);
   __nv_bfloat16* ZT = wsT<__nv_bfloat16>(h, "tcs_zt", (size_t)s_pad * n_pad);
   __nv_bfloat16* Xh = wsT<__nv_bfloat16>(h, "tcs_xh", (size_t)n_pad * kp);
@@ -633,7 +690,7 @@ void precond_setup_rff_tc(krr_handle* h, const float* Xd, int n, int d, int ldx,
   int* scr = wsT<int>(h, "tcs_scr", 4);
   KRR_CUDA(cudaMemsetAsync(scr, 0, 4 * sizeof(int), st));
   const int e = launch_rff_tc(st, Xd, n, d, ldx, Wd, bd, s, Xh, Xl, Wh, Wl,
-                              (__nv_bfloat16*)pc.Z.p, ZT, scr + 1);
+                              (signed char*)pc.Z.p, ZT, scr + 1);
   precond_fixed_gram_factor(h, ZT, e, n, s, lambda_p, form, scr + 1);
 }
 
@@ -974,6 +1031,18 @@ krr_status solve_mixed(krr_handle* h, const SolveArgs& a, krr_report* rep, int* 
       for (int c = 0; c < KRR_MAX_RHS; ++c)
         S.rscale.v[c] = (c < k && norm_prev[c] > 0.0 && inv.v[c] > 0.0)
                             ? norm_prev[c] / inv.v[c] : 0.0;
+      // the fused body: the plain tensor-core product of the training points
+      // and the streamed ZL apply
+      if (a.o.fuse_step && a.o.precond && !h->kern.poly && prec != KRR_BF16P &&
+          apply_cg_supported(h->pc, n, k) &&
+          tc_loop_prepare(h->tc, st, a.X, n, a.ldx, a.d, a.sigma, k, prec == KRR_BF16X3 ? 1 : 0,
+                          prec == KRR_FP16 ? 1 : 0, &S.tl)) {
+        S.fused = true;
+        S.tc_split = prec == KRR_BF16X3 ? 1 : 0;
+        S.tc_f16 = prec == KRR_FP16 ? 1 : 0;
+        S.shift = a.lambda;
+        S.rn = wsT<float>(h, "v_rnf", nk);
+      }
       launch_convert<double, float>(st, Rs, n, k, k, S.r, k, one);
       KRR_CUDA(cudaMemsetAsync(S.x, 0, nk * sizeof(float), st));
       pcg_loop<float>(h, S, a.o.use_graph != 0, &lo, matvecs);
@@ -1193,7 +1262,8 @@ struct BatchEntry {
 // graph executor may run the solves' kernels concurrently; the tail keeps
 // the loop going while any solve runs.  pcg_begin must have run for every
 // entry.
-void pcg_loop_batched(krr_handle* h, std::vector<BatchEntry>& E) {
+void pcg_loop_batched(krr_handle* h, std::vector<BatchEntry>& E,
+                      const std::function<void(cudaStream_t)>& pre = nullptr) {
   const int ne = (int)E.size();
   if (ne == 0) return;
   cudaStream_t st = h->stream;
@@ -1225,12 +1295,23 @@ void pcg_loop_batched(krr_handle* h, std::vector<BatchEntry>& E) {
                              st));
     KRR_CUDA(cudaMemcpyAsync(d_cond, conds.data(), ne * sizeof(unsigned long long),
                              cudaMemcpyHostToDevice, st));
-    fixed += capture_into(h, body, nullptr, 0,
-                          [&](cudaStream_t cs) { launch_batch_gate(cs, d_scs, d_cond, ne); });
-    size_t nn = 1;
-    cudaGraphNode_t gate = nullptr;
-    KRR_CUDA(cudaGraphGetNodes(body, &gate, &nn));
-    KRR_REQUIRE(nn == 1 && gate, "batched loop: unexpected gate graph");
+    // the gate, then the products shared by several solves (one launch
+    // sequence over all their problems), before any solve's own body
+    fixed += capture_into(h, body, nullptr, 0, [&](cudaStream_t cs) {
+      launch_batch_gate(cs, d_scs, d_cond, ne);
+      if (pre) pre(cs);
+    });
+    size_t nn = 0;
+    KRR_CUDA(cudaGraphGetNodes(body, nullptr, &nn));
+    std::vector<cudaGraphNode_t> heads(nn);
+    KRR_CUDA(cudaGraphGetNodes(body, heads.data(), &nn));
+    cudaGraphNode_t gate = nullptr;   // the chain's last node
+    for (cudaGraphNode_t nd : heads) {
+      size_t nd_out = 0;
+      KRR_CUDA(cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &nd_out));
+      if (nd_out == 0) gate = nd;
+    }
+    KRR_REQUIRE(nn >= 1 && gate, "batched loop: unexpected gate graph");
     std::vector<cudaGraphNode_t> ifn(ne);
     for (int i = 0; i < ne; ++i) {
       cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
@@ -1464,6 +1545,10 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
   for (;;) {
     std::vector<BatchEntry> E;
     std::vector<int> act;
+    // the FP16-point products of the low-level solves (one right-hand side,
+    // d <= 128) run as one persistent launch over all their problems
+    std::vector<BatchProb> bp;
+    const bool can_batch = o.batch_product != 0 && low_precision(o) == KRR_FP16;
     for (size_t i = 0; i < B.size(); ++i) {
       BItem& it = B[i];
       if (it.done) continue;
@@ -1532,6 +1617,11 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
         launch_convert<double, float>(g->stream, Rs, it.n, it.k, it.k, S.r, it.k, one);
         KRR_CUDA(cudaMemsetAsync(S.x, 0, nk * sizeof(float), g->stream));
         pcg_begin<float>(g, S);
+        if (can_batch && it.k == 1 && it.d <= 128 && (int)bp.size() < BATCH_MAX &&
+            g->tc.half_ready) {
+          S.skip_matvec = true;
+          bp.push_back(BatchProb{&g->tc.half, S.p, S.q, it.lambda, &g->sc->run});
+        }
         E.push_back(BatchEntry{g, [g, S](cudaStream_t cs) { pcg_body<float>(g, S, cs, 0ull); }, 0});
       } else {
         // FP64 vectors; the split or HP product
@@ -1551,7 +1641,14 @@ void batched_mixed(krr_handle* h, std::vector<BItem>& B, const krr_opts& o) {
       act.push_back((int)i);
     }
     if (E.empty()) break;
-    pcg_loop_batched(h, E);
+    if (!bp.empty()) {
+      tc_batch_reserve(h->batch, h->stream, bp);   // the sub-handles share h's stream
+      pcg_loop_batched(h, E, [&](cudaStream_t cs) { tc_batch_matvec(h->batch, cs, bp); });
+      if (tc_batch_error(h->batch, h->stream))
+        for (int i : act) B[i].status = KRR_ETIMEOUT;
+    } else {
+      pcg_loop_batched(h, E);
+    }
     for (int i : act) {
       BItem& it = B[i];
       krr_handle* g = it.sub;
@@ -1622,9 +1719,11 @@ void krr_default_opts(krr_opts* o) {
   o->inner_tol = 3e-2;
   o->max_outer = 30;
   o->z_format = -1;
+  o->batch_product = 1;
   o->warm_start = 0;
   o->inner_precision = KRR_FP16;
   o->keep_direction = 0;
+  o->fuse_step = 1;
 }
 
 const char* krr_status_string(krr_status s) {
@@ -1683,6 +1782,9 @@ krr_status krr_destroy(krr_handle* h) {
   h->subs.clear();
   tc_release(h->tc);
   hp_release(h->hp);
+  tc_batch_release(h->batch);
+  for (TcState& t : h->batch_tc) tc_release(t);
+  if (h->batch_ones.p) cudaFree(h->batch_ones.p);
   if (h->sc) cudaFree(h->sc);
   if (h->sc_host) cudaFreeHost(h->sc_host);
   if (h->hostd) cudaFreeHost(h->hostd);
@@ -1715,10 +1817,10 @@ krr_status krr_rff_features(krr_handle* h, const float* X, int n, int d, int ldx
 }
 
 krr_status krr_rff_features_fixed(krr_handle* h, const float* X, int n, int d, int ldx,
-                                  const float* W, const float* b, int s, uint16_t* Zs, int ldz,
+                                  const float* W, const float* b, int s, signed char* Zq, int ldz,
                                   int* e_out) {
   return guard(h, [&]() -> krr_status {
-    KRR_REQUIRE(X && W && b && Zs && e_out, "rff_features_fixed: null pointer");
+    KRR_REQUIRE(X && W && b && Zq && e_out, "rff_features_fixed: null pointer");
     KRR_REQUIRE(n > 0 && d > 0 && s > 0, "rff_features_fixed: sizes must be positive");
     KRR_REQUIRE(ldx >= d && ldz >= s, "rff_features_fixed: leading dimension too small");
     cudaStream_t st = h->stream;
@@ -1728,13 +1830,12 @@ krr_status krr_rff_features_fixed(krr_handle* h, const float* X, int n, int d, i
     __nv_bfloat16* Xl = wsT<__nv_bfloat16>(h, "tcs_xl", (size_t)n_pad * kp);
     __nv_bfloat16* Wh = wsT<__nv_bfloat16>(h, "tcs_wh", (size_t)s_pad * kp);
     __nv_bfloat16* Wl = wsT<__nv_bfloat16>(h, "tcs_wl", (size_t)s_pad * kp);
-    __nv_bfloat16* Zo = ldz == s ? reinterpret_cast<__nv_bfloat16*>(Zs)
-                                 : wsT<__nv_bfloat16>(h, "tcs_zout", (size_t)n * s);
+    signed char* Zo = ldz == s ? Zq : wsT<signed char>(h, "tcs_zout", (size_t)n * s);
     int* scr = wsT<int>(h, "tcs_scr", 4);
     KRR_CUDA(cudaMemsetAsync(scr, 0, 4 * sizeof(int), st));
     *e_out = launch_rff_tc(st, X, n, d, ldx, W, b, s, Xh, Xl, Wh, Wl, Zo, ZT, scr + 1);
     if (ldz != s)
-      KRR_CUDA(cudaMemcpy2DAsync(Zs, (size_t)ldz * 2, Zo, (size_t)s * 2, (size_t)s * 2, n,
+      KRR_CUDA(cudaMemcpy2DAsync(Zq, (size_t)ldz, Zo, (size_t)s, (size_t)s, n,
                                  cudaMemcpyDeviceToDevice, st));
     int flag = 0;
     KRR_CUDA(cudaMemcpyAsync(&flag, scr + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -2491,3 +2592,38 @@ extern "C" krr_status krr_precond_setup_adaptive(
     return KRR_OK;
   });
 }
+
+// ------------------------------------------------ batched kernel products ---
+extern "C" krr_status krr_kernel_matvec_batched(krr_handle* h, const krr_matvec_problem* probs,
+                                                int count) {
+  return guard(h, [&]() -> krr_status {
+    KRR_REQUIRE(probs && count >= 1 && count <= BATCH_MAX,
+                "kernel_matvec_batched: 1 <= count <= 64 problems");
+    for (int i = 0; i < count; ++i) {
+      const krr_matvec_problem& q = probs[i];
+      KRR_REQUIRE(q.X && q.V && q.Q, "kernel_matvec_batched: null pointer");
+      KRR_REQUIRE(q.n > 0 && q.d > 0 && q.d <= 128 && q.ldx >= q.d,
+                  "kernel_matvec_batched: need n > 0 and 0 < d <= 128");
+      KRR_REQUIRE(q.sigma > 0.0 && std::isfinite(q.sigma), "kernel_matvec_batched: sigma > 0");
+    }
+    cudaStream_t st = h->stream;
+    if ((int)h->batch_tc.size() < count) h->batch_tc.resize(count);
+    if (!h->batch_ones.p) {
+      ensure_buf(h->batch_ones, sizeof(int));
+      const int one = 1;
+      KRR_CUDA(cudaMemcpy(h->batch_ones.p, &one, sizeof(int), cudaMemcpyHostToDevice));
+    }
+    std::vector<BatchProb> bp(count);
+    for (int i = 0; i < count; ++i) {
+      const krr_matvec_problem& q = probs[i];
+      tc_prepare_f16(h->batch_tc[i], st, q.X, q.n, q.ldx, q.d, q.sigma);
+      bp[i] = BatchProb{&h->batch_tc[i].half, q.V, q.Q, q.shift, (const int*)h->batch_ones.p};
+    }
+    tc_batch_reserve(h->batch, st, bp);
+    tc_batch_matvec(h->batch, st, bp);
+    if (tc_batch_error(h->batch, st))
+      throw Error{KRR_ETIMEOUT, "batched product: a pipeline wait hit its limit"};
+    return KRR_OK;
+  });
+}
+

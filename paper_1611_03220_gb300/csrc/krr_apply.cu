@@ -9,12 +9,15 @@
 //   trmv_kernel  u = L^-1 t, w = L^-T u   (FP64, explicit inverse from set-up)
 //   zw_kernel    z = (r - Z w) / lambda_p GEMV over Z with w staged in
 //                               shared memory
-// Both GEMVs stream Z once with 16-byte loads (8 BF16 or 4 FP32 values), so
-// the apply is bound by HBM: about 2 n s b_Z bytes per application.
+// Both GEMVs stream Z once with 16-byte loads (16 fixed-point bytes, 8 BF16
+// or 4 FP32 values), so the apply is bound by HBM: about 2 n s b_Z bytes per
+// application.  Z is stored as FP32 (ZF = 0), BF16 (ZF = 1) or, for the
+// fixed-point features of the mixed solves, 8-bit integers q with
+// Z = q / 128 (ZF = 2, exact: the features are q / 128 by construction).
 #include <algorithm>
 #include <type_traits>
 
-#include "krr_internal.cuh"
+#include "krr_cgstep.cuh"
 
 namespace krr {
 namespace {
@@ -31,41 +34,76 @@ int kv_of(int k) {
   return 16;
 }
 
+// Eight Z values from their storage: FP32, BF16 or 8-bit q / 128.
+template <int ZF>
+__device__ __forceinline__ float zval(const void* Zs, size_t off) {
+  if (ZF == 1) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(Zs)[off]);
+  if (ZF == 2) return (float)reinterpret_cast<const signed char*>(Zs)[off] * 0.0078125f;
+  return reinterpret_cast<const float*>(Zs)[off];
+}
+
+// Eight consecutive 8-bit codes (one 8-byte word) as the floats q, without
+// integer conversions: with the sign bit flipped a code is u = q + 128, the
+// byte permute builds the float 2^23 + u, and one subtraction leaves q exactly.
+__device__ __forceinline__ float q8f(uint32_t w, uint32_t i) {
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u + i)) - 8388736.f;
+}
+__device__ __forceinline__ void unpack_q8(uint2 v, float (&z)[8]) {
+  const uint32_t a = v.x ^ 0x80808080u, b = v.y ^ 0x80808080u;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    z[q] = q8f(a, q);
+    z[4 + q] = q8f(b, q);
+  }
+}
+
+// The scale between stage8's values and Z: 1/128 for the 8-bit codes (the
+// streamed kernels apply it once to their sums), 1 otherwise.
+template <int ZF>
+__device__ __forceinline__ constexpr float zscale() { return ZF == 2 ? 0.0078125f : 1.f; }
+
+// Eight consecutive Z values at byte address p of a stage (ZF storage); the
+// 8-bit codes come back as q (multiply by zscale<ZF>() for Z).
+template <int ZF>
+__device__ __forceinline__ void stage8(const uint8_t* p, float (&z)[8]) {
+  if (ZF == 1) {
+    const uint4 v = *reinterpret_cast<const uint4*>(p);
+    const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float2 f = __bfloat1622float2(h2[q]);
+      z[2 * q] = f.x;
+      z[2 * q + 1] = f.y;
+    }
+  } else if (ZF == 2) {
+    unpack_q8(*reinterpret_cast<const uint2*>(p), z);
+  } else {
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+    const float4 a = p4[0], b = p4[1];
+    z[0] = a.x; z[1] = a.y; z[2] = a.z; z[3] = a.w;
+    z[4] = b.x; z[5] = b.y; z[6] = b.z; z[7] = b.w;
+  }
+}
+
 // Eight consecutive Z values starting at element `off` (n_ok of them valid).
-template <int BF16>
+template <int ZF>
 __device__ __forceinline__ void load8(const void* Zs, size_t off, int n_ok, bool vec,
                                       float (&z)[8]) {
   if (vec && n_ok >= 8) {
-    if (BF16) {
-      uint4 v = *reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(Zs) + off);
-      const __nv_bfloat162* p = reinterpret_cast<const __nv_bfloat162*>(&v);
+    constexpr int ES = ZF == 1 ? 2 : (ZF == 2 ? 1 : 4);
+    stage8<ZF>(reinterpret_cast<const uint8_t*>(Zs) + off * ES, z);
+    if (ZF == 2) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float2 f = __bfloat1622float2(p[q]);
-        z[2 * q] = f.x;
-        z[2 * q + 1] = f.y;
-      }
-    } else {
-      const float4* p = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(Zs) + off);
-      float4 a = p[0], b = p[1];
-      z[0] = a.x; z[1] = a.y; z[2] = a.z; z[3] = a.w;
-      z[4] = b.x; z[5] = b.y; z[6] = b.z; z[7] = b.w;
+      for (int q = 0; q < 8; ++q) z[q] *= zscale<ZF>();
     }
     return;
   }
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    if (q < n_ok) {
-      z[q] = BF16 ? __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(Zs)[off + q])
-                  : reinterpret_cast<const float*>(Zs)[off + q];
-    } else {
-      z[q] = 0.f;
-    }
-  }
+  for (int q = 0; q < 8; ++q) z[q] = q < n_ok ? zval<ZF>(Zs, off + q) : 0.f;
 }
 
 // part[chunk, col, c] = sum_{i in chunk} Z[i, col] R[i, c]; 8 columns per thread.
-template <int BF16, typename T, typename ACC, int KV>
+template <int ZF, typename T, typename ACC, int KV>
 __global__ void __launch_bounds__(AT)
 zt_kernel(const void* __restrict__ Zs, int n, int s, const T* __restrict__ R, int ldr, int k,
           ACC* __restrict__ part, int rpc, int vec) {
@@ -90,7 +128,7 @@ zt_kernel(const void* __restrict__ Zs, int n, int s, const T* __restrict__ R, in
 #pragma unroll 4
       for (int rr = 0; rr < nrow; ++rr) {
         float z[8];
-        load8<BF16>(Zs, (size_t)(base + rr) * s + col0, n_ok, vec != 0, z);
+        load8<ZF>(Zs, (size_t)(base + rr) * s + col0, n_ok, vec != 0, z);
 #pragma unroll
         for (int c = 0; c < KV; ++c) {
           const ACC rv = rs[rr][c];
@@ -195,7 +233,7 @@ trmv_kernel(const double* __restrict__ A, int s, const double* __restrict__ x, i
 constexpr int ZW_ROWS_PER_WARP = 4;
 constexpr int ZW_ROWS = ZW_ROWS_PER_WARP * (AT / 32);
 
-template <int BF16, typename T, typename ACC, int KV>
+template <int ZF, typename T, typename ACC, int KV>
 __global__ void __launch_bounds__(AT)
 zw_kernel(const void* __restrict__ Zs, int n, int s, const double* __restrict__ w, int k,
           const T* __restrict__ R, int ldr, double inv_lam, T* __restrict__ Zo, int ldo, int sch,
@@ -224,7 +262,7 @@ zw_kernel(const void* __restrict__ Zs, int n, int s, const double* __restrict__ 
       if (i >= n) break;
       for (int bb = lane * 8; bb < nb; bb += 256) {
         float z[8];
-        load8<BF16>(Zs, (size_t)i * s + b0 + bb, min(8, nb - bb), vec != 0, z);
+        load8<ZF>(Zs, (size_t)i * s + b0 + bb, min(8, nb - bb), vec != 0, z);
 #pragma unroll
         for (int c = 0; c < KV; ++c) {
           const ACC* wc = wsm + c * sch + bb;
@@ -319,13 +357,17 @@ __device__ __forceinline__ void stg_issue(uint8_t* ring, uint64_t* full, int st,
 
 // part[cta, col, c] = sum over the CTA's rows of Z[i, col] R[i, c]; thread t
 // owns columns c0 + 8t .. c0 + 8t + 7 of the column block blockIdx.x.
-template <int BF16, typename T, typename ACC, int KV>
+// FUSE: R is the residual before the iteration's update; the kernel stages
+// r' = r - alpha q instead (alpha from the CG scalars), and the CTAs of
+// column block 0 also write x' = x + alpha p and r' (to f.Rn) and reduce
+// ||r'||^2 (the stopping test), exactly as the separate x, r update kernel.
+template <int ZF, typename T, typename ACC, int KV, int FUSE = 0>
 __global__ void __launch_bounds__(AT, 1)
 zt_stream_kernel(const void* __restrict__ Zs, int n, int s, const T* __restrict__ R, int ldr,
-                 int k, ACC* __restrict__ part, int* err) {
+                 int k, ACC* __restrict__ part, int* err, CgStepArgs<T> f) {
   extern __shared__ __align__(128) uint8_t ring[];
   __shared__ __align__(8) uint64_t full[NSTG];
-  constexpr int ES = BF16 ? 2 : 4;
+  constexpr int ES = ZF == 1 ? 2 : (ZF == 2 ? 1 : 4);
   const int cb = blockIdx.x;
   const int c0 = cb * AT * 8;
   const int seg = min(AT * 8, s - c0);                 // columns in this block (multiple of 8)
@@ -345,11 +387,46 @@ zt_stream_kernel(const void* __restrict__ Zs, int n, int s, const T* __restrict_
   // the CTA's rows of R, staged once (the per-row loads would each expose
   // a memory round trip)
   ACC* rsm = reinterpret_cast<ACC*>(ring + (size_t)NSTG * SBYTES);
+  __shared__ double alpha_s[FUSE ? KRR_MAX_RHS : 1];
+  double vr[KRR_MAX_RHS];
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c) vr[c] = 0.0;
+  if (FUSE) {
+    if (threadIdx.x < KRR_MAX_RHS)
+      alpha_s[threadIdx.x] = (int)threadIdx.x < k ? f.sc->alpha[threadIdx.x] : 0.0;
+    __syncthreads();
+  }
   for (int e = threadIdx.x; e < (r1 - r0) * KV; e += AT) {
     const int rr = e / KV, c = e % KV;
-    rsm[e] = (r0 < r1 && c < k) ? (ACC)R[(size_t)(r0 + rr) * ldr + c] : (ACC)0;
+    ACC val = (ACC)0;
+    if (r0 < r1 && c < k) {
+      const size_t ei = (size_t)(r0 + rr) * ldr + c;
+      if (FUSE) {
+        double r = (double)R[ei];
+        const double a = alpha_s[c];
+        if (a != 0.0) {
+          r = (double)(T)(r - a * (double)f.Q[ei]);
+          if (blockIdx.x == 0) f.X[ei] = (T)((double)f.X[ei] + a * (double)f.P[ei]);
+        }
+        if (blockIdx.x == 0) {
+          f.Rn[ei] = (T)r;
+#pragma unroll
+          for (int cc = 0; cc < KV; ++cc)
+            if (cc == c) vr[cc] = fma(r, r, vr[cc]);
+        }
+        val = (ACC)r;
+      } else {
+        val = (ACC)R[ei];
+      }
+    }
+    rsm[e] = val;
   }
   __syncthreads();
+  if (FUSE && blockIdx.x == 0) {
+    double tot[KRR_MAX_RHS];
+    if (grid_colsum_nt<AT>(vr, k, f.cpart, &f.sc->counter[CGC_XR], blockIdx.y, gridDim.y, tot))
+      cg_xr_finish(f.sc, tot, k);
+  }
   const int col = threadIdx.x * 8;  // within the block
   const bool mine = col < seg;
   ACC acc[8][KV];
@@ -369,21 +446,7 @@ zt_stream_kernel(const void* __restrict__ Zs, int n, int s, const T* __restrict_
     if (mine) {
       for (int rr = 0; rr < nrow; ++rr) {
         float z[8];
-        if (BF16) {
-          const uint4 v = *reinterpret_cast<const uint4*>(base + (size_t)rr * seg_bytes + col * 2);
-          const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&v);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float2 f = __bfloat1622float2(h2[q]);
-            z[2 * q] = f.x;
-            z[2 * q + 1] = f.y;
-          }
-        } else {
-          const float4* p4 = reinterpret_cast<const float4*>(base + (size_t)rr * seg_bytes + col * 4);
-          const float4 a = p4[0], b = p4[1];
-          z[0] = a.x; z[1] = a.y; z[2] = a.z; z[3] = a.w;
-          z[4] = b.x; z[5] = b.y; z[6] = b.z; z[7] = b.w;
-        }
+        stage8<ZF>(base + (size_t)rr * seg_bytes + col * ES, z);
 #pragma unroll
         for (int c = 0; c < KV; ++c) {
           const ACC rv = rsm[(row0 - r0 + rr) * KV + c];
@@ -411,7 +474,8 @@ zt_stream_kernel(const void* __restrict__ Zs, int n, int s, const T* __restrict_
 #pragma unroll
   for (int q = 0; q < 8; ++q)
 #pragma unroll
-    for (int c = 0; c < KV; ++c) out[(size_t)(c0 + col + q) * KV + c] = acc[q][c];
+    for (int c = 0; c < KV; ++c)
+      out[(size_t)(c0 + col + q) * KV + c] = acc[q][c] * (ACC)zscale<ZF>();
 }
 
 // Zo[i, c] = (R[i, c] - sum_b Z[i, b] w[b, c]) / lambda_p with whole rows of Z
@@ -420,14 +484,17 @@ zt_stream_kernel(const void* __restrict__ Zs, int n, int s, const T* __restrict_
 // shared-memory latency of each row's dot product set the pace.
 constexpr int ZAT = 512;
 
-template <int BF16, typename T, typename ACC, int KV>
+// FUSE: R is the updated residual r' (f.Rn); the kernel also copies it to
+// Rout, reduces r'.z and, in the last CTA, forms beta and the loop's continue
+// decision, exactly as the separate r.z and tail kernels.
+template <int ZF, typename T, typename ACC, int KV, int FUSE = 0>
 __global__ void __launch_bounds__(ZAT, 1)
 zw_stream_kernel(const void* __restrict__ Zs, int n, int s, const double* __restrict__ w, int k,
                  const T* __restrict__ R, int ldr, double inv_lam, T* __restrict__ Zo, int ldo,
-                 int* err) {
+                 int* err, T* __restrict__ Rout, CgStepArgs<T> f) {
   extern __shared__ __align__(128) uint8_t ring[];
   __shared__ __align__(8) uint64_t full[NSTG];
-  constexpr int ES = BF16 ? 2 : 4;
+  constexpr int ES = ZF == 1 ? 2 : (ZF == 2 ? 1 : 4);
   ACC* wsm = reinterpret_cast<ACC*>(ring + (size_t)NSTG * SBYTES);  // [c][b]
   const uint32_t row_bytes = (uint32_t)s * ES;
   const int rps = SBYTES / (int)row_bytes;
@@ -453,8 +520,18 @@ zw_stream_kernel(const void* __restrict__ Zs, int n, int s, const double* __rest
   double* rsm = reinterpret_cast<double*>(wsm + (size_t)s * KV);
   for (int e = threadIdx.x; e < (r1 - r0) * KV; e += ZAT) {
     const int rr = e / KV, c = e % KV;
-    rsm[e] = (r0 < r1 && c < k) ? (double)R[(size_t)(r0 + rr) * ldr + c] : 0.0;
+    double r = 0.0;
+    if (r0 < r1 && c < k) {
+      const size_t ei = (size_t)(r0 + rr) * ldr + c;
+      const T rv = R[ei];
+      if (FUSE) Rout[ei] = rv;
+      r = (double)rv;
+    }
+    rsm[e] = r;
   }
+  double vz[KRR_MAX_RHS];
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c) vz[c] = 0.0;
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // One right-hand side in FP32 with s <= 2048: each lane keeps its 8 x 8
@@ -487,32 +564,20 @@ zw_stream_kernel(const void* __restrict__ Zs, int n, int s, const double* __rest
         for (int it = 0; it < 8; ++it) {
           if (it < nit) {
             float z[8];
-            if (BF16) {
-              const uint4 v = *reinterpret_cast<const uint4*>(base + (size_t)rr * row_bytes +
-                                                             (lane * 8 + 256 * it) * 2);
-              const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&v);
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const float2 f = __bfloat1622float2(h2[q]);
-                z[2 * q] = f.x;
-                z[2 * q + 1] = f.y;
-              }
-            } else {
-              const float4* p4 = reinterpret_cast<const float4*>(
-                  base + (size_t)rr * row_bytes + (lane * 8 + 256 * it) * 4);
-              const float4 a4 = p4[0], b4 = p4[1];
-              z[0] = a4.x; z[1] = a4.y; z[2] = a4.z; z[3] = a4.w;
-              z[4] = b4.x; z[5] = b4.y; z[6] = b4.z; z[7] = b4.w;
-            }
+            stage8<ZF>(base + (size_t)rr * row_bytes + (lane * 8 + 256 * it) * ES, z);
 #pragma unroll
             for (int q = 0; q < 8; ++q) a[q & 3] = fmaf(z[q], wr[it][q], a[q & 3]);
           }
         }
         float v = (a[0] + a[1]) + (a[2] + a[3]);
         for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        v *= zscale<ZF>();
         const int i = row0 + rr;
-        if (lane == 0 && k > 0)
-          Zo[(size_t)i * ldo] = (T)((rsm[i - r0] - (double)v) * inv_lam);
+        if (lane == 0 && k > 0) {
+          const T zo = (T)((rsm[i - r0] - (double)v) * inv_lam);
+          Zo[(size_t)i * ldo] = zo;
+          if (FUSE) vz[0] = fma(rsm[i - r0], (double)zo, vz[0]);
+        }
       }
     } else
     // one row per warp and pass (RW = 1): sixteen rows of a BF16 stage in one pass
@@ -531,23 +596,7 @@ zw_stream_kernel(const void* __restrict__ Zs, int n, int s, const double* __rest
 #pragma unroll
         for (int h = 0; h < RW; ++h) {
           const int row = h ? (two ? rb : rr) : rr;
-          if (BF16) {
-            const uint4 v =
-                *reinterpret_cast<const uint4*>(base + (size_t)row * row_bytes + b0 * 2);
-            const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&v);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const float2 f = __bfloat1622float2(h2[q]);
-              z[h][2 * q] = f.x;
-              z[h][2 * q + 1] = f.y;
-            }
-          } else {
-            const float4* p4 =
-                reinterpret_cast<const float4*>(base + (size_t)row * row_bytes + b0 * 4);
-            const float4 a4 = p4[0], b4 = p4[1];
-            z[h][0] = a4.x; z[h][1] = a4.y; z[h][2] = a4.z; z[h][3] = a4.w;
-            z[h][4] = b4.x; z[h][5] = b4.y; z[h][6] = b4.z; z[h][7] = b4.w;
-          }
+          stage8<ZF>(base + (size_t)row * row_bytes + b0 * ES, z[h]);
         }
 #pragma unroll
         for (int c = 0; c < KV; ++c) {
@@ -584,8 +633,13 @@ zw_stream_kernel(const void* __restrict__ Zs, int n, int s, const double* __rest
           // reduce in the accumulator type (FP64 adds are slow on this GPU)
           ACC v = acc[h][c];
           for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-          if (lane == 0)
-            Zo[(size_t)i * ldo + c] = (T)((rsm[(i - r0) * KV + c] - (double)v) * inv_lam);
+          v *= (ACC)zscale<ZF>();
+          if (lane == 0) {
+            const double r = rsm[(i - r0) * KV + c];
+            const T zo = (T)((r - (double)v) * inv_lam);
+            Zo[(size_t)i * ldo + c] = zo;
+            if (FUSE) vz[c] = fma(r, (double)zo, vz[c]);
+          }
         }
       }
     }
@@ -600,6 +654,16 @@ zw_stream_kernel(const void* __restrict__ Zs, int n, int s, const double* __rest
     atomicOr(err, 1);
     for (int gg = g; gg < nstage && gg < g + NSTG; ++gg)
       stg_wait(sh_u32(&full[gg % NSTG]), (uint32_t)((gg / NSTG) & 1));
+  }
+  if (FUSE) {
+    double tot[KRR_MAX_RHS];
+    if (grid_colsum_nt<ZAT>(vz, k, f.cpart, &f.sc->counter[CGC_RZ], blockIdx.x, gridDim.x,
+                            tot)) {
+      cg_rz_finish(f.sc, tot, k);
+      // a streamed pass that gave up on a copy left z incomplete: stop the loop
+      if (*reinterpret_cast<volatile int*>(err)) f.sc->flags |= FLAG_NAN;
+      cg_tail_finish(f.sc, (cudaGraphConditionalHandle)f.cond);
+    }
   }
 }
 
@@ -675,32 +739,56 @@ ApplyPlan plan(int n, int s, int k) {
   return p;
 }
 
-template <int BF16, typename T, typename ACC, int KV>
-void apply_zl(cudaStream_t st, const Precond& pc, const ApplyPlan& pl, const T* R, int k, int ldr,
-              T* Zo, int ldo, double* t1, double* t2, void* part, bool ginv_only = false) {
+// Launch shapes of the streamed GEMVs of one apply and whether they apply.
+struct StreamPlan {
+  bool zt, zw;            // the streamed Z^T r / Z w kernels serve this apply
+  int nchunk;             // row chunks of the streamed Z^T r
+  size_t zt_bytes, zw_bytes;
+};
+
+template <int ZF, typename ACC, int KV>
+StreamPlan stream_plan(const Precond& pc, const ApplyPlan& pl) {
   const int n = pc.n, s = pc.s;
-  const int vec = (s % 8 == 0) ? 1 : 0;
-  int* err = reinterpret_cast<int*>(pc.err.p);
+  // whole 16-byte groups per row: 8 BF16 / FP32 values, 16 fixed-point bytes
+  const bool vec = s % (ZF == 2 ? 16 : 8) == 0;
+  const bool err = pc.err.p != nullptr;
   // streamed GEMVs: rows 16-byte aligned; zw also needs w beside the ring
   const size_t w_bytes = (size_t)s * KV * sizeof(ACC);
   const size_t ring_bytes = (size_t)NSTG * SBYTES;
-  const int nchunk_s = std::min(pl.nchunk, std::max(1, sm_count() / pl.colblocks));
-  const size_t zt_bytes = ring_bytes + (size_t)((n + nchunk_s - 1) / nchunk_s) * KV * sizeof(ACC);
-  const size_t zw_bytes = ring_bytes + w_bytes +
-                          (size_t)((n + sm_count() - 1) / sm_count()) * KV * sizeof(double);
-  const bool stream = vec && err != nullptr && zt_bytes <= (size_t)220 * 1024;
-  const bool stream_zw = vec && err != nullptr && (size_t)s * (BF16 ? 2 : 4) <= (size_t)SBYTES &&
-                         zw_bytes <= (size_t)220 * 1024;
+  StreamPlan sp;
+  sp.nchunk = std::min(pl.nchunk, std::max(1, sm_count() / pl.colblocks));
+  sp.zt_bytes = ring_bytes + (size_t)((n + sp.nchunk - 1) / sp.nchunk) * KV * sizeof(ACC);
+  sp.zw_bytes = ring_bytes + w_bytes +
+                (size_t)((n + sm_count() - 1) / sm_count()) * KV * sizeof(double);
+  constexpr int ES = ZF == 1 ? 2 : (ZF == 2 ? 1 : 4);
+  sp.zt = vec && err && sp.zt_bytes <= (size_t)220 * 1024;
+  sp.zw = vec && err && (size_t)s * ES <= (size_t)SBYTES && sp.zw_bytes <= (size_t)220 * 1024;
+  return sp;
+}
+
+// fuse: run the PCG iteration's vector work in the two streamed passes (both
+// must be streamed; R is then the residual before the update, and ldr == ldo == k).
+template <int ZF, typename T, typename ACC, int KV>
+void apply_zl(cudaStream_t st, const Precond& pc, const ApplyPlan& pl, const T* R, int k, int ldr,
+              T* Zo, int ldo, double* t1, double* t2, void* part, bool ginv_only = false,
+              const CgStepArgs<T>* fuse = nullptr) {
+  const int n = pc.n, s = pc.s;
+  const int vec = (s % (ZF == 2 ? 16 : 8) == 0) ? 1 : 0;
+  int* err = reinterpret_cast<int*>(pc.err.p);
+  const StreamPlan sp = stream_plan<ZF, ACC, KV>(pc, pl);
+  if (fuse && !(sp.zt && sp.zw && !ginv_only))
+    throw Error{KRR_EINVAL, "fused apply: the streamed kernels do not serve this shape"};
+  const CgStepArgs<T> nof{};
   int nchunk = pl.nchunk;
-  if (stream) {
-    nchunk = nchunk_s;
-    auto kz = zt_stream_kernel<BF16, T, ACC, KV>;
+  if (sp.zt) {
+    nchunk = sp.nchunk;
+    auto kz = fuse ? zt_stream_kernel<ZF, T, ACC, KV, 1> : zt_stream_kernel<ZF, T, ACC, KV, 0>;
     KRR_CUDA(cudaFuncSetAttribute(kz, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)zt_bytes));
-    kz<<<dim3(pl.colblocks, nchunk), AT, zt_bytes, st>>>(pc.Z.p, n, s, R, ldr, k,
-                                                         reinterpret_cast<ACC*>(part), err);
+                                  (int)sp.zt_bytes));
+    kz<<<dim3(pl.colblocks, nchunk), AT, sp.zt_bytes, st>>>(
+        pc.Z.p, n, s, R, ldr, k, reinterpret_cast<ACC*>(part), err, fuse ? *fuse : nof);
   } else {
-    zt_kernel<BF16, T, ACC, KV><<<dim3(pl.colblocks, pl.nchunk), AT, 0, st>>>(
+    zt_kernel<ZF, T, ACC, KV><<<dim3(pl.colblocks, pl.nchunk), AT, 0, st>>>(
         pc.Z.p, n, s, R, ldr, k, reinterpret_cast<ACC*>(part), pl.rpc, vec);
   }
   KRR_CHECK_LAUNCH();
@@ -713,16 +801,19 @@ void apply_zl(cudaStream_t st, const Precond& pc, const ApplyPlan& pl, const T* 
   trmv_kernel<1, KV><<<tb, AT, 0, st>>>(reinterpret_cast<const double*>(pc.LinvT.p), s, t2, k, t1);
   KRR_CHECK_LAUNCH();
   if (ginv_only) return;  // t1 = G^-1 Z^T R (the random-features solution)
-  if (stream_zw) {
-    auto kw = zw_stream_kernel<BF16, T, ACC, KV>;
+  if (sp.zw) {
+    auto kw = fuse ? zw_stream_kernel<ZF, T, ACC, KV, 1> : zw_stream_kernel<ZF, T, ACC, KV, 0>;
     KRR_CUDA(cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)zw_bytes));
-    kw<<<sm_count(), ZAT, zw_bytes, st>>>(pc.Z.p, n, s, t1, k, R, ldr, 1.0 / pc.lam_p, Zo, ldo,
-                                          err);
+                                  (int)sp.zw_bytes));
+    // fused: z from the updated residual, which is copied back to R
+    const T* Rin = fuse ? fuse->Rn : R;
+    T* Rout = fuse ? const_cast<T*>(R) : nullptr;
+    kw<<<sm_count(), ZAT, sp.zw_bytes, st>>>(pc.Z.p, n, s, t1, k, Rin, ldr, 1.0 / pc.lam_p, Zo,
+                                             ldo, err, Rout, fuse ? *fuse : nof);
     KRR_CHECK_LAUNCH();
     return;
   }
-  auto kern = zw_kernel<BF16, T, ACC, KV>;
+  auto kern = zw_kernel<ZF, T, ACC, KV>;
   if (pl.zw_smem > 48 * 1024)
     KRR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)pl.zw_smem));
@@ -734,11 +825,25 @@ void apply_zl(cudaStream_t st, const Precond& pc, const ApplyPlan& pl, const T* 
 template <typename T, typename ACC, int KV>
 void apply_zl_kv(cudaStream_t st, const Precond& pc, const ApplyPlan& pl, const T* R, int k,
                  int ldr, T* Zo, int ldo, double* t1, double* t2, void* part,
-                 bool ginv_only = false) {
-  if (pc.z_bf16)
-    apply_zl<1, T, ACC, KV>(st, pc, pl, R, k, ldr, Zo, ldo, t1, t2, part, ginv_only);
+                 bool ginv_only = false, const CgStepArgs<T>* fuse = nullptr) {
+  if (pc.z_bf16 == 2)
+    apply_zl<2, T, ACC, KV>(st, pc, pl, R, k, ldr, Zo, ldo, t1, t2, part, ginv_only, fuse);
+  else if (pc.z_bf16)
+    apply_zl<1, T, ACC, KV>(st, pc, pl, R, k, ldr, Zo, ldo, t1, t2, part, ginv_only, fuse);
   else
-    apply_zl<0, T, ACC, KV>(st, pc, pl, R, k, ldr, Zo, ldo, t1, t2, part, ginv_only);
+    apply_zl<0, T, ACC, KV>(st, pc, pl, R, k, ldr, Zo, ldo, t1, t2, part, ginv_only, fuse);
+}
+
+template <typename ACC, int KV>
+bool stream_both(const Precond& pc, const ApplyPlan& pl) {
+  StreamPlan sp;
+  if (pc.z_bf16 == 2)
+    sp = stream_plan<2, ACC, KV>(pc, pl);
+  else if (pc.z_bf16)
+    sp = stream_plan<1, ACC, KV>(pc, pl);
+  else
+    sp = stream_plan<0, ACC, KV>(pc, pl);
+  return sp.zt && sp.zw;
 }
 
 // F[i, c] = sum_b Zf[i, b] w[b, c] (FP64 sums): one warp per row.
@@ -827,6 +932,39 @@ void launch_apply(cudaStream_t st, const Precond& pc, const T* R, int k, int ldr
     default: apply_zl_kv<T, ACC, 16>(st, pc, pl, R, k, ldr, Zo, ldo, t1, t2, part); break;
   }
 }
+
+bool apply_cg_supported(const Precond& pc, int n, int k) {
+  if (pc.form != KRR_APPLY_ZL || !pc.Z.p || pc.n != n || k < 1 || k > KRR_MAX_RHS) return false;
+  const ApplyPlan pl = plan<float>(pc.n, pc.s, k);
+  switch (pl.kv) {
+    case 1: return stream_both<float, 1>(pc, pl);
+    case 2: return stream_both<float, 2>(pc, pl);
+    case 4: return stream_both<float, 4>(pc, pl);
+    case 8: return stream_both<float, 8>(pc, pl);
+    case 12: return stream_both<float, 12>(pc, pl);
+    default: return stream_both<float, 16>(pc, pl);
+  }
+}
+
+template <typename T>
+void launch_apply_cg(cudaStream_t st, const Precond& pc, T* R, int k, T* Zo, double* t1,
+                     double* t2, double* part, const CgStepArgs<T>& f) {
+  static_assert(std::is_same<T, float>::value, "the fused apply serves FP32 vectors");
+  if (!apply_cg_supported(pc, pc.n, k))
+    throw Error{KRR_EINVAL, "fused apply: not available for this preconditioner shape"};
+  const ApplyPlan pl = plan<float>(pc.n, pc.s, k);
+  switch (pl.kv) {
+    case 1: apply_zl_kv<T, float, 1>(st, pc, pl, R, k, k, Zo, k, t1, t2, part, false, &f); break;
+    case 2: apply_zl_kv<T, float, 2>(st, pc, pl, R, k, k, Zo, k, t1, t2, part, false, &f); break;
+    case 4: apply_zl_kv<T, float, 4>(st, pc, pl, R, k, k, Zo, k, t1, t2, part, false, &f); break;
+    case 8: apply_zl_kv<T, float, 8>(st, pc, pl, R, k, k, Zo, k, t1, t2, part, false, &f); break;
+    case 12: apply_zl_kv<T, float, 12>(st, pc, pl, R, k, k, Zo, k, t1, t2, part, false, &f); break;
+    default: apply_zl_kv<T, float, 16>(st, pc, pl, R, k, k, Zo, k, t1, t2, part, false, &f); break;
+  }
+}
+
+template void launch_apply_cg<float>(cudaStream_t, const Precond&, float*, int, float*, double*,
+                                     double*, double*, const CgStepArgs<float>&);
 
 template void launch_apply<float>(cudaStream_t, const Precond&, const float*, int, int, float*,
                                   int, double*, double*, double*);

@@ -9,7 +9,9 @@
 // sum: warp shuffles, one partial per CTA, and the last CTA to finish
 // (atomic counter) adds the partials in CTA order, which keeps the result
 // deterministic, and then updates the scalars.
-#include "krr_internal.cuh"
+#include <algorithm>
+
+#include "krr_cgstep.cuh"
 
 namespace krr {
 namespace {
@@ -17,7 +19,8 @@ namespace {
 constexpr int CT = 256;           // threads per CTA
 constexpr int NW = CT / 32;
 
-enum CounterSlot { C_INIT = 0, C_RZ = 1, C_ALPHA = 2, C_XR = 3, C_NORM = 4 };
+constexpr int C_INIT = CGC_INIT, C_RZ = CGC_RZ, C_ALPHA = CGC_ALPHA, C_XR = CGC_XR,
+              C_NORM = CGC_NORM;
 
 int cg_blocks(int n) {
   int b = (n + CT - 1) / CT;
@@ -25,61 +28,12 @@ int cg_blocks(int n) {
   return b < 1 ? 1 : (b > cap ? cap : b);
 }
 
-// Sum v[c] over the grid.  Returns true in thread 0 of the last CTA to
-// finish, with tot[c] the column totals.  The last CTA adds the per-CTA
-// partials with all its threads (thread t takes CTAs t, t + CT, ...) and a
-// fixed tree, so the result does not depend on the order the CTAs finish in.
-__device__ bool grid_colsum(double (&v)[KRR_MAX_RHS], int k, double* part,
-                            unsigned int* counter, double (&tot)[KRR_MAX_RHS]) {
-  __shared__ double red[NW][KRR_MAX_RHS];
-  __shared__ int last;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int c = 0; c < KRR_MAX_RHS; ++c) {
-    if (c >= k) break;
-    double x = v[c];
-    for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-    if (lane == 0) red[w][c] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x < k) {
-    double s = 0.0;
-    for (int q = 0; q < NW; ++q) s += red[q][threadIdx.x];
-    part[blockIdx.x * KRR_MAX_RHS + threadIdx.x] = s;
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (!last) return false;
-  __threadfence();
-  double loc[KRR_MAX_RHS];
-#pragma unroll
-  for (int c = 0; c < KRR_MAX_RHS; ++c) loc[c] = 0.0;
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += CT) {
-#pragma unroll
-    for (int c = 0; c < KRR_MAX_RHS; ++c)
-      if (c < k) loc[c] += __ldcg(&part[b * KRR_MAX_RHS + c]);
-  }
-#pragma unroll
-  for (int c = 0; c < KRR_MAX_RHS; ++c) {
-    if (c >= k) break;
-    double x = loc[c];
-    for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-    if (lane == 0) red[w][c] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return false;
-  for (int c = 0; c < k; ++c) {
-    double t = 0.0;
-    for (int q = 0; q < NW; ++q) t += red[q][c];
-    tot[c] = t;
-  }
-  *counter = 0u;
-  return true;
+__device__ __forceinline__ bool grid_colsum(double (&v)[KRR_MAX_RHS], int k, double* part,
+                                            unsigned int* counter, double (&tot)[KRR_MAX_RHS]) {
+  return grid_colsum_nt<CT>(v, k, part, counter, blockIdx.x, gridDim.x, tot);
 }
 
-__device__ __forceinline__ bool bad(double x) { return isnan(x) || isinf(x); }
+__device__ __forceinline__ bool bad(double x) { return cg_bad(x); }
 
 template <typename T>
 __global__ void __launch_bounds__(CT)
@@ -257,21 +211,7 @@ cg_alpha_kernel(CgScalars* sc, const T* __restrict__ P, const T* __restrict__ Q,
       }
   }
   if (!grid_colsum(v, k, part, &sc->counter[C_ALPHA], tot)) return;
-  for (int c = 0; c < k; ++c) {
-    sc->pq[c] = tot[c];
-    double a = 0.0;
-    if (sc->active[c]) {
-      if (bad(tot[c])) {
-        sc->flags |= FLAG_NAN;
-      } else if (!(tot[c] > 0.0)) {
-        sc->flags |= FLAG_BREAKDOWN;
-      } else {
-        a = sc->rz[c] / tot[c];
-      }
-    }
-    sc->alpha[c] = a;
-    if (sc->iter < sc->hist_cap) sc->hist[((size_t)sc->iter * 2) * KRR_MAX_RHS + c] = a;
-  }
+  cg_alpha_finish(sc, tot, k);
 }
 
 template <typename T>
@@ -300,14 +240,7 @@ cg_update_xr_kernel(CgScalars* sc, T* __restrict__ X, T* __restrict__ R, const T
       }
   }
   if (!grid_colsum(v, k, part, &sc->counter[C_XR], tot)) return;
-  for (int c = 0; c < k; ++c) {
-    sc->rr[c] = tot[c];
-    if (bad(tot[c])) sc->flags |= FLAG_NAN;
-    if (sc->active[c]) {
-      sc->iters[c] += 1;
-      if (tot[c] <= sc->tol2[c]) sc->active[c] = 0;
-    }
-  }
+  cg_xr_finish(sc, tot, k);
 }
 
 template <typename T>
@@ -326,21 +259,7 @@ cg_rz_kernel(CgScalars* sc, const T* __restrict__ R, const T* __restrict__ Z, in
       }
   }
   if (!grid_colsum(v, k, part, &sc->counter[C_RZ], tot)) return;
-  for (int c = 0; c < k; ++c) {
-    double b = 0.0;
-    if (sc->active[c]) {
-      if (bad(tot[c])) {
-        sc->flags |= FLAG_NAN;
-      } else if (!(tot[c] > 0.0)) {
-        sc->flags |= FLAG_BREAKDOWN;
-      } else {
-        b = tot[c] / sc->rz[c];
-      }
-      sc->rz[c] = tot[c];
-    }
-    sc->beta[c] = b;
-    if (sc->iter < sc->hist_cap) sc->hist[((size_t)sc->iter * 2 + 1) * KRR_MAX_RHS + c] = b;
-  }
+  cg_rz_finish(sc, tot, k);
 }
 
 template <typename T>
@@ -363,17 +282,74 @@ cg_update_p_kernel(const CgScalars* sc, T* __restrict__ P, const T* __restrict__
   }
 }
 
-__global__ void cg_tail_kernel(CgScalars* sc, cudaGraphConditionalHandle cond) {
-  int any = 0;
-  for (int c = 0; c < sc->k; ++c) any |= sc->active[c];
-  sc->iter += 1;
-  bool stop = !any || (sc->flags & (FLAG_BREAKDOWN | FLAG_NAN));
-  if (!stop && sc->iter >= sc->max_iter) {
-    sc->flags |= FLAG_CAP;
-    stop = true;
+// The tensor-core product's chunk sums finished and p.q reduced in the same
+// pass: q_i = ra_i sum_ch part[ch, i] + shift p_i (FP64 sum over the chunks,
+// rounded to T), then alpha = r.z / p.q as in cg_alpha_kernel.
+template <typename T>
+__global__ void __launch_bounds__(CT)
+cg_reduce_alpha_kernel(CgScalars* sc, const float* __restrict__ part, int nchunk, int n_rpad,
+                       int kv, const float* __restrict__ ra, double shift,
+                       const T* __restrict__ P, T* __restrict__ Q, int n, int k, double* cpart) {
+  double v[KRR_MAX_RHS], tot[KRR_MAX_RHS];
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c) v[c] = 0.0;
+  for (int i = blockIdx.x * CT + threadIdx.x; i < n; i += gridDim.x * CT) {
+    const double rai = (double)ra[i];
+#pragma unroll
+    for (int c = 0; c < KRR_MAX_RHS; ++c)
+      if (c < k) {
+        double s = 0.0;
+        for (int ch = 0; ch < nchunk; ++ch) s += (double)part[((size_t)ch * n_rpad + i) * kv + c];
+        s *= rai;
+        const size_t e = (size_t)i * k + c;
+        const double p = (double)P[e];
+        if (shift != 0.0) s += shift * p;
+        const T q = (T)s;
+        Q[e] = q;
+        v[c] = fma(p, (double)q, v[c]);
+      }
   }
-  sc->run = stop ? 0 : 1;
-  if (cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
+  if (!grid_colsum(v, k, cpart, &sc->counter[C_ALPHA], tot)) return;
+  cg_alpha_finish(sc, tot, k);
+}
+
+// p = z + beta p for the active columns (update != 0), then the product's
+// weights w[j, c] = ra_j p[j, c] over the padded n_pad x kv block (zero for
+// rows >= n and columns >= k), as the product's own weight kernel forms them.
+template <typename T>
+__global__ void __launch_bounds__(CT)
+cg_update_pw_kernel(const CgScalars* sc, T* __restrict__ P, const T* __restrict__ Z, int n, int k,
+                    int update, const float* __restrict__ ra, int n_pad, int kv,
+                    float* __restrict__ w) {
+  double b[KRR_MAX_RHS];
+  int act[KRR_MAX_RHS];
+#pragma unroll
+  for (int c = 0; c < KRR_MAX_RHS; ++c) {
+    b[c] = c < k ? sc->beta[c] : 0.0;
+    act[c] = (update && c < k) ? sc->active[c] : 0;
+  }
+  for (int i = blockIdx.x * CT + threadIdx.x; i < n_pad; i += gridDim.x * CT) {
+    const float rai = i < n ? ra[i] : 0.f;
+#pragma unroll
+    for (int c = 0; c < KRR_MAX_RHS; ++c) {
+      if (c >= kv) break;
+      float wv = 0.f;
+      if (i < n && c < k) {
+        const size_t e = (size_t)i * k + c;
+        T p = P[e];
+        if (act[c]) {
+          p = (T)((double)Z[e] + b[c] * (double)p);
+          P[e] = p;
+        }
+        wv = rai * (float)p;
+      }
+      w[(size_t)i * kv + c] = wv;
+    }
+  }
+}
+
+__global__ void cg_tail_kernel(CgScalars* sc, cudaGraphConditionalHandle cond) {
+  cg_tail_finish(sc, cond);
 }
 
 __global__ void batch_gate_kernel(CgScalars* const* scs, const unsigned long long* conds,
@@ -490,7 +466,9 @@ int ew_blocks(size_t total) {
 
 size_t cg_part_elems(int n, int k) {
   (void)k;
-  return (size_t)cg_blocks(n) * KRR_MAX_RHS;
+  // also the partials of the fused reductions, whose kernels run up to two
+  // CTAs per SM whatever n is
+  return (size_t)std::max(cg_blocks(n), 2 * sm_count()) * KRR_MAX_RHS;
 }
 
 template <typename T>
@@ -546,6 +524,29 @@ void launch_cg_update_p(cudaStream_t st, CgScalars* sc, T* P, const T* Z, int n,
   cg_update_p_kernel<T><<<ew_blocks((size_t)n), CT, 0, st>>>(sc, P, Z, n, k);
   KRR_CHECK_LAUNCH();
 }
+
+template <typename T>
+void launch_cg_reduce_alpha(cudaStream_t st, CgScalars* sc, const float* part, int nchunk,
+                            int n_rpad, int kv, const float* ra, double shift, const T* P, T* Q,
+                            int n, int k, double* cpart) {
+  cg_reduce_alpha_kernel<T><<<cg_blocks(n), CT, 0, st>>>(sc, part, nchunk, n_rpad, kv, ra, shift,
+                                                        P, Q, n, k, cpart);
+  KRR_CHECK_LAUNCH();
+}
+
+template <typename T>
+void launch_cg_update_pw(cudaStream_t st, CgScalars* sc, T* P, const T* Z, int n, int k,
+                         int update, const float* ra, int n_pad, int kv, float* w) {
+  cg_update_pw_kernel<T><<<ew_blocks((size_t)n_pad), CT, 0, st>>>(sc, P, Z, n, k, update, ra,
+                                                                  n_pad, kv, w);
+  KRR_CHECK_LAUNCH();
+}
+
+template void launch_cg_reduce_alpha<float>(cudaStream_t, CgScalars*, const float*, int, int,
+                                            int, const float*, double, const float*, float*,
+                                            int, int, double*);
+template void launch_cg_update_pw<float>(cudaStream_t, CgScalars*, float*, const float*, int,
+                                         int, int, const float*, int, int, float*);
 
 void launch_cg_tail(cudaStream_t st, CgScalars* sc, unsigned long long cond) {
   cg_tail_kernel<<<1, 1, 0, st>>>(sc, (cudaGraphConditionalHandle)cond);

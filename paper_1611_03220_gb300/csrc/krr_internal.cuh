@@ -92,7 +92,7 @@ struct Precond {
   int n = 0, s = 0, form = KRR_APPLY_ZL, z_bf16 = 0;
   int z_fixed_e = 0;  // fixed-point features: Z ~= 2^e Zs (0 otherwise)
   double lam_p = 0.0;
-  DevBuf Z;      // n x s (ld = s), FP32 or BF16
+  DevBuf Z;      // n x s (ld = s): FP32 (z_bf16 0), BF16 (1) or 8-bit q (2, Z = q / 128)
   DevBuf L;      // s x s FP64 lower Cholesky factor of G
   DevBuf Linv;   // s x s FP64 lower inverse of L (ZL form)
   DevBuf LinvT;  // s x s FP64, (L^-1)^T, upper (ZL form)
@@ -142,14 +142,14 @@ int setup_tc_s_pad(int s);
 int setup_tc_kp(int d);
 int fixed_point_exponent(double maxabs);
 size_t gram_tc_part_elems(int n, int s);
-// Features of X (n x d, ldx) for W (d x s), b (s): Z (n x s BF16) and Z^T;
-// returns e.
+// Features of X (n x d, ldx) for W (d x s), b (s): Z as the 8-bit q
+// (n x s, Zs = q / 128) and Zs^T (BF16); returns e.
 int launch_rff_tc(cudaStream_t st, const float* X, int n, int d, int ldx, const float* W,
                   const float* b, int s, __nv_bfloat16* Xh, __nv_bfloat16* Xl,
-                  __nv_bfloat16* Wh, __nv_bfloat16* Wl, __nv_bfloat16* Z, __nv_bfloat16* ZT,
+                  __nv_bfloat16* Wh, __nv_bfloat16* Wl, signed char* Z, __nv_bfloat16* ZT,
                   int* err);
 // Fixed-point copy of a caller's FP32 Z (synchronises once for max |Z|); returns e.
-int launch_quantize_z(cudaStream_t st, const float* Z, int n, int s, int ldz, __nv_bfloat16* Zs,
+int launch_quantize_z(cudaStream_t st, const float* Z, int n, int s, int ldz, signed char* Zs,
                       __nv_bfloat16* ZT, int* scratch);
 // F = scale A B^T (A: n x K, B: s x K, FP32 row-major) on tcgen05 from split
 // BF16 operands (about 2^-16 of sum |a||b| per entry); the split buffers are
@@ -192,7 +192,12 @@ void launch_gram(cudaStream_t st, const void* Zs, int bf16, int n, int s, double
                  double* G, double* part, int nchunk);
 int gram_chunks(int n, int s);
 void launch_cholesky(cudaStream_t st, double* A, int s, int* info);
-void launch_tri_inverse(cudaStream_t st, const double* L, int s, double* Linv);
+// Linv = L^-1 (lower, FP64) by recursive blocking; scratch: tri_inverse_scratch_elems(s).
+size_t tri_inverse_scratch_elems(int s);
+void launch_tri_inverse(cudaStream_t st, const double* L, int s, double* Linv, double* scratch);
+// C = alpha op(A) op(B) + beta C, FP64, row-major with leading dimensions.
+void launch_gemm_d(cudaStream_t st, int m, int n, int k, double alpha, const double* A, int lda,
+                   int ta, const double* B, int ldb, int tb, double beta, double* C, int ldc);
 void launch_transpose_d(cudaStream_t st, const double* A, int s, double* B);
 void launch_form_u(cudaStream_t st, const double* Linv, const void* Zs, int bf16, int n, int s,
                    float* U);
@@ -210,6 +215,29 @@ void launch_feature_gemv(cudaStream_t st, const float* Zf, int m, int s, const d
 template <typename T>
 void launch_apply(cudaStream_t st, const Precond& pc, const T* R, int k, int ldr, T* Zo,
                   int ldo, double* t1, double* t2, double* part);
+
+// The apply with one PCG iteration's vector work fused into its two streamed
+// passes over Z (the fused loop body, vectors n x k with ld = k):
+//   Z^T pass: r' = r - alpha q and x' = x + alpha p (alpha from sc), written
+//             to Rn and X, ||r'||^2 reduced and the stopping test applied;
+//   Z w pass: z = M^-1 r' from Rn, r' copied back to R, r'.z reduced, beta
+//             and the loop's continue decision (graph condition `cond`).
+template <typename T>
+struct CgStepArgs {
+  CgScalars* sc = nullptr;
+  T* X = nullptr;
+  const T* P = nullptr;
+  const T* Q = nullptr;
+  T* Rn = nullptr;            // n x k scratch: the updated residual between the passes
+  double* cpart = nullptr;    // cg_part_elems() doubles (the CG reductions' partials)
+  unsigned long long cond = 0;
+};
+// True when launch_apply_cg can serve k right-hand sides (the streamed ZL
+// kernels: rows of Z 16-byte aligned, the staged rows within shared memory).
+bool apply_cg_supported(const Precond& pc, int n, int k);
+template <typename T>
+void launch_apply_cg(cudaStream_t st, const Precond& pc, T* R, int k, T* Zo, double* t1,
+                     double* t2, double* part, const CgStepArgs<T>& f);
 
 // CG vector kernels (krr_cg.cu).  `part` is cg_part_elems() doubles.
 struct ColScale {
@@ -242,6 +270,17 @@ void launch_cg_rz(cudaStream_t st, CgScalars* sc, const T* R, const T* Z, int n,
                   double* part);
 template <typename T>
 void launch_cg_update_p(cudaStream_t st, CgScalars* sc, T* P, const T* Z, int n, int k);
+// The fused loop body's CG steps (FP32 vectors, the tensor-core product):
+// q from the product's chunk sums (nchunk x n_rpad x kv, row factors ra) with
+// p.q and alpha in the same pass; and p = z + beta p (update != 0) with the
+// product's weights w = ra p (n_pad x kv) for the next iteration.
+template <typename T>
+void launch_cg_reduce_alpha(cudaStream_t st, CgScalars* sc, const float* part, int nchunk,
+                            int n_rpad, int kv, const float* ra, double shift, const T* P, T* Q,
+                            int n, int k, double* cpart);
+template <typename T>
+void launch_cg_update_pw(cudaStream_t st, CgScalars* sc, T* P, const T* Z, int n, int k,
+                         int update, const float* ra, int n_pad, int kv, float* w);
 // iter += 1; decides whether the loop continues; sets the graph condition
 // when `cond` is nonzero (a cudaGraphConditionalHandle).
 void launch_cg_tail(cudaStream_t st, CgScalars* sc, unsigned long long cond);

@@ -23,14 +23,16 @@
 // two column halves (shared memory, one named barrier per row quadrant).
 //
 // Status: correct (it passes the same parity tests as the full product) but
-// slower on this GPU -- 0.85 ms against 0.65 ms for tc_matvec_kernel at
-// n = 65,536 -- so it is only a candidate of the tile-plan autotuner.  The
+// slower on this GPU -- at n = 65,536 0.845 ms with 16 epilogue warps and
+// 0.868 ms with 8, against 0.676 ms for tc_matvec_kernel -- so it is only a
+// candidate of the tile-plan autotuner (modes 2 and 3 select it).  The
 // epilogue needs about three issue slots per exponential (row FMA, column FMA,
-// MUFU) against two in the full product, and the 64 column accumulators cap
-// the epilogue at eight warps; ncu puts the MUFU at 28 % of its peak with
-// fixed-latency and TMEM-load stalls on top.  Packed FP32 FMAs, four TMEM
-// accumulators, 16-column TMEM chunks with the next one in flight and split
-// row-sum chains each left the time unchanged.
+// MUFU) against two in the full product, and every tile ends in a combine of
+// its row sums across the column groups (a named barrier per row quadrant);
+// ncu put the 8-warp MUFU at 28 % of its peak with fixed-latency and
+// TMEM-load stalls on top.  Packed FP32 FMAs, four TMEM accumulators,
+// 16-column TMEM chunks with the next one in flight, split row-sum chains and
+// twice the epilogue warps each left the time within 3 %.
 //
 // Output: rowpart[J][i] = sum over columns of J of E_ij w_j (i in I <= J) and
 // colpart[c][j] = the column sums of item c of column block J(j); a second
@@ -41,7 +43,7 @@
 // once, into one of two resident buffers; each row block into a ring of NS
 // stages), warp 1 issues
 // the MMAs (M = N = 128, K = 16, four FP32 accumulators in the 512 TMEM
-// columns) and warps 2..9 are the epilogue.  Every mbarrier wait is
+// columns) and warps 2.. are the epilogue (8 or 16 warps).  Every mbarrier wait is
 // bounded; on expiry the kernel raises the error flag, drains its own copies
 // and MMAs, frees TMEM and returns.
 #include <cuda.h>

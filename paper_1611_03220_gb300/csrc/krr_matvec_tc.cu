@@ -1270,6 +1270,8 @@ TcOperand& operand_of(TcState& t, int fmt) {
   return fmt == 1 ? t.split : (fmt == 2 ? t.half : t.cols);
 }
 
+void run_core(TcState& t, cudaStream_t st, TcOperand& op, const Plan& pl, int split, int f16);
+
 // Enqueue one fused product with plan `pl` (w, kernel, chunk sums).
 void run_fused(TcState& t, cudaStream_t st, TcOperand& op, const Plan& pl, int split, int f16,
                int nr, const float* V, int k, int ldv, double shift, float* Q, int ldq) {
@@ -1277,12 +1279,23 @@ void run_fused(TcState& t, cudaStream_t st, TcOperand& op, const Plan& pl, int s
     sym_matvec(t, st, op, f16, pl.C, pl.ns, nr, V, ldv, shift, Q, ldq, pl.nepi);
     return;
   }
-  const int nkb = split ? 2 : op.kp / BK;
-  const int a_res = (split || nkb == 1) ? 1 : 0;
   make_w_kernel<<<std::min(8 * sm_count(), (int)(((size_t)op.n_pad * pl.kv + 255) / 256)), 256,
                   0, st>>>(V, op.n, k, ldv, (const float*)op.ra.p, op.n_pad, pl.kv,
                            (float*)t.w.p);
   KRR_CHECK_LAUNCH();
+  run_core(t, st, op, pl, split, f16);
+  const size_t total = (size_t)nr * k;
+  tc_reduce_kernel<<<std::min(8 * sm_count(), (int)((total + 255) / 256)), 256, 0, st>>>(
+      (const float*)t.part.p, pl.nchunk, op.n_pad, pl.kv, (const float*)op.ra.p, nr, k, V, ldv,
+      shift, Q, ldq);
+  KRR_CHECK_LAUNCH();
+}
+
+// The product kernel alone of plan `pl`: chunk sums of exp2(S) w into t.part
+// from the weights already in t.w.
+void run_core(TcState& t, cudaStream_t st, TcOperand& op, const Plan& pl, int split, int f16) {
+  const int nkb = split ? 2 : op.kp / BK;
+  const int a_res = (split || nkb == 1) ? 1 : 0;
   TcParams p;
   p.n_rt = pl.n_rt;
   p.n_ct = pl.n_ct;
@@ -1300,11 +1313,6 @@ void run_fused(TcState& t, cudaStream_t st, TcOperand& op, const Plan& pl, int s
   const int items = pl.n_rt * pl.nchunk;
   const int grid = std::min(items, sm_count());
   dispatch(pl.kv, st, op, p, grid, pl.kv == 1 ? pl.emu : 0);
-  const size_t total = (size_t)nr * k;
-  tc_reduce_kernel<<<std::min(8 * sm_count(), (int)((total + 255) / 256)), 256, 0, st>>>(
-      (const float*)t.part.p, pl.nchunk, op.n_pad, pl.kv, (const float*)op.ra.p, nr, k, V, ldv,
-      shift, Q, ldq);
-  KRR_CHECK_LAUNCH();
 }
 
 // The fused product for a row set other than the columns (prediction, the
@@ -1675,6 +1683,37 @@ void tc_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr, c
     return;
   }
   run_fused(t, st, op, pl, split, f16, nr, V, k, ldv, shift, Q, ldq);
+}
+
+bool tc_loop_prepare(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int d,
+                     double sigma, int k, int split, int f16, TcLoop* out) {
+  if (f16 && split) return false;
+  if (split)
+    tc_prepare_split(t, st, X, n, ldx, d, sigma);
+  else if (f16)
+    tc_prepare_f16(t, st, X, n, ldx, d, sigma);
+  else
+    tc_prepare(t, st, X, n, ldx, d, sigma);
+  const int fmt = split ? 1 : (f16 ? 2 : 0);
+  tc_reserve(t, st, k, 0, fmt);
+  TcOperand& op = operand_of(t, fmt);
+  const Plan pl = resolve_plan(t, st, op, k, 0, fmt);
+  if (pl.sym) return false;
+  out->ra = (const float*)op.ra.p;
+  out->w = (float*)t.w.p;
+  out->part = (const float*)t.part.p;
+  out->n_pad = op.n_pad;
+  out->kv = pl.kv;
+  out->nchunk = pl.nchunk;
+  return true;
+}
+
+void tc_loop_product(TcState& t, cudaStream_t st, int k, int split, int f16) {
+  const int fmt = split ? 1 : (f16 ? 2 : 0);
+  TcOperand& op = operand_of(t, fmt);
+  const Plan pl = resolve_plan(t, st, op, k, 0, fmt);
+  if (pl.sym) throw Error{KRR_EINVAL, "loop product: the plan changed since tc_loop_prepare"};
+  run_core(t, st, op, pl, split, f16);
 }
 
 void tc_dsigma_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr,

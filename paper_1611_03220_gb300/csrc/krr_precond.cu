@@ -23,9 +23,11 @@ namespace {
 
 constexpr int NB = 64;   // block size of every s x s kernel
 
+// One stored feature: FP32 (0), BF16 (1) or an 8-bit fixed-point q / 128 (2).
 template <int BF16>
 __device__ __forceinline__ float zload(const void* Zs, size_t idx) {
-  if (BF16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(Zs)[idx]);
+  if (BF16 == 1) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(Zs)[idx]);
+  if (BF16 == 2) return (float)reinterpret_cast<const signed char*>(Zs)[idx] * 0.0078125f;
   return reinterpret_cast<const float*>(Zs)[idx];
 }
 
@@ -264,6 +266,61 @@ __global__ void zero_upper_kernel(double* A, int s) {
   }
 }
 
+// -------------------------------------------------------- FP64 products --
+// C = alpha op(A) op(B) + beta C with op(A) m x k, op(B) k x n, row-major
+// with leading dimensions; op(X) = X^T when tX.  64 x 64 output tiles of
+// 16 x 16 threads, 4 x 4 results each, K in slabs of 16 through shared
+// memory.  C must not alias A or B.
+constexpr int GT = 64;
+constexpr int GKS = 16;
+
+__global__ void __launch_bounds__(256)
+gemm_f64_kernel(int m, int n, int k, double alpha, const double* __restrict__ A, int lda, int ta,
+                const double* __restrict__ B, int ldb, int tb, double beta,
+                double* __restrict__ C, int ldc) {
+  __shared__ double As[GKS][GT + 1];
+  __shared__ double Bs[GKS][GT + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
+  double acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+  for (int k0 = 0; k0 < k; k0 += GKS) {
+    for (int e = threadIdx.x; e < GKS * GT; e += 256) {
+      const int t = ta ? e / GT : e % GKS, r = ta ? e % GT : e / GKS;
+      const int i = i0 + r, kk = k0 + t;
+      As[t][r] = (i < m && kk < k) ? (ta ? A[(size_t)kk * lda + i] : A[(size_t)i * lda + kk]) : 0.0;
+    }
+    for (int e = threadIdx.x; e < GKS * GT; e += 256) {
+      const int t = tb ? e % GKS : e / GT, c = tb ? e / GKS : e % GT;
+      const int j = j0 + c, kk = k0 + t;
+      Bs[t][c] = (j < n && kk < k) ? (tb ? B[(size_t)j * ldb + kk] : B[(size_t)kk * ldb + j]) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < GKS; ++t)
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(As[t][ty + 16 * r], Bs[t][tx + 16 * c], acc[r][c]);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = i0 + ty + 16 * r;
+    if (i >= m) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = j0 + tx + 16 * c;
+      if (j >= n) continue;
+      double* cp = C + (size_t)i * ldc + j;
+      *cp = alpha * acc[r][c] + (beta != 0.0 ? beta * *cp : 0.0);
+    }
+  }
+}
+
 // ------------------------------------------------------ triangular inverse --
 // Diagonal blocks: D_kk = L_kk^-1 by forward substitution, one column per
 // thread.
@@ -294,63 +351,6 @@ __global__ void __launch_bounds__(NB) diag_inv_kernel(const double* L, int s, do
   }
 }
 
-// Off-diagonal block (I, J), J < I:
-//   Linv[I, J] = -D_II * sum_{q = J*NB}^{I*NB-1} L[I, q] Linv[q, J].
-// Launched once per block row I (blocks J = 0..I-1 in parallel) because
-// block row I reads every earlier block row.
-__global__ void __launch_bounds__(256)
-offdiag_inv_kernel(const double* L, int s, int I, double* Linv) {
-  extern __shared__ double sm[];
-  double* Sacc = sm;                    // NB x (NB+1): the sum
-  double* Dt = sm + NB * (NB + 1);      // NB x (NB+1): D_II
-  __shared__ double Pa[16][NB + 1];
-  __shared__ double Pb[16][NB + 1];
-  const int J = blockIdx.x;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int oI = I * NB, nI = min(NB, s - oI);
-  const int oJ = J * NB;
-  double acc[4][4];
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
-  for (int q0 = oJ; q0 < oI; q0 += 16) {
-    __syncthreads();
-    for (int e = tid; e < 16 * NB; e += 256) {
-      int row = e / 16, t = e % 16;
-      int q = q0 + t;
-      Pa[t][row] = (row < nI && q < oI) ? L[(size_t)(oI + row) * s + q] : 0.0;
-    }
-    for (int e = tid; e < 16 * NB; e += 256) {
-      int t = e / NB, col = e % NB;
-      int q = q0 + t;
-      Pb[t][col] = (q < oI) ? Linv[(size_t)q * s + oJ + col] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < 16; ++t)
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-          acc[r][c] = fma(Pa[t][ty + 16 * r], Pb[t][tx + 16 * c], acc[r][c]);
-  }
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) Sacc[(ty + 16 * r) * (NB + 1) + tx + 16 * c] = acc[r][c];
-  for (int e = tid; e < NB * NB; e += 256) {
-    int i = e / NB, j = e % NB;
-    Dt[i * (NB + 1) + j] = (i < nI && j < nI) ? Linv[(size_t)(oI + i) * s + oI + j] : 0.0;
-  }
-  __syncthreads();
-  for (int e = tid; e < nI * NB; e += 256) {
-    int i = e / NB, j = e % NB;
-    double v = 0.0;
-    for (int m = 0; m <= i; ++m) v = fma(Dt[i * (NB + 1) + m], Sacc[m * (NB + 1) + j], v);
-    Linv[(size_t)(oI + i) * s + oJ + j] = -v;
-  }
-}
 
 __global__ void transpose_d_kernel(const double* __restrict__ A, int s, double* __restrict__ B) {
   __shared__ double t[32][33];
@@ -466,22 +466,47 @@ void launch_cholesky(cudaStream_t st, double* A, int s, int* info) {
   KRR_CHECK_LAUNCH();
 }
 
-void launch_tri_inverse(cudaStream_t st, const double* L, int s, double* Linv) {
+namespace {
+// Recursive blocked inverse of the lower triangle L[o:o+m, o:o+m] (m a
+// multiple of NB or the tail of the matrix): with L = [L11 0; L21 L22],
+// L^-1 = [X11 0; X21 X22], X21 = -X22 L21 X11.  The diagonal NB-blocks are
+// already inverted; each level adds two FP64 products, so the work is in a
+// few large GEMMs rather than a serial sweep of block rows.  T: scratch of
+// at least (m/2) x (m/2) doubles (ld s).
+void tri_inverse_rec(cudaStream_t st, const double* L, int s, double* Linv, int o, int m,
+                     double* T) {
+  if (m <= NB) return;
+  const int nb = (m + NB - 1) / NB;
+  const int h = (nb / 2) * NB;          // split at a block boundary
+  const int m2 = m - h;
+  tri_inverse_rec(st, L, s, Linv, o, h, T);
+  tri_inverse_rec(st, L, s, Linv, o + h, m2, T);
+  // T = L21 X11 (m2 x h), then X21 = -X22 T (m2 x h)
+  dim3 g1((h + GT - 1) / GT, (m2 + GT - 1) / GT);
+  gemm_f64_kernel<<<g1, 256, 0, st>>>(m2, h, h, 1.0, L + (size_t)(o + h) * s + o, s, 0,
+                                      Linv + (size_t)o * s + o, s, 0, 0.0, T, s);
+  KRR_CHECK_LAUNCH();
+  gemm_f64_kernel<<<g1, 256, 0, st>>>(m2, h, m2, -1.0, Linv + (size_t)(o + h) * s + o + h, s, 0,
+                                      T, s, 0, 0.0, Linv + (size_t)(o + h) * s + o, s);
+  KRR_CHECK_LAUNCH();
+}
+}  // namespace
+
+size_t tri_inverse_scratch_elems(int s) { return ((size_t)s / 2 + NB) * (size_t)s; }
+
+void launch_tri_inverse(cudaStream_t st, const double* L, int s, double* Linv, double* scratch) {
   const int T = (s + NB - 1) / NB;
   KRR_CUDA(cudaMemsetAsync(Linv, 0, (size_t)s * s * sizeof(double), st));
   diag_inv_kernel<<<T, NB, 0, st>>>(L, s, Linv);
   KRR_CHECK_LAUNCH();
-  const size_t smem = 2 * NB * (NB + 1) * sizeof(double);
-  static bool attr_set = false;
-  if (!attr_set) {
-    KRR_CUDA(cudaFuncSetAttribute(offdiag_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
-    attr_set = true;
-  }
-  for (int I = 1; I < T; ++I) {
-    offdiag_inv_kernel<<<I, 256, smem, st>>>(L, s, I, Linv);
-    KRR_CHECK_LAUNCH();
-  }
+  if (T > 1) tri_inverse_rec(st, L, s, Linv, 0, s, scratch);
+}
+
+void launch_gemm_d(cudaStream_t st, int m, int n, int k, double alpha, const double* A, int lda,
+                   int ta, const double* B, int ldb, int tb, double beta, double* C, int ldc) {
+  dim3 g((n + GT - 1) / GT, (m + GT - 1) / GT);
+  gemm_f64_kernel<<<g, 256, 0, st>>>(m, n, k, alpha, A, lda, ta, B, ldb, tb, beta, C, ldc);
+  KRR_CHECK_LAUNCH();
 }
 
 void launch_transpose_d(cudaStream_t st, const double* A, int s, double* B) {
@@ -493,7 +518,9 @@ void launch_transpose_d(cudaStream_t st, const double* A, int s, double* B) {
 void launch_form_u(cudaStream_t st, const double* Linv, const void* Zs, int bf16, int n, int s,
                    float* U) {
   dim3 grid((n + NB - 1) / NB, (s + NB - 1) / NB);
-  if (bf16)
+  if (bf16 == 2)
+    form_u_kernel<2><<<grid, 256, 0, st>>>(Linv, Zs, n, s, U);
+  else if (bf16)
     form_u_kernel<1><<<grid, 256, 0, st>>>(Linv, Zs, n, s, U);
   else
     form_u_kernel<0><<<grid, 256, 0, st>>>(Linv, Zs, n, s, U);

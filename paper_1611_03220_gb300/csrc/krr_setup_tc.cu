@@ -15,7 +15,8 @@
 // preconditioner is built from these quantised features: with
 // Zt = 2^e Zs,  (Zt Zt^T + lambda_p I)^-1 = (r - Zs G'^-1 Zs^T r) / lambda_p
 // where G' = Zs^T Zs + lambda_p 2^-2e I, so the Woodbury apply runs unchanged
-// on Zs (stored BF16: q / 128 is exact in BF16).
+// on Zs.  The apply reads the 8-bit q (one byte per feature, half the bytes
+// of BF16); the Gram reads Zs^T in BF16 (q / 128 is exact in BF16).
 //
 // Exact Gram.  Every product zs_i zs_j = q_i q_j 2^-14 is exact in FP32, and
 // a sum of 256 of them is an integer multiple of 2^-14 below 2^8, i.e. fewer
@@ -66,7 +67,7 @@ struct RffParams {
   const float* b;       // s phases
   float zscale;         // sqrt(2/s) (the plain product's scale with MODE 1)
   float qscale;         // 2^(7-e)
-  __nv_bfloat16* Z;     // n x s, ld s
+  signed char* Z;       // n x s, ld s: the 8-bit q of Zs = q / 128
   __nv_bfloat16* ZT;    // s_pad x n_pad
   float* F;             // MODE 1: F = zscale X W (n x s, ld ldf), FP32
   int ldf;
@@ -285,24 +286,25 @@ rff_tc_kernel(const __grid_constant__ CUtensorMap tmXh, const __grid_constant__ 
       for (int c = 0; c < 64; ++c)
         p.ZT[(size_t)(j0 + c) * p.n_pad + i] = __float2bfloat16_rn(__uint_as_float(raw[c]));
       if (row_ok) {
-        __nv_bfloat16* zr = p.Z + (size_t)i * p.s;
-        if ((p.s & 7) == 0 && j0 + 64 <= p.s && ((uintptr_t)p.Z & 15) == 0) {
+        signed char* zr = p.Z + (size_t)i * p.s;
+        if ((p.s & 15) == 0 && j0 + 64 <= p.s && ((uintptr_t)p.Z & 15) == 0) {
 #pragma unroll
-          for (int c = 0; c < 64; c += 8) {
-            uint4 v;
-            __nv_bfloat162 t0 = __floats2bfloat162_rn(__uint_as_float(raw[c]), __uint_as_float(raw[c + 1]));
-            __nv_bfloat162 t1 = __floats2bfloat162_rn(__uint_as_float(raw[c + 2]), __uint_as_float(raw[c + 3]));
-            __nv_bfloat162 t2 = __floats2bfloat162_rn(__uint_as_float(raw[c + 4]), __uint_as_float(raw[c + 5]));
-            __nv_bfloat162 t3 = __floats2bfloat162_rn(__uint_as_float(raw[c + 6]), __uint_as_float(raw[c + 7]));
-            v.x = *reinterpret_cast<uint32_t*>(&t0);
-            v.y = *reinterpret_cast<uint32_t*>(&t1);
-            v.z = *reinterpret_cast<uint32_t*>(&t2);
-            v.w = *reinterpret_cast<uint32_t*>(&t3);
-            *reinterpret_cast<uint4*>(zr + j0 + c) = v;
+          for (int c = 0; c < 64; c += 16) {
+            uint32_t wd[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              uint32_t b = 0;
+#pragma unroll
+              for (int v = 0; v < 4; ++v)
+                b |= ((uint32_t)(uint8_t)(signed char)(int)(__uint_as_float(raw[c + 4 * u + v]) * 128.f))
+                     << (8 * v);
+              wd[u] = b;
+            }
+            *reinterpret_cast<uint4*>(zr + j0 + c) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
           }
         } else {
           for (int c = 0; c < 64 && j0 + c < p.s; ++c)
-            zr[j0 + c] = __float2bfloat16_rn(__uint_as_float(raw[c]));
+            zr[j0 + c] = (signed char)(int)(__uint_as_float(raw[c]) * 128.f);
         }
       }
     }
@@ -497,7 +499,7 @@ __global__ void absmax_kernel(const float* __restrict__ Z, int n, int s, int ldz
 // rint(z * qscale) of the FP32 input.
 __global__ void quantize_z_kernel(const float* __restrict__ Z, int n, int s, int ldz,
                                   float qscale, int n_pad, int s_pad,
-                                  __nv_bfloat16* __restrict__ Zs, __nv_bfloat16* __restrict__ ZT) {
+                                  signed char* __restrict__ Zs, __nv_bfloat16* __restrict__ ZT) {
   // 32 x 32 tiles through shared memory so both outputs are written coalesced
   __shared__ float t[32][33];
   const int tiles_j = s_pad / 32;
@@ -511,7 +513,7 @@ __global__ void quantize_z_kernel(const float* __restrict__ Z, int n, int s, int
       if (i < n && j < s) {
         const float q = fminf(fmaxf(rintf(Z[(size_t)i * ldz + j] * qscale), -127.f), 127.f);
         zs = q * 0.0078125f;
-        Zs[(size_t)i * s + j] = __float2bfloat16_rn(zs);
+        Zs[(size_t)i * s + j] = (signed char)(int)q;
       }
       t[r][threadIdx.x] = zs;
     }
@@ -570,7 +572,7 @@ void launch_split_rows(cudaStream_t st, const float* A, int rows, int cols, size
 
 int launch_rff_tc(cudaStream_t st, const float* X, int n, int d, int ldx, const float* W,
                   const float* b, int s, __nv_bfloat16* Xh, __nv_bfloat16* Xl,
-                  __nv_bfloat16* Wh, __nv_bfloat16* Wl, __nv_bfloat16* Z, __nv_bfloat16* ZT,
+                  __nv_bfloat16* Wh, __nv_bfloat16* Wl, signed char* Z, __nv_bfloat16* ZT,
                   int* err) {
   const int n_pad = setup_tc_n_pad(n), s_pad = setup_tc_s_pad(s), kp = setup_tc_kp(d);
   launch_split_rows(st, X, n, d, (size_t)ldx, 1, n_pad, kp, Xh, Xl);
@@ -608,7 +610,7 @@ int launch_rff_tc(cudaStream_t st, const float* X, int n, int d, int ldx, const 
   return e;
 }
 
-int launch_quantize_z(cudaStream_t st, const float* Z, int n, int s, int ldz, __nv_bfloat16* Zs,
+int launch_quantize_z(cudaStream_t st, const float* Z, int n, int s, int ldz, signed char* Zs,
                       __nv_bfloat16* ZT, int* scratch) {
   KRR_CUDA(cudaMemsetAsync(scratch, 0, sizeof(int), st));
   const size_t total = (size_t)n * s;

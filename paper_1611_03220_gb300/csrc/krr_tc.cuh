@@ -68,6 +68,31 @@ struct HpState {
   CUtensorMap map_b;
 };
 
+// One persistent launch for the products of many problems (krr_matvec_batch.cu).
+constexpr int BATCH_MAX = 64;
+struct BatchProb {
+  const TcOperand* op;   // the problem's prepared FP16 points (TcState::half)
+  const float* V;        // n x 1 right-hand side (device)
+  float* Q;              // n x 1 product (device)
+  double shift;          // lambda of the problem's system
+  const int* run;        // the problem's loop flag: no work while it is 0
+};
+struct BatchState {
+  DevBuf items, table, w, part, err;
+  int n_items = 0, nprob = 0;
+  std::vector<int> chunks;   // per problem: column chunks of its row tiles
+};
+// Plans the work list of `probs` (at most BATCH_MAX, FP16 points, d <= 128)
+// and allocates the shared buffers; call before a graph capture.
+void tc_batch_reserve(BatchState& bs, cudaStream_t st, const std::vector<BatchProb>& probs);
+// Enqueues the products of every problem whose run flag is set: the weights,
+// the persistent kernel over all problems' (row tile, column chunk) items and
+// the chunk sums (three launches).
+void tc_batch_matvec(BatchState& bs, cudaStream_t st, const std::vector<BatchProb>& probs);
+// Nonzero if a batched launch hit a bounded-wait limit since the reserve.
+int tc_batch_error(BatchState& bs, cudaStream_t st);
+void tc_batch_release(BatchState& bs);
+
 // Grow a device buffer to at least `bytes` (contents not kept).
 void tc_ensure(DevBuf& b, size_t bytes);
 // TMA map of a K-major BF16 matrix (rows x row_elems, row_elems a multiple of
@@ -118,6 +143,22 @@ void tc_matvec(TcState& t, cudaStream_t st, const float* Xr, int nr, int ldxr, c
 // points, 2 FP16 points.  With autotuning on, this is where an untimed shape
 // gets timed (the tuner launches and synchronises, so never during capture).
 void tc_reserve(TcState& t, cudaStream_t st, int k, int gemm2 = 0, int fmt = 0);
+// The product of the training points split for a PCG loop that forms the
+// weights and finishes the chunk sums in its own kernels: ra (n_pad row
+// factors), w (n_pad x kv weights, w = ra v) and part (nchunk x n_pad x kv
+// chunk sums, q_i = ra_i sum_ch part[ch, i] + shift v_i).  tc_loop_prepare
+// prepares the operands and plan outside any capture and returns false when
+// the plan is not the full product (the symmetric plan), then tc_loop_product
+// enqueues the product kernel alone.
+struct TcLoop {
+  const float* ra = nullptr;
+  float* w = nullptr;
+  const float* part = nullptr;
+  int n_pad = 0, kv = 0, nchunk = 0;
+};
+bool tc_loop_prepare(TcState& t, cudaStream_t st, const float* X, int n, int ldx, int d,
+                     double sigma, int k, int split, int f16, TcLoop* out);
+void tc_loop_product(TcState& t, cudaStream_t st, int k, int split, int f16);
 // Plan selection of the fused product: 0 the fixed rule (default), 1 autotune,
 // 2 the symmetric kernel where it applies (k = 1, d <= 64, no split).
 void tc_set_autotune(TcState& t, int mode);

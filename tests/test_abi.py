@@ -68,7 +68,7 @@ def test_struct_layout_matches_c_compiler(lib_path):
 #include "krr.h"
 int main(void) {
   printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(krr_opts), offsetof(krr_opts, inner_tol),
-         offsetof(krr_opts, warm_start), offsetof(krr_opts, keep_direction), sizeof(krr_report),
+         offsetof(krr_opts, warm_start), offsetof(krr_opts, fuse_step), sizeof(krr_report),
          offsetof(krr_report, rel_res), offsetof(krr_report, ms_total));
   printf("%zu %zu\n", offsetof(krr_report, kappa), offsetof(krr_report, rel_res_rec));
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(krr_problem), offsetof(krr_problem, sigma),
@@ -86,7 +86,7 @@ int main(void) {
                                                check=True).stdout.split()]
     O, R, P = _krr.krr_opts, _krr.krr_report, _krr.krr_problem
     assert vals == [ctypes.sizeof(O), O.inner_tol.offset, O.warm_start.offset,
-                    O.keep_direction.offset, ctypes.sizeof(R), R.rel_res.offset,
+                    O.fuse_step.offset, ctypes.sizeof(R), R.rel_res.offset,
                     R.ms_total.offset, R.kappa.offset, R.rel_res_rec.offset,
                     ctypes.sizeof(P), P.sigma.offset, P.s.offset, P.Y.offset, P.C.offset,
                     P.ldc.offset]

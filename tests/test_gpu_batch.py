@@ -146,3 +146,80 @@ def test_batched_rejects_bad_arguments(K, h):
     probs[1].lam = -1.0
     with pytest.raises(K.KrrError):
         K.krr_pcg_solve_batched(h, items(probs), K.default_opts())
+
+
+def test_batched_mixed_one_launch_product(K, h):
+    """The FP16-point products of all low-level solves run as one persistent
+    launch per iteration (batch_product = 1, the default) instead of one
+    launch sequence per problem: the same solutions to the same tolerance,
+    iteration counts within the rounding noise of the FP32 inner loops."""
+    probs = ks.make_uneven(nprob=12, scale=0.2)
+    res_runs = {}
+    for bp in (0, 1):
+        opts = K.default_opts(tol=1e-6, max_iter=60000, precision="mixed", max_outer=60,
+                              batch_product=bp)
+        reps, Cs = _run(K, h, probs, opts)
+        res_runs[bp] = (reps, Cs)
+        for P, r, C in zip(probs, reps, Cs):
+            assert r["status_code"] == K.KRR_OK, (bp, P.name, P.n, P.d, r)
+            res = O.true_rel_residual(P.X, P.Y, C, P.sigma, P.lam)
+            hp_err = 0.0
+            if P.d <= 64:
+                scale = O.kernel_matvec_blocked(P.X, P.X, np.abs(C), P.sigma) + P.lam * np.abs(C)
+                hp_err = 2e-12 * np.linalg.norm(scale, axis=0) / np.linalg.norm(P.Y, axis=0)
+            assert np.all(res <= 1e-6 + hp_err), (bp, P.name, res, hp_err)
+    for r0, r1 in zip(res_runs[0][0], res_runs[1][0]):
+        a, b = r0["iters"][0], r1["iters"][0]
+        assert abs(a - b) <= 0.15 * max(a, b) + 10, (a, b)
+
+
+def test_batched_product_matches_single_products(K, h):
+    """The one-launch product of many problems (d = 16 ... 128, n from a few
+    hundred to a few thousand, ragged tiles) equals each problem's own FP16
+    product up to FP32 summation order (1e-5 of sum_j |K_ij||v_j|)."""
+    probs = ks.make_uneven(nprob=20, scale=0.15)
+    rng = np.random.default_rng(20)
+    items, Vs, Qs = [], [], []
+    for P in probs:
+        V = torch.from_numpy(rng.standard_normal((P.n, 1)).astype(np.float32)).cuda()
+        Q = torch.full((P.n, 1), float("nan"), dtype=torch.float32, device="cuda")
+        items.append((cuda(P.X), P.sigma, P.lam, V, Q))
+        Vs.append(V)
+        Qs.append(Q)
+    K.krr_kernel_matvec_batched(h, items)
+    torch.cuda.synchronize()
+    for P, (X, sigma, lam, V, Q) in zip(probs, items):
+        Q1 = torch.empty_like(Q)
+        K.krr_kernel_matvec(h, X, X, sigma, lam, V, Q1, "fp16")
+        scale = (torch.from_numpy(O.gaussian_kernel(P.X, P.X, sigma)).cuda()
+                 @ V.abs().double()).float() + lam * V.abs()
+        assert torch.all(torch.isfinite(Q))
+        assert torch.all((Q - Q1).abs() <= 1e-5 * scale), (P.name, P.n, P.d,
+                                                           float(((Q - Q1).abs() / scale).max()))
+
+
+@pytest.mark.parametrize("picks", [(37, 43, 61, 3, 59), (43,)])
+def test_batched_product_full_size(K, h, picks):
+    """The one-launch product at the uneven batch's full sizes (n = 20,284 ...
+    30,402 with d = 32, next to small problems): every problem's result equals
+    its own FP16 product to 1e-5 of sum_j |K_ij||v_j| (that scale from the FP64
+    product of |v|), over many items per CTA and chunks of eight column tiles."""
+    allp = ks.make_uneven()
+    probs = [allp[i] for i in picks]
+    rng = np.random.default_rng(sum(picks))
+    items = []
+    for P in probs:
+        V = torch.from_numpy(rng.standard_normal((P.n, 1)).astype(np.float32)).cuda()
+        Q = torch.full((P.n, 1), float("nan"), dtype=torch.float32, device="cuda")
+        items.append((cuda(P.X), P.sigma, P.lam, V, Q))
+    K.krr_kernel_matvec_batched(h, items)
+    torch.cuda.synchronize()
+    for P, (X, sigma, lam, V, Q) in zip(probs, items):
+        Q1 = torch.empty_like(Q)
+        K.krr_kernel_matvec(h, X, X, sigma, lam, V, Q1, "fp16")
+        S = torch.empty((P.n, 1), dtype=torch.float64, device="cuda")
+        K.krr_kernel_matvec(h, X, X, sigma, lam, V.abs().double(), S, "fp64")
+        torch.cuda.synchronize()
+        err = (Q.double() - Q1.double()).abs()
+        assert torch.all(torch.isfinite(Q)), P.name
+        assert torch.all(err <= 1e-5 * S), (P.name, P.n, P.d, float((err / S).max()))
