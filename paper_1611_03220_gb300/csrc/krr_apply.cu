@@ -455,7 +455,10 @@ zt_stream_kernel(const void* __restrict__ Zs, int n, int s, const T* __restrict_
         }
       }
     }
-    __syncthreads();  // every thread is done with the stage
+    // every thread is done with the stage; its reads are ordered before the
+    // bulk copy that refills it
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
     if (threadIdx.x == 0 && g + NSTG < nstage)
       stg_issue(ring, full, st, (const uint8_t*)Zs, (size_t)s * ES, (size_t)c0 * ES, seg_bytes,
                 r0 + (g + NSTG) * rps, min(rps, r1 - r0 - (g + NSTG) * rps));
@@ -643,6 +646,7 @@ zw_stream_kernel(const void* __restrict__ Zs, int n, int s, const double* __rest
         }
       }
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // see zt_stream_kernel
     __syncthreads();
     if (threadIdx.x == 0 && g + NSTG < nstage) {
       int a0, na;

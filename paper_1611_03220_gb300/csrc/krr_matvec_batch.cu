@@ -215,7 +215,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_batch_kernel(const __grid_const
         uint32_t raw[2][32];
         tmem_ld16_nowait(tbase, *reinterpret_cast<uint32_t(*)[16]>(&raw[0][0]));
         tmem_ld16_nowait(tbase + 16, *reinterpret_cast<uint32_t(*)[16]>(&raw[0][16]));
-        tmem_wait_ld();
+        tmem_wait_ld(*reinterpret_cast<uint32_t(*)[16]>(&raw[0][0]));
+        tmem_keep(*reinterpret_cast<uint32_t(*)[16]>(&raw[0][16]));
         constexpr int NCH = COLS / 32;
 #pragma unroll
         for (int cc = 0; cc < NCH; ++cc) {
@@ -241,7 +242,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_batch_kernel(const __grid_const
                             make_float2(wv.z, wv.w), qq);
           }
           if (cc + 1 < NCH) {
-            tmem_wait_ld();
+            tmem_wait_ld(*reinterpret_cast<uint32_t(*)[16]>(&raw[cur ^ 1][0]));
+            tmem_keep(*reinterpret_cast<uint32_t(*)[16]>(&raw[cur ^ 1][16]));
             if (cc + 2 == NCH) {
               fence_before();
               __syncwarp();
@@ -249,6 +251,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_batch_kernel(const __grid_const
             }
           }
         }
+        fence_proxy_async_smem();   // the weight slot goes back to the bulk copies
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&wempty[ws]));
         acc ^= 1;

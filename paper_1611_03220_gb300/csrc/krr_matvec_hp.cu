@@ -289,7 +289,9 @@ hp_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
           const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + acc * NLEV * BN + col0;
 #pragma unroll
           for (int m = 0; m < NLEV; ++m) tmem_ld16_nowait(tbase + m * BN, L[m]);
-          tmem_wait_ld();
+          tmem_wait_ld(L[0]);
+#pragma unroll
+          for (int m = 1; m < NLEV; ++m) tmem_keep(L[m]);
           if (cc == 1) {
             fence_before();
             __syncwarp();
@@ -334,6 +336,7 @@ hp_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             }
           }
         }
+        fence_proxy_async_smem();   // the weight slot goes back to the bulk copies
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&cempty[cs]));
         acc ^= 1;

@@ -313,7 +313,8 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         uint32_t raw[2][32];
         tmem_ld16_nowait(tbase, *reinterpret_cast<uint32_t(*)[16]>(&raw[0][0]));
         tmem_ld16_nowait(tbase + 16, *reinterpret_cast<uint32_t(*)[16]>(&raw[0][16]));
-        tmem_wait_ld();
+        tmem_wait_ld(*reinterpret_cast<uint32_t(*)[16]>(&raw[0][0]));
+        tmem_keep(*reinterpret_cast<uint32_t(*)[16]>(&raw[0][16]));
         if (NCH == 1) {
           fence_before();
           __syncwarp();
@@ -376,7 +377,8 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             }
           }
           if (cc + 1 < NCH) {
-            tmem_wait_ld();
+            tmem_wait_ld(*reinterpret_cast<uint32_t(*)[16]>(&raw[cur ^ 1][0]));
+            tmem_keep(*reinterpret_cast<uint32_t(*)[16]>(&raw[cur ^ 1][16]));
             if (cc + 2 == NCH) {
               fence_before();
               __syncwarp();
@@ -384,6 +386,7 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             }
           }
         }
+        fence_proxy_async_smem();   // the weight slot goes back to the bulk copies
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&wempty[ws]));
         acc ^= 1;
@@ -727,7 +730,8 @@ tc_matvec2_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant
         uint32_t raw[32];
         tmem_ld16_nowait(tbase, *reinterpret_cast<uint32_t(*)[16]>(&raw[0]));
         tmem_ld16_nowait(tbase + 16, *reinterpret_cast<uint32_t(*)[16]>(&raw[16]));
-        tmem_wait_ld();
+        tmem_wait_ld(*reinterpret_cast<uint32_t(*)[16]>(&raw[0]));
+        tmem_keep(*reinterpret_cast<uint32_t(*)[16]>(&raw[16]));
         fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&tempty[acc]));
@@ -757,7 +761,7 @@ tc_matvec2_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant
         fence_after();
         uint32_t dv[16];
         tmem_ld16_nowait(tmem + ((uint32_t)(quad * 32) << 16) + TMEM_D2, dv);
-        tmem_wait_ld();
+        tmem_wait_ld(dv);
         float* out = p.part + ((size_t)ch * p.n_rpad + (size_t)rt * BM + row) * p.kv;
 #pragma unroll
         for (int c = 0; c < N2; ++c)

@@ -149,7 +149,9 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
 #pragma unroll
   for (int q = 0; q < 4; ++q)
     tmem_ld16_nowait(taddr + 16 * q, *reinterpret_cast<uint32_t(*)[16]>(&r[16 * q]));
-  tmem_wait_ld();
+  tmem_wait_ld(*reinterpret_cast<uint32_t(*)[16]>(&r[0]));
+#pragma unroll
+  for (int q = 1; q < 4; ++q) tmem_keep(*reinterpret_cast<uint32_t(*)[16]>(&r[16 * q]));
 }
 
 // ------------------------------------------------------------ features --
