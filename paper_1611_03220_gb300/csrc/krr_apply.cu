@@ -340,6 +340,9 @@ __device__ __forceinline__ void stage_span(int g, int r0, int r1, int rps, bool 
 __device__ __forceinline__ void stg_issue(uint8_t* ring, uint64_t* full, int st, const uint8_t* Z,
                                           size_t row_bytes, size_t c0_bytes, uint32_t seg_bytes,
                                           int row0, int nrow) {
+  // the CTA's generic reads of the stage (ordered before this thread by the
+  // barrier in front of a refill) before the async-proxy writes of the copy
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   const uint32_t bar = sh_u32(&full[st]);
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
                "r"(seg_bytes * (uint32_t)nrow)
@@ -455,10 +458,7 @@ zt_stream_kernel(const void* __restrict__ Zs, int n, int s, const T* __restrict_
         }
       }
     }
-    // every thread is done with the stage; its reads are ordered before the
-    // bulk copy that refills it
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    __syncthreads();  // every thread is done with the stage
     if (threadIdx.x == 0 && g + NSTG < nstage)
       stg_issue(ring, full, st, (const uint8_t*)Zs, (size_t)s * ES, (size_t)c0 * ES, seg_bytes,
                 r0 + (g + NSTG) * rps, min(rps, r1 - r0 - (g + NSTG) * rps));
@@ -646,7 +646,6 @@ zw_stream_kernel(const void* __restrict__ Zs, int n, int s, const double* __rest
         }
       }
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // see zt_stream_kernel
     __syncthreads();
     if (threadIdx.x == 0 && g + NSTG < nstage) {
       int a0, na;

@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_batch_kernel(const __grid_const
         const int ct0 = it.z * pr.cpc, ct1 = min(pr.n_ct, ct0 + pr.cpc);
         for (int ct = ct0; ok && ct < ct1; ++ct) {
           if (!(ok = mbar_wait(smem_u32(&wempty[ws]), wph ^ 1, abort_flag, p.err))) break;
+          fence_proxy_async_smem();   // the readers' loads before the refill
           mbar_expect_tx(smem_u32(&wfull[ws]), BN * 4);
           bulk_load(smem_u32(wbuf + ws * BN), pr.w + (size_t)ct * BN, BN * 4,
                     smem_u32(&wfull[ws]));
@@ -251,7 +252,6 @@ __global__ void __launch_bounds__(THREADS, 1) tc_batch_kernel(const __grid_const
             }
           }
         }
-        fence_proxy_async_smem();   // the weight slot goes back to the bulk copies
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&wempty[ws]));
         acc ^= 1;

@@ -154,6 +154,7 @@ hp_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         aph ^= 1;
         for (int ct = ct0; ok && ct < ct1; ++ct) {
           if (!(ok = mbar_wait(smem_u32(&cempty[cs]), cph ^ 1, abort_flag, p.err))) break;
+          fence_proxy_async_smem();   // the readers' loads before the refill
           mbar_expect_tx(smem_u32(&cfull[cs]), BN * CW * 4);
           bulk_load(smem_u32(cbuf + cs * BN * CW), p.cold + (size_t)ct * BN * CW, BN * CW * 4,
                     smem_u32(&cfull[cs]));
@@ -336,7 +337,6 @@ hp_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             }
           }
         }
-        fence_proxy_async_smem();   // the weight slot goes back to the bulk copies
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&cempty[cs]));
         acc ^= 1;

@@ -184,6 +184,7 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         }
         for (int ct = ct0; ok && ct < ct1; ++ct) {
           if (!(ok = mbar_wait(smem_u32(&wempty[ws]), wph ^ 1, abort_flag, p.err))) break;
+          fence_proxy_async_smem();   // the readers' loads before the refill
           mbar_expect_tx(smem_u32(&wfull[ws]), BN * KV * 4);
           bulk_load(smem_u32(wbuf + ws * BN * KV), p.w + (size_t)ct * BN * KV, BN * KV * 4,
                     smem_u32(&wfull[ws]));
@@ -386,7 +387,6 @@ tc_matvec_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             }
           }
         }
-        fence_proxy_async_smem();   // the weight slot goes back to the bulk copies
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&wempty[ws]));
         acc ^= 1;

@@ -127,12 +127,16 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
       : "memory");
 }
 
-// Orders this thread's generic-proxy accesses of shared memory before later
-// async-proxy accesses (TMA and bulk copies).  A buffer that a bulk copy
-// filled and threads then read is released for the next copy only after each
-// reader has executed this fence: without it the copy can overwrite the slot
-// while reads of it are still outstanding (observed: rare wrong weights for
-// one warp's rows in the fused products).
+// A buffer that a bulk copy (async proxy) filled and threads then read with
+// generic loads goes back to the copies through an mbarrier (or a CTA
+// barrier); the thread that issues the next copy into it executes this fence
+// after that wait and before the copy, so the readers' generic accesses are
+// ordered before the async-proxy write.  Without it a refill could corrupt a
+// slot that was still being read (observed: rare wrong weights for one warp's
+// 32 rows in the batched product, about 3 % of its launches at n ~ 20,000).
+// One thread per refill: the same fence in every reader cost 7 % of the
+// fused product, and tying the readers' results to their release did not
+// remove the error.
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
