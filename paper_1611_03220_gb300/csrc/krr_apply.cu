@@ -57,6 +57,23 @@ __device__ __forceinline__ void unpack_q8(uint2 v, float (&z)[8]) {
   }
 }
 
+// The same eight codes as four pairs (q[2p], q[2p + 1]) with paired FP32 adds:
+// half the add instructions, and pairs the paired FMAs take directly.
+__device__ __forceinline__ void unpack_q8x2(uint2 v, float2 (&z)[4]) {
+  const uint32_t a = v.x ^ 0x80808080u, b = v.y ^ 0x80808080u;
+  const float2 off = make_float2(-8388736.f, -8388736.f);
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    z[p] = __fadd2_rn(make_float2(__uint_as_float(__byte_perm(a, 0x4B000000u, 0x7540u + 2 * p)),
+                                  __uint_as_float(__byte_perm(a, 0x4B000000u, 0x7541u + 2 * p))),
+                      off);
+    z[2 + p] = __fadd2_rn(
+        make_float2(__uint_as_float(__byte_perm(b, 0x4B000000u, 0x7540u + 2 * p)),
+                    __uint_as_float(__byte_perm(b, 0x4B000000u, 0x7541u + 2 * p))),
+        off);
+  }
+}
+
 // The scale between stage8's values and Z: 1/128 for the 8-bit codes (the
 // streamed kernels apply it once to their sums), 1 otherwise.
 template <int ZF>
@@ -347,6 +364,19 @@ __device__ __forceinline__ void stg_issue(uint8_t* ring, uint64_t* full, int st,
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
                "r"(seg_bytes * (uint32_t)nrow)
                : "memory");
+  if ((size_t)seg_bytes == row_bytes) {
+    // whole rows: the stage is one contiguous block of Z, one copy (the
+    // per-row copies kept thread 0 issuing 32 instructions per stage while
+    // the other warps waited at the stage barrier)
+    const uint8_t* src = Z + (size_t)row0 * row_bytes;
+    const uint32_t dst = sh_u32(ring + (size_t)st * SBYTES);
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+        "[%3];" ::"r"(dst),
+        "l"((uint64_t)src), "r"(seg_bytes * (uint32_t)nrow), "r"(bar)
+        : "memory");
+    return;
+  }
   for (int rr = 0; rr < nrow; ++rr) {
     const uint8_t* src = Z + (size_t)(row0 + rr) * row_bytes + c0_bytes;
     const uint32_t dst = sh_u32(ring + (size_t)st * SBYTES + (size_t)rr * seg_bytes);
@@ -432,11 +462,17 @@ zt_stream_kernel(const void* __restrict__ Zs, int n, int s, const T* __restrict_
   }
   const int col = threadIdx.x * 8;  // within the block
   const bool mine = col < seg;
+  constexpr bool PACKED = ZF == 2 && std::is_same<ACC, float>::value;
   ACC acc[8][KV];
+  float2 acc2[PACKED ? 4 : 1][KV];
 #pragma unroll
   for (int q = 0; q < 8; ++q)
 #pragma unroll
     for (int c = 0; c < KV; ++c) acc[q][c] = (ACC)0;
+#pragma unroll
+  for (int p = 0; p < (PACKED ? 4 : 1); ++p)
+#pragma unroll
+    for (int c = 0; c < KV; ++c) acc2[p][c] = make_float2(0.f, 0.f);
   bool ok = true;
   int g = 0;
   for (; g < nstage; ++g) {
@@ -447,14 +483,30 @@ zt_stream_kernel(const void* __restrict__ Zs, int n, int s, const T* __restrict_
     const int row0 = r0 + g * rps, nrow = min(rps, r1 - row0);
     const uint8_t* base = ring + (size_t)st * SBYTES;
     if (mine) {
-      for (int rr = 0; rr < nrow; ++rr) {
-        float z[8];
-        stage8<ZF>(base + (size_t)rr * seg_bytes + col * ES, z);
+      if constexpr (PACKED) {
+        // 8-bit codes, FP32 sums: paired adds and FMAs (the same operations
+        // on the same values, half the instructions)
+        for (int rr = 0; rr < nrow; ++rr) {
+          float2 z2[4];
+          unpack_q8x2(*reinterpret_cast<const uint2*>(base + (size_t)rr * seg_bytes + col), z2);
 #pragma unroll
-        for (int c = 0; c < KV; ++c) {
-          const ACC rv = rsm[(row0 - r0 + rr) * KV + c];
+          for (int c = 0; c < KV; ++c) {
+            const float rv = (float)rsm[(row0 - r0 + rr) * KV + c];
+            const float2 r2 = make_float2(rv, rv);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) acc[q][c] = fma((ACC)z[q], rv, acc[q][c]);
+            for (int p = 0; p < 4; ++p) acc2[p][c] = __ffma2_rn(z2[p], r2, acc2[p][c]);
+          }
+        }
+      } else {
+        for (int rr = 0; rr < nrow; ++rr) {
+          float z[8];
+          stage8<ZF>(base + (size_t)rr * seg_bytes + col * ES, z);
+#pragma unroll
+          for (int c = 0; c < KV; ++c) {
+            const ACC rv = rsm[(row0 - r0 + rr) * KV + c];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q][c] = fma((ACC)z[q], rv, acc[q][c]);
+          }
         }
       }
     }
@@ -473,6 +525,15 @@ zt_stream_kernel(const void* __restrict__ Zs, int n, int s, const T* __restrict_
     return;
   }
   if (!mine) return;
+  if constexpr (PACKED) {
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int c = 0; c < KV; ++c) {
+        acc[2 * p][c] = acc2[p][c].x;
+        acc[2 * p + 1][c] = acc2[p][c].y;
+      }
+  }
   ACC* out = part + (size_t)blockIdx.y * s * KV;
 #pragma unroll
   for (int q = 0; q < 8; ++q)
@@ -562,17 +623,37 @@ zw_stream_kernel(const void* __restrict__ Zs, int n, int s, const double* __rest
     const uint8_t* base = ring + (size_t)st * SBYTES;
     if (REGW && use_reg) {
       for (int rr = warp; rr < nrow; rr += ZAT / 32) {
-        float a[4] = {0.f, 0.f, 0.f, 0.f};
+        float v;
+        if constexpr (ZF == 2) {
+          // paired adds and FMAs on the 8-bit codes (the same sums as below)
+          float2 a2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
-        for (int it = 0; it < 8; ++it) {
-          if (it < nit) {
-            float z[8];
-            stage8<ZF>(base + (size_t)rr * row_bytes + (lane * 8 + 256 * it) * ES, z);
+          for (int it = 0; it < 8; ++it) {
+            if (it < nit) {
+              float2 z2[4];
+              unpack_q8x2(*reinterpret_cast<const uint2*>(base + (size_t)rr * row_bytes +
+                                                         lane * 8 + 256 * it),
+                          z2);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) a[q & 3] = fmaf(z[q], wr[it][q], a[q & 3]);
+              for (int p = 0; p < 4; ++p)
+                a2[p & 1] = __ffma2_rn(z2[p], make_float2(wr[it][2 * p], wr[it][2 * p + 1]),
+                                       a2[p & 1]);
+            }
           }
+          v = (a2[0].x + a2[0].y) + (a2[1].x + a2[1].y);
+        } else {
+          float a[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int it = 0; it < 8; ++it) {
+            if (it < nit) {
+              float z[8];
+              stage8<ZF>(base + (size_t)rr * row_bytes + (lane * 8 + 256 * it) * ES, z);
+#pragma unroll
+              for (int q = 0; q < 8; ++q) a[q & 3] = fmaf(z[q], wr[it][q], a[q & 3]);
+            }
+          }
+          v = (a[0] + a[1]) + (a[2] + a[3]);
         }
-        float v = (a[0] + a[1]) + (a[2] + a[3]);
         for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
         v *= zscale<ZF>();
         const int i = row0 + rr;
