@@ -61,10 +61,12 @@ def parse():
     ap.add_argument("--no-c3", action="store_true",
                     help="skip the d = 784, k = 10 product (workload 3's shape)")
     ap.add_argument("--profile", default=None,
-                    choices=["step", "bf16", "fp16", "fp16sym", "hp", "fp32", "apply"],
+                    choices=["step", "bf16", "fp16", "fp16sym", "hp", "fp32", "apply", "batch"],
                     help="short run for ncu: 'step' = one mixed and one FP32 solve of "
                          "--profile-iters PCG iterations with the host-driven loop (every "
-                         "launch listed); otherwise 3 launches of that kernel product / apply")
+                         "launch listed); 'batch' = 3 one-launch products of the 16 largest "
+                         "problems of the uneven batch; otherwise 3 launches of that kernel "
+                         "product / apply")
     ap.add_argument("--workload", type=int, default=None, choices=[3, 4, 5, 6],
                     help="solve one other workload at full size (mixed, tol 1e-6) and print "
                          "one JSON line of its results instead of the bench line; 6 is the "
@@ -305,6 +307,15 @@ def run_profile(args):
             rep = K.krr_pcg_solve(h, X, P.sigma, P.lam, W, b, Y, C, o, check=False)
             torch.cuda.synchronize()
             print(prec, rep["status"], rep["iters"], rep["matvecs"], flush=True)
+    elif args.profile == "batch":
+        probs = sorted(ks.make_uneven(), key=lambda q: -q.n)[:16]
+        rng = np.random.default_rng(4)
+        items = []
+        for q in probs:
+            Vb = torch.from_numpy(rng.standard_normal((q.n, 1)).astype(np.float32)).cuda()
+            items.append((torch.from_numpy(q.X).cuda(), q.sigma, q.lam, Vb, torch.empty_like(Vb)))
+        for _ in range(3):
+            K.krr_kernel_matvec_batched(h, items)
     elif args.profile == "apply":
         Z = torch.empty((n, P.s), dtype=torch.float32, device="cuda")
         K.krr_rff_features(h, X, W, b, Z)
