@@ -1555,7 +1555,7 @@ Tuned tune_shape(TcState& t, cudaStream_t st, TcOperand& op, int k, int fmt) {
 // the wave-balance rule.
 Plan resolve_plan(TcState& t, cudaStream_t st, TcOperand& op, int k, int gemm2, int fmt) {
   // the symmetric kernel is a tuner candidate only: at n = 65,536 it
-  // measures 0.85 ms against 0.65 ms for this kernel (see krr_matvec_sym.cu)
+  // measures 0.845 ms (16 epilogue warps) against 0.676 ms for this kernel
   Plan pl = plan_for(op, k, gemm2);
   if (!gemm2 && (t.autotune == 2 || t.autotune == 3) && sym_supported(op, k, fmt == 1)) {
     pl.sym = 1;   // asked for explicitly: 16 (mode 2) or 8 (mode 3) epilogue warps
